@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Throughput of the implicit multigroup source-term update on GB300.
+
+One step = one ``rhd_source_update`` call over the whole synthetic grid (all
+steps of the method: load, group table, inner Newton with the arrowhead
+elimination, write-back, flux and momentum update, outer iteration, store).
+The grid is restored from a pristine device copy before every step, outside
+the timed region; that copy (2 x 35 GB at the default size) also flushes L2.
+The metric is cell-group source updates per second: cells x groups advanced
+per second, every cell converged to the same tolerance.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+                    [--workload full_256cube_ng64] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank draws its own grid (seed + rank) and the
+ranks share no data: weak scaling, no collective on the data path.  Rank 0
+prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-group source updates/sec, mixed+surrogate vs FP64 Newton, same tol"
+UNIT = "cell-group updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
+    ap.add_argument("--fp64-steps", type=int, default=2,
+                    help="steps of the plain FP64 form timed beside a mixed run (0: skip)")
+    ap.add_argument("--workload", default="full_256cube_ng64")
+    ap.add_argument("--n-cells", type=int, default=None, help="override the cell count")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=2048,
+                    help="cells of the workload the CPU oracle baseline solves")
+    return ap.parse_args()
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allsum(x: float, ws: int) -> float:
+    if ws == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of the SM clock and throttle reasons while timing."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if f[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        loaded = [s for s in sm if s > 0.5 * max(sm)] if sm else []
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def fp_peaks() -> dict:
+    """Measured scalar FMA peaks (TFLOP/s) from the fp_peak microbenchmark."""
+    from paper_2407_18304_gb300 import build
+    try:
+        exe = build.build_fp_peak()
+        out = subprocess.run([exe, "5"], capture_output=True, text=True, timeout=120, check=True)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # the bench still reports, with the nominal figure
+        return {"error": str(e)}
+
+
+def run_ours(args, ws, rank):
+    from paper_2407_18304_gb300 import rhd, synth
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    name = args.workload
+    seed = synth.PRESET_SEED[name] + 1000 * rank
+    w = synth.preset(name, device=dev, n_cells=args.n_cells, seed=seed)
+    n, G = w.n_cells, w.n_groups
+    prec = rhd.FP64 if args.precision == "fp64" else rhd.MIXED
+    pristine = w.state
+    st = synth.clone_state(pristine)
+    status = torch.empty(n, dtype=torch.uint8, device=dev)
+    iters = torch.empty(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def restore():
+        for k in ("mom", "egas", "erad", "frad"):
+            st[k].copy_(pristine[k])
+
+    def timed(p, steps, warmup, sample_clocks=False):
+        """Run warmup + steps solves of precision p; per-step CUDA-event times."""
+        for _ in range(warmup):
+            restore()
+            rhd.source_update(st, w.edges, w.law, dt=w.dt, c_v=w.c_v, consts=w.consts,
+                              precision=p, status=status, iters=iters, stream=stream)
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        clocks = ClockSampler(dev.index)
+        if sample_clocks:
+            clocks.start()
+        barrier(ws)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in range(steps):
+            restore()
+            starts[k].record(stream)
+            rhd.source_update(st, w.edges, w.law, dt=w.dt, c_v=w.c_v, consts=w.consts,
+                              precision=p, status=status, iters=iters, stream=stream)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        wall = time.perf_counter() - t0
+        clk = clocks.stop() if sample_clocks else None
+        ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        stat = status.cpu().numpy()
+        it = iters.cpu().numpy().astype(np.int64)
+        return ms, wall, clk, float((stat == 0).mean()), float(it.mean())
+
+    ms, wall, clk, conv_frac, mean_iters = timed(prec, args.steps, args.warmup, True)
+    t_dev = sum(ms) / 1e3
+    t_max = allmax(t_dev, ws)
+    units = float(n) * G * args.steps
+    total_units = allsum(units, ws)
+
+    res = {"metric": METRIC, "value": total_units / t_max, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if prec == rhd.FP64 else "f32+f64",
+           "data": "synthetic (seeded; recipe in DESIGN.md)",
+           "config": {"workload": name, "cells": n, "n_groups": G, "precision": args.precision,
+                      "tol": 1e-11, "tol_outer": 1e-13,
+                      "l2": "state restored from a pristine copy before each step (2x state > L2)",
+                      "parallelism": f"weak x{ws}, no collective"},
+           "converged_fraction": conv_frac, "mean_newton_iters": mean_iters,
+           "gpu_launches": args.steps, "wall_s_timed": wall, "clocks": clk}
+
+    # the plain FP64 form on the same grid, same tolerance (the comparison)
+    if prec != rhd.FP64 and args.fp64_steps > 0:
+        ms64, _, _, conv64, it64 = timed(rhd.FP64, args.fp64_steps, 1)
+        t64 = allmax(sum(ms64) / 1e3, ws)
+        res["fp64_form"] = {"value": allsum(float(n) * G * args.fp64_steps, ws) / t64,
+                            "ms_per_step": 1e3 * t64 / args.fp64_steps, "steps": args.fp64_steps,
+                            "converged_fraction": conv64, "mean_newton_iters": it64}
+        res["speedup_vs_fp64_form"] = res["value"] / res["fp64_form"]["value"]
+
+    # roofline of the solve kernel (the only kernel of a step)
+    peaks = fp_peaks()
+    res["fp_peaks_measured"] = peaks
+    bytes_alg = n * (G * 64 + 82)  # in+out FP64 SoA per launch
+    mean_launch_s = t_dev / args.steps
+    peak = _measured_hbm()
+    ach = bytes_alg / mean_launch_s / 1e9
+    res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                       "frac": ach / peak, "traffic": None,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+
+    if not args.no_e2e:
+        res["e2e"] = run_e2e(args, w, prec, dev, ws)
+    if rank == 0 and ws == 1:
+        res["cpu_baseline"] = cpu_baseline(args, w)
+    return res
+
+
+def _measured_hbm() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except Exception:
+        return 6800.0
+
+
+def run_e2e(args, w, prec, dev, ws):
+    """The same metric through the C ABI with the state in pinned host memory:
+    H2D of the inputs, the call, D2H of the results, all inside the timing."""
+    from paper_2407_18304_gb300 import rhd
+    n, G = w.n_cells, w.n_groups
+    keys_in = ["rho", "mom", "egas", "kappa0", "erad", "frad"]
+    keys_out = ["mom", "egas", "erad", "frad"]
+    host_in = {k: torch.empty(tuple(w.state[k].shape), dtype=torch.float64, pin_memory=True)
+               for k in keys_in}
+    for k in keys_in:
+        host_in[k].copy_(w.state[k])
+    host_out = {k: torch.empty(tuple(host_in[k].shape), dtype=torch.float64, pin_memory=True)
+                for k in keys_out}
+    host_status = torch.empty(n, dtype=torch.uint8).pin_memory()
+    dst = {k: torch.empty_like(w.state[k]) for k in keys_in}
+    dst["src"] = None
+    status = torch.empty(n, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    h2d = sum(host_in[k].numel() * 8 for k in keys_in)
+    d2h = sum(host_out[k].numel() * 8 for k in keys_out) + n
+
+    def step():
+        for k in keys_in:
+            dst[k].copy_(host_in[k], non_blocking=True)
+        rhd.source_update(dst, w.edges, w.law, dt=w.dt, c_v=w.c_v, consts=w.consts,
+                          precision=prec, status=status, stream=stream)
+        for k in keys_out:
+            host_out[k].copy_(dst[k], non_blocking=True)
+        host_status.copy_(status, non_blocking=True)
+
+    step()
+    torch.cuda.synchronize()
+    barrier(ws)
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        step()
+    torch.cuda.synchronize()
+    dt = allmax(time.perf_counter() - t0, ws)
+    units = allsum(float(n) * G * args.e2e_steps, ws)
+    del dst
+    return {"value": units / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
+            "path": "pinned host -> device copies, rhd_source_update, device -> pinned host"}
+
+
+def cpu_baseline(args, w):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload."""
+    import oracle as O
+    from paper_2407_18304_gb300 import synth
+    m = min(args.cpu_sample, w.n_cells)
+    idx = torch.arange(m, device=w.state["rho"].device)
+    sub = synth.to_numpy(synth.take_cells(w.state, idx))
+    km, al = O.group_table(w.edges, O.PPL_FIXED, w.law.nu_break, w.law.seg_logk, w.law.seg_beta,
+                           w.law.nu_ref)
+    p = O.Params(c=w.consts["c"], c_hat=w.consts["c_hat"], a_rad=w.consts["a_rad"],
+                 h=w.consts["h"], k_B=w.consts["k_B"], c_v=w.c_v, dt=w.dt, max_iter=200)
+    t0 = time.perf_counter()
+    out = O.source_update(sub, p, O.Groups(w.edges, km, al))
+    dt = time.perf_counter() - t0
+    return {"value": m * w.n_groups / dt, "unit": UNIT, "cores": O.max_threads(), "kind": "oracle",
+            "sample": f"first {m} cells of the workload, all {w.n_groups} groups, one call",
+            "seconds": dt, "converged_fraction": float((out["status"] == 0).mean())}
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 oracle on the host cores, on bounded samples."""
+    if rank != 0:
+        return None
+    import oracle as O
+    from paper_2407_18304_gb300 import synth
+    m = min(args.cpu_sample // 4, 512)
+    w = synth.preset(args.workload, n_cells=m)
+    km, al = O.group_table(w.edges, O.PPL_FIXED, w.law.nu_break, w.law.seg_logk, w.law.seg_beta,
+                           w.law.nu_ref)
+    p = O.Params(c=w.consts["c"], c_hat=w.consts["c_hat"], a_rad=w.consts["a_rad"],
+                 h=w.consts["h"], k_B=w.consts["k_B"], c_v=w.c_v, dt=w.dt, max_iter=200)
+    g = O.Groups(w.edges, km, al)
+    st = synth.to_numpy(w.state)
+    for _ in range(args.warmup):
+        O.source_update(st, p, g)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        O.source_update(st, p, g)
+        times.append(time.perf_counter() - t0)
+    t = sum(times)
+    v = m * w.n_groups * args.steps / t
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": args.workload, "cells_per_step": m, "n_groups": w.n_groups},
+            "cpu_baseline": {"value": v, "unit": UNIT, "kind": "oracle", "cores": O.max_threads(),
+                             "sample": f"{m} cells of the workload per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    ws, rank = dist_setup(args) if args.impl == "ours" else (int(os.environ.get("WORLD_SIZE", "1")),
+                                                             int(os.environ.get("RANK", "0")))
+    if args.impl == "reference":
+        res = run_reference(args, ws, rank)
+    else:
+        res = run_ours(args, ws, rank)
+    if rank == 0 and res is not None:
+        print(json.dumps(res), flush=True)
+    if ws > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,151 @@
+/* rhd.h -- C ABI of the GB300 library for the implicit multigroup
+ * matter-radiation source-term update of He, Wibking & Krumholz (2024),
+ * "A novel numerical method for mixed-frame multigroup radiation-hydrodynamics
+ * with GPU acceleration implemented in the QUOKKA code".
+ *
+ * One call advances, in every cell independently, the implicit stage of Sec. 3:
+ * eqs. egupdate and eupdate (gas and group energies), vupdate and fupdate (gas
+ * momentum and group fluxes), with the four-force of eqs. G0_3 / G1_3 and the
+ * piecewise-powerlaw (PPL) mean opacities of Sec. 2.2.2.  Per cell it runs the
+ * paper's inner Newton-Raphson over x = (E_gas, R_1..R_Ng) with the arrowhead
+ * Jacobian of eq. matrix, eliminated in O(N_g), the convergence test after
+ * eq. matrix, the conservative energy write-back, the closed-form flux update
+ * eq. numF1, the momentum update that follows it, and the outer iteration of
+ * the last paragraph of Sec. 3.
+ *
+ * Units are the caller's (cgs in the paper, Table 1); the constants are fields
+ * so that dimensionless test units work as well.  The radiation constant and
+ * the Planck shape are used as 4 pi B_nu / c = a_R T^4 (15/pi^4) x^3/(e^x-1)
+ * dx/dnu with x = h nu / (k_B T), i.e. the group Planck integrals sum to
+ * a_R T^4 over all frequencies.
+ *
+ * Memory: every array pointer in rhd_state_t is a DEVICE pointer owned by the
+ * caller; the library never frees or keeps it.  Arrays in rhd_groups_t and
+ * rhd_opacity_law_t are HOST pointers, read during the call (they are packed
+ * into the launch).  Calls are asynchronous on `stream` (a cudaStream_t passed
+ * as void*, NULL = the legacy default stream).  Per-cell problems never fail a
+ * call; they are reported in status[].  Negative return values are errors;
+ * rhd_strerror() names them.  Not thread-safe for concurrent calls that share
+ * a context.
+ */
+#ifndef RHD_H
+#define RHD_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define RHD_OK 0
+#define RHD_EINVAL (-1)   /* a pointer, size or parameter is invalid */
+#define RHD_EEDGES (-2)   /* group edges not strictly increasing, or not finite and > 0 for PPL */
+#define RHD_ELAW (-3)     /* opacity law rejected (segment count, breakpoints, nu_ref) */
+#define RHD_ECUDA (-4)    /* a CUDA call failed (launch, copy, device query) */
+#define RHD_ENOMEM (-5)   /* workspace allocation failed */
+#define RHD_ESIZE (-6)    /* a size exceeds a compiled limit (groups, segments, grids) */
+
+/* compiled limits */
+#define RHD_MAX_GROUPS 256
+#define RHD_MAX_SEGMENTS 64
+
+/* rhd_state_t.precision */
+#define RHD_FP64 0  /* every step in FP64 */
+#define RHD_MIXED 1 /* FP32 Newton; FP64 Planck differences, final residual, write-back */
+
+/* rhd_state_t.closure (Sec. 2.1: applied group by group) */
+#define RHD_M1 0        /* Levermore (1984) M1 closure, the paper's default */
+#define RHD_EDDINGTON 1 /* P = E/3 I (used by the paper's radiative-shock test) */
+
+/* rhd_opacity_law_t.mode */
+#define RHD_PPL_FIXED 0 /* piecewise powerlaw, alpha_Q = -1 (Sec. 2.2.2, favoured) */
+#define RHD_PC 1        /* piecewise constant (Sec. 2.2.1) */
+
+/* rhd_state_t.flags */
+#define RHD_GROUP_TEST 1 /* also stop only when every group meets the tolerances relative
+                            to its own energy (the paper's tests are relative to E_tot,
+                            which leaves groups far below E_tot loosely converged) */
+
+/* per-cell status codes written to rhd_state_t.status */
+#define RHD_STATUS_OK 0
+#define RHD_STATUS_FALLBACK 1 /* converged after a fallback start */
+#define RHD_STATUS_MAXITER 2  /* an iteration cap was reached; the last iterate is written back */
+#define RHD_STATUS_INVALID 3  /* rho <= 0, E_int <= 0, non-finite or negative input: cell untouched */
+
+/* One grid's cell state, FP64 structure of arrays.  Per-cell arrays have
+ * n_cells entries; per-group arrays are [n_groups][group_stride] with the
+ * cell index fastest (group g of cell i at g*group_stride + i). */
+typedef struct {
+  const double *rho;    /* in    gas density, > 0 */
+  double *mom[3];       /* inout gas momentum density rho*v, one array per component */
+  double *egas;         /* inout total gas energy density (internal + kinetic) */
+  const double *kappa0; /* in    opacity normaliser: chi_0(nu) = rho*kappa0*khat(nu); NULL = 1 */
+  double *erad;         /* inout E_g, lab frame */
+  double *frad[3];      /* inout F_g components, lab frame */
+  const double *src;    /* in    optional radiation source S_g of eq. FGFR; NULL = 0 */
+  uint8_t *status;      /* out   per-cell status (RHD_STATUS_*); NULL = not written */
+  uint8_t *iters;       /* out   Newton iterations summed over outer passes, saturating
+                                 at 255; NULL = not written */
+  int64_t group_stride; /* elements between groups in erad/frad/src; 0 = n_cells */
+  double c_v;           /* specific heat per unit mass: E_int = rho*c_v*T */
+  double theta;         /* IMEX stage weight: 1 (first stage) or 1/2 (second), Sec. 3 */
+  double c, c_hat, a_rad, h, k_B; /* speed of light, reduced speed of light, radiation
+                                     constant, Planck and Boltzmann constants */
+  double tol;           /* Newton tolerance epsilon of the convergence test (paper: 1e-11);
+                           <= 0 selects 1e-11 */
+  double tol_outer;     /* outer-iteration tolerance (paper: 1e-13); <= 0 selects 1e-13 */
+  int32_t max_newton;   /* Newton cap per inner solve; <= 0 selects 64 */
+  int32_t max_outer;    /* outer-iteration cap; <= 0 selects 16 */
+  int32_t precision;    /* RHD_FP64 | RHD_MIXED */
+  int32_t closure;      /* RHD_M1 | RHD_EDDINGTON */
+  int32_t flags;        /* 0 (the paper's tests) or RHD_GROUP_TEST */
+} rhd_state_t;
+
+/* Lab-frame group edges (Sec. 2.1, eq. Qg: contiguous groups).  HOST array of
+ * n_groups+1 strictly increasing frequencies; PPL needs them finite and > 0,
+ * PC also accepts a first edge of 0 and a last edge of +inf. */
+typedef struct {
+  int32_t n_groups; /* 1 .. RHD_MAX_GROUPS */
+  const double *edges;
+} rhd_groups_t;
+
+/* Opacity shape khat(nu), chi_0 = rho*kappa0*khat(nu)*(T/T_ref)^temp_exponent.
+ * Either a piecewise powerlaw law -- segment s (s = 0..n_seg-1, separated by
+ * the n_seg-1 increasing breakpoints nu_break) has khat = exp(seg_logk[s] +
+ * seg_beta[s]*ln(nu/nu_ref)) -- or, when khat_gminus is non-NULL, a per-group
+ * table given directly (the paper lets the user give the slopes, Sec. 2.2.2).
+ * PPL_FIXED takes khat_gminus = khat just above nu_g- and alpha_g =
+ * ln(khat(nu_g+)/khat(nu_g-))/ln(nu_g+/nu_g-) (Sec. 2.2.2, the tabulated-opacity
+ * slope; a breakpoint on an edge belongs to the group above it).  PC takes khat
+ * at the logarithmic group centre and alpha = 0.  All arrays are HOST memory. */
+typedef struct {
+  int32_t mode;            /* RHD_PPL_FIXED | RHD_PC */
+  int32_t n_seg;           /* 1 .. RHD_MAX_SEGMENTS (ignored when khat_gminus != NULL) */
+  const double *nu_break;  /* [n_seg-1] */
+  const double *seg_logk;  /* [n_seg] natural log of khat at nu_ref for the segment's powerlaw */
+  const double *seg_beta;  /* [n_seg] powerlaw index of the segment */
+  double nu_ref;           /* > 0 */
+  const double *khat_gminus; /* [n_groups] optional per-group table: khat at the lower edge */
+  const double *alpha_g;     /* [n_groups] its in-group slopes (PC: ignored, alpha = 0) */
+  double temp_exponent, T_ref; /* optional (T/T_ref)^p factor; p = 0 disables it */
+} rhd_opacity_law_t;
+
+/* Advance every cell of one grid by one implicit source-term stage of length
+ * dt (in place).  n_cells may be 0.  Returns RHD_OK or a negative RHD_E* code
+ * (then nothing was launched).  The first call on a device initialises the
+ * library's constant tables on that device (synchronously), so make it before
+ * any stream capture. */
+int rhd_source_update(rhd_state_t *state, const rhd_groups_t *groups,
+                      const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
+                      void *stream);
+
+/* Text for a return code. */
+const char *rhd_strerror(int code);
+
+/* Library version (major*10000 + minor*100 + patch). */
+int rhd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,234 @@
+// rhd.cu -- host side of the C ABI in include/rhd.h: argument checks, the
+// once-per-device constant tables, and the kernel launches.  The kernels are
+// in rhd_fp64.cuh (FP64 form) and rhd_mixed.cuh (mixed form); this is the
+// only translation unit.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "rhd_common.cuh"
+#include "rhd_fp64.cuh"
+#include "rhd_mixed.cuh"
+
+namespace rhd {
+namespace {
+
+std::mutex g_mu;
+constexpr int kMaxDevices = 64;
+bool g_ready[kMaxDevices];
+int g_sms[kMaxDevices];
+
+// B_2j/(2j)! = (-1)^(j+1) 2 zeta(2j) / (2 pi)^(2j).  zeta(2j) in closed form for
+// j <= 4 and from the Euler product over the primes below 2000 for j >= 5
+// (the neglected factors differ from 1 by less than 2000^-10).
+void series_tables(double *b, double *b3, double *invn) {
+  const double pi = 3.14159265358979323846;
+  std::vector<int> primes;
+  std::vector<char> sieve(2000, 1);
+  for (int p = 2; p < 2000; ++p) {
+    if (!sieve[p]) continue;
+    primes.push_back(p);
+    for (int q = 2 * p; q < 2000; q += p) sieve[q] = 0;
+  }
+  for (int j = 1; j <= kNB; ++j) {
+    double zeta;
+    switch (j) {
+      case 1: zeta = std::pow(pi, 2) / 6.0; break;
+      case 2: zeta = std::pow(pi, 4) / 90.0; break;
+      case 3: zeta = std::pow(pi, 6) / 945.0; break;
+      case 4: zeta = std::pow(pi, 8) / 9450.0; break;
+      default: {
+        zeta = 1.0;
+        for (int p : primes) zeta /= (1.0 - std::pow((double)p, -2.0 * j));
+      }
+    }
+    const double sign = (j % 2 == 1) ? 1.0 : -1.0;
+    b[j - 1] = sign * 2.0 * zeta / std::pow(2.0 * pi, 2.0 * j);
+    b3[j - 1] = b[j - 1] / (2.0 * j + 3.0);
+  }
+  invn[0] = 0.0;
+  for (int n = 1; n <= kNQ; ++n) invn[n] = 1.0 / n;
+}
+
+int ensure_device(int *sms) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RHD_ECUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_ready[dev]) {
+    double b[kNB], b3[kNB], invn[kNQ + 1];
+    series_tables(b, b3, invn);
+    if (cudaMemcpyToSymbol(c_bern, b, sizeof(b)) != cudaSuccess) return RHD_ECUDA;
+    if (cudaMemcpyToSymbol(c_bern3, b3, sizeof(b3)) != cudaSuccess) return RHD_ECUDA;
+    if (cudaMemcpyToSymbol(c_invn, invn, sizeof(invn)) != cudaSuccess) return RHD_ECUDA;
+    float bf[kNB32], b3f[kNB32], invnf[kNQ32 + 1];
+    for (int j = 0; j < kNB32; ++j) {
+      bf[j] = (float)b[j];
+      b3f[j] = (float)b3[j];
+    }
+    for (int n = 0; n <= kNQ32; ++n) invnf[n] = (float)invn[n];
+    if (cudaMemcpyToSymbol(c_bern_f, bf, sizeof(bf)) != cudaSuccess) return RHD_ECUDA;
+    if (cudaMemcpyToSymbol(c_bern3_f, b3f, sizeof(b3f)) != cudaSuccess) return RHD_ECUDA;
+    if (cudaMemcpyToSymbol(c_invn_f, invnf, sizeof(invnf)) != cudaSuccess) return RHD_ECUDA;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+      return RHD_ECUDA;
+    g_sms[dev] = n;
+    g_ready[dev] = true;
+  }
+  *sms = g_sms[dev];
+  return RHD_OK;
+}
+
+bool pos_finite(double x) { return std::isfinite(x) && x > 0.0; }
+
+// Fill the launch parameters from the public structs; RHD_OK or an error.
+int pack(const rhd_state_t *s, const rhd_groups_t *gr, const rhd_opacity_law_t *law, double dt,
+         int64_t n, KParams *kp) {
+  if (!s || !gr || !law || n < 0) return RHD_EINVAL;
+  if (gr->n_groups < 1) return RHD_EINVAL;
+  if (gr->n_groups > kMaxG) return RHD_ESIZE;
+  if (!gr->edges) return RHD_EINVAL;
+  const int G = gr->n_groups;
+  if (n > 0 && (!s->rho || !s->mom[0] || !s->mom[1] || !s->mom[2] || !s->egas || !s->erad ||
+                !s->frad[0] || !s->frad[1] || !s->frad[2]))
+    return RHD_EINVAL;
+  const int64_t gs = s->group_stride == 0 ? n : s->group_stride;
+  if (gs < n) return RHD_EINVAL;
+  if (!pos_finite(s->c_v) || !pos_finite(s->theta) || !pos_finite(s->c) || !pos_finite(s->c_hat) ||
+      !pos_finite(s->a_rad) || !pos_finite(s->h) || !pos_finite(s->k_B))
+    return RHD_EINVAL;
+  if (!std::isfinite(dt) || dt < 0.0) return RHD_EINVAL;
+  if (s->precision != RHD_FP64 && s->precision != RHD_MIXED) return RHD_EINVAL;
+  if (s->closure != RHD_M1 && s->closure != RHD_EDDINGTON) return RHD_EINVAL;
+  if (s->flags & ~RHD_GROUP_TEST) return RHD_EINVAL;
+  if (law->mode != RHD_PPL_FIXED && law->mode != RHD_PC) return RHD_ELAW;
+  // edges: strictly increasing; PPL needs finite positive edges
+  for (int e = 0; e <= G; ++e) {
+    const double x = gr->edges[e];
+    if (std::isnan(x) || x < 0.0) return RHD_EEDGES;
+    if (e > 0 && !(x > gr->edges[e - 1])) return RHD_EEDGES;
+    if (law->mode == RHD_PPL_FIXED && !pos_finite(x)) return RHD_EEDGES;
+    if (law->mode == RHD_PC && std::isinf(x) && e != G) return RHD_EEDGES;
+  }
+  std::memset(kp, 0, sizeof(KParams));
+  kp->has_table = law->khat_gminus != nullptr;
+  if (kp->has_table) {
+    for (int g = 0; g < G; ++g) {
+      if (!pos_finite(law->khat_gminus[g])) return RHD_ELAW;
+      kp->khat_g[g] = law->khat_gminus[g];
+      if (law->mode == RHD_PPL_FIXED) {
+        if (!law->alpha_g || !std::isfinite(law->alpha_g[g])) return RHD_ELAW;
+        kp->alpha_g[g] = law->alpha_g[g];
+      }
+    }
+    kp->n_seg = 1;
+    kp->nu_ref = 1.0;
+  } else {
+    if (law->n_seg < 1) return RHD_ELAW;
+    if (law->n_seg > kMaxSeg) return RHD_ESIZE;
+    if (!law->seg_logk || !law->seg_beta || (law->n_seg > 1 && !law->nu_break)) return RHD_ELAW;
+    if (!pos_finite(law->nu_ref)) return RHD_ELAW;
+    for (int k = 0; k < law->n_seg; ++k) {
+      if (!std::isfinite(law->seg_logk[k]) || !std::isfinite(law->seg_beta[k])) return RHD_ELAW;
+      kp->seg_logk[k] = law->seg_logk[k];
+      kp->seg_beta[k] = law->seg_beta[k];
+    }
+    for (int k = 0; k + 1 < law->n_seg; ++k) {
+      if (!pos_finite(law->nu_break[k])) return RHD_ELAW;
+      if (k > 0 && !(law->nu_break[k] > law->nu_break[k - 1])) return RHD_ELAW;
+      kp->nu_break[k] = law->nu_break[k];
+    }
+    kp->n_seg = law->n_seg;
+    kp->nu_ref = law->nu_ref;
+  }
+  if (!std::isfinite(law->temp_exponent)) return RHD_ELAW;
+  if (law->temp_exponent != 0.0 && !pos_finite(law->T_ref)) return RHD_ELAW;
+  kp->temp_exp = law->temp_exponent;
+  kp->T_ref = law->temp_exponent != 0.0 ? law->T_ref : 1.0;
+  for (int e = 0; e <= G; ++e) kp->edges[e] = gr->edges[e];
+
+  kp->rho = s->rho;
+  for (int d = 0; d < 3; ++d) {
+    kp->mom[d] = s->mom[d];
+    kp->frad[d] = s->frad[d];
+  }
+  kp->egas = s->egas;
+  kp->kappa0 = s->kappa0;
+  kp->erad = s->erad;
+  kp->src = s->src;
+  kp->status = s->status;
+  kp->iters = s->iters;
+  kp->n = n;
+  kp->gs = gs;
+  kp->c_v = s->c_v;
+  kp->theta = s->theta;
+  kp->dt = dt;
+  kp->c = s->c;
+  kp->c_hat = s->c_hat;
+  kp->a_rad = s->a_rad;
+  kp->h_over_k = s->h / s->k_B;
+  kp->tol = s->tol > 0.0 ? s->tol : 1e-11;
+  kp->tol_outer = s->tol_outer > 0.0 ? s->tol_outer : 1e-13;
+  kp->max_newton = s->max_newton > 0 ? s->max_newton : 64;
+  kp->max_outer = s->max_outer > 0 ? s->max_outer : 16;
+  kp->closure = s->closure;
+  kp->flags = s->flags;
+  kp->G = G;
+  kp->mode = law->mode;
+  return RHD_OK;
+}
+
+int launch(const KParams &kp, int precision, int sms, cudaStream_t st) {
+  const int threads = 128;
+  const int64_t want = (kp.n + threads - 1) / threads;
+  const int blocks = (int)(want < (int64_t)sms * 32 ? want : (int64_t)sms * 32);
+  const size_t smem = table_bytes(kp.G);
+  if (precision == RHD_FP64) {
+    if (kp.G <= 16)
+      solve_fp64_kernel<16><<<blocks, threads, smem, st>>>(kp);
+    else if (kp.G <= 64)
+      solve_fp64_kernel<64><<<blocks, threads, smem, st>>>(kp);
+    else
+      solve_fp64_kernel<kMaxG><<<blocks, threads, smem, st>>>(kp);
+  } else {
+    if (kp.G <= 16)
+      solve_mixed_kernel<16><<<blocks, threads, smem, st>>>(kp);
+    else if (kp.G <= 64)
+      solve_mixed_kernel<64><<<blocks, threads, smem, st>>>(kp);
+    else
+      solve_mixed_kernel<kMaxG><<<blocks, threads, smem, st>>>(kp);
+  }
+  return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
+}
+
+}  // namespace
+}  // namespace rhd
+
+extern "C" int rhd_source_update(rhd_state_t *state, const rhd_groups_t *groups,
+                                 const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
+                                 void *stream) {
+  static thread_local rhd::KParams kp;
+  int rc = rhd::pack(state, groups, opacity_law, dt, n_cells, &kp);
+  if (rc != RHD_OK) return rc;
+  if (n_cells == 0) return RHD_OK;
+  int sms = 0;
+  rc = rhd::ensure_device(&sms);
+  if (rc != RHD_OK) return rc;
+  return rhd::launch(kp, state->precision, sms, (cudaStream_t)stream);
+}
+
+extern "C" const char *rhd_strerror(int code) {
+  switch (code) {
+    case RHD_OK: return "ok";
+    case RHD_EINVAL: return "invalid argument";
+    case RHD_EEDGES: return "invalid group edges";
+    case RHD_ELAW: return "invalid opacity law";
+    case RHD_ECUDA: return "CUDA error";
+    case RHD_ENOMEM: return "out of workspace memory";
+    case RHD_ESIZE: return "size exceeds a compiled limit";
+    default: return "unknown error";
+  }
+}
+
+extern "C" int rhd_version(void) { return 100; }

@@ -1,0 +1,242 @@
+// rhd_common.cuh -- launch parameters, the per-grid group table and the FP64
+// Planck / closure building blocks shared by the solver kernels.
+//
+// Notation follows He, Wibking & Krumholz (2024): x = h nu / (k_B T); the
+// group Planck integral b_g = 4 pi B_g / c = a_R T^4 [P(x_g+) - P(x_g-)] with
+// P(x) = (15/pi^4) int_0^x t^3/(e^t-1) dt (eq. Qg applied to B_nu); the edge
+// term D(x) = (15/pi^4) x^4/(e^x-1) = nu (4 pi B_nu / c) / (a_R T^4), so that
+// (4 pi/c) Delta_g(nu B_nu) = a_R T^4 [D(x_g+) - D(x_g-)] (Sec. 2.2.1) and
+// (4 pi/c) Delta_g(nu chi_0 B_nu) = a_R T^4 [chi_0(nu_g+) D(x_g+) -
+// chi_0(nu_g-) D(x_g-)] with chi_0 at each edge from group g's own powerlaw.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/rhd.h"
+
+namespace rhd {
+
+constexpr int kMaxG = RHD_MAX_GROUPS;
+constexpr int kMaxSeg = RHD_MAX_SEGMENTS;
+constexpr int kNB = 18;  // Bernoulli terms of the small-x series (x < 2)
+constexpr int kNQ = 21;  // exponential terms of the large-x series (x >= 2)
+constexpr double kPlanckNorm = 0.15398973382026502;  // 15 / pi^4
+constexpr double kXSplit = 2.0;
+
+// Everything one launch needs, passed by value (about 8 KB; the group table
+// is built from it inside each CTA).
+struct KParams {
+  const double *rho;
+  double *mom[3];
+  double *egas;
+  const double *kappa0;
+  double *erad;
+  double *frad[3];
+  const double *src;
+  uint8_t *status;
+  uint8_t *iters;
+  int64_t n;   // cells
+  int64_t gs;  // group stride
+  double c_v, theta, dt, c, c_hat, a_rad, h_over_k;
+  double tol, tol_outer;
+  int max_newton, max_outer, closure, flags;
+  int G, mode, n_seg, has_table;
+  double nu_ref, temp_exp, T_ref;
+  double edges[kMaxG + 1];
+  double nu_break[kMaxSeg];
+  double seg_logk[kMaxSeg];
+  double seg_beta[kMaxSeg];
+  double khat_g[kMaxG];
+  double alpha_g[kMaxG];
+};
+
+// Shared-memory group table, structure of arrays:
+//   xe[G+1]  h nu_e / k_B of every edge (x_e = xe[e] / T)
+//   kbar[G]  PPL fixed-slope mean opacity shape khat_g- (r^a - 1)/(a ln r)
+//            (eq. chiQg with alpha_Q = -1), so chi_B = chi_E = rho kappa0 kbar
+//   ikbar[G] 1 / kbar
+//   rm[G]    khat_g- / kbar   (chi_0 at the lower edge over chi_E)
+//   rp[G]    khat_g- r^a / kbar (chi_0 at the upper edge over chi_E)
+//   alpha[G] in-group powerlaw index a
+// and FP32 copies xef[G+1], rmf, rpf, alphaf (read by the FP32 iterations, so
+// they never convert).
+struct GroupTable {
+  const double *xe, *kbar, *ikbar, *rm, *rp, *alpha;
+  const float *xef, *rmf, *rpf, *alphaf;
+};
+
+constexpr int kTableArrays = 6;
+__host__ __device__ __forceinline__ size_t table_bytes(int G) {
+  return sizeof(double) * (kTableArrays * G + 1) + sizeof(float) * (4 * G + 1);
+}
+
+// khat from the piecewise law; right = 1 takes the segment above a breakpoint
+// that coincides with nu, right = 0 the one below.
+__device__ inline double law_logk(const KParams &P, double nu, int right) {
+  int s = 0;
+  for (int b = 0; b < P.n_seg - 1; ++b) {
+    const double nb = P.nu_break[b];
+    if (right ? (nb <= nu) : (nb < nu)) s = b + 1;
+  }
+  return P.seg_logk[s] + P.seg_beta[s] * log(nu / P.nu_ref);
+}
+
+// (r^a - 1)/(a ln r), 1 at a = 0 (Taylor near 0)
+__device__ inline double ppl_mean_factor(double a, double lr) {
+  const double z = a * lr;
+  if (fabs(z) < 1e-6) return 1.0 + z * (0.5 + z * (1.0 / 6.0 + z * (1.0 / 24.0)));
+  return expm1(z) / z;
+}
+
+// Build the group table in shared memory (step a2): all threads of the CTA
+// take part; ends with __syncthreads().
+__device__ inline GroupTable build_table(const KParams &P, double *sm) {
+  const int G = P.G;
+  double *xe = sm, *kbar = sm + G + 1, *ikbar = kbar + G, *rm = ikbar + G, *rp = rm + G,
+         *alp = rp + G;
+  for (int t = threadIdx.x; t <= G; t += blockDim.x) {
+    xe[t] = P.h_over_k * P.edges[t];  // inf stays inf, 0 stays 0
+    if (t == G) continue;
+    const double n0 = P.edges[t], n1 = P.edges[t + 1];
+    if (P.mode == RHD_PPL_FIXED) {
+      const double lr = log(n1 / n0);
+      double lk0, a;
+      if (P.has_table) {
+        lk0 = log(P.khat_g[t]);
+        a = P.alpha_g[t];
+      } else {
+        lk0 = law_logk(P, n0, 1);
+        a = (law_logk(P, n1, 0) - lk0) / lr;
+      }
+      const double mf = ppl_mean_factor(a, lr);
+      kbar[t] = exp(lk0) * mf;
+      ikbar[t] = 1.0 / kbar[t];
+      rm[t] = 1.0 / mf;
+      rp[t] = exp(a * lr) / mf;
+      alp[t] = a;
+    } else {
+      double k0;
+      if (P.has_table) {
+        k0 = P.khat_g[t];
+      } else {
+        double centre;
+        if (n0 == 0.0 && isinf(n1)) centre = P.nu_ref;
+        else if (n0 == 0.0) centre = 0.5 * n1;
+        else if (isinf(n1)) centre = 2.0 * n0;
+        else centre = sqrt(n0 * n1);
+        k0 = exp(law_logk(P, centre, 1));
+      }
+      kbar[t] = k0;
+      ikbar[t] = 1.0 / k0;
+      rm[t] = 1.0;
+      rp[t] = 1.0;
+      alp[t] = 0.0;
+    }
+  }
+  float *xef = reinterpret_cast<float *>(alp + G), *rmf = xef + G + 1, *rpf = rmf + G,
+        *alf = rpf + G;
+  __syncthreads();
+  for (int t = threadIdx.x; t <= G; t += blockDim.x) {
+    xef[t] = (float)xe[t];
+    if (t == G) continue;
+    rmf[t] = (float)rm[t];
+    rpf[t] = (float)rp[t];
+    alf[t] = (float)alp[t];
+  }
+  __syncthreads();
+  return GroupTable{xe, kbar, ikbar, rm, rp, alp, xef, rmf, rpf, alf};
+}
+
+// Series coefficients (set once per device by the host):
+//   c_bern[j-1]  = B_2j / (2j)!          x/(e^x-1) = 1 - x/2 + sum_j c_bern x^(2j)
+//   c_bern3[j-1] = B_2j / ((2j)! (2j+3))  int_0^x t^3/(e^t-1) dt
+//                                          = x^3/3 - x^4/8 + x^3 sum_j c_bern3 x^(2j)
+//   c_invn[n]    = 1/n
+// (This header is compiled into exactly one translation unit, rhd.cu.)
+__constant__ double c_bern[kNB];
+__constant__ double c_bern3[kNB];
+__constant__ double c_invn[kNQ + 1];
+
+// FP64 edge values: pq = P(x) when low (x < 2), else Q(x) = 1 - P(x);
+// d = D(x) = (15/pi^4) x^4/(e^x-1).  Small x: Bernoulli series (no
+// transcendental); large x: sum_n e^(-n x) (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4)
+// (Widger & Woodall 1976) with the terms cut where e^(-(n-1)x) < 1e-17.
+__device__ __forceinline__ void edge_fp64(double x, double &pq, double &d, bool &low) {
+  if (!(x > 0.0)) {
+    pq = 0.0;
+    d = 0.0;
+    low = true;
+    return;
+  }
+  if (isinf(x)) {
+    pq = 0.0;
+    d = 0.0;
+    low = false;
+    return;
+  }
+  if (x < kXSplit) {
+    const double z = x * x;
+    double s1 = c_bern[kNB - 1], s3 = c_bern3[kNB - 1];
+#pragma unroll
+    for (int j = kNB - 2; j >= 0; --j) {
+      s1 = fma(s1, z, c_bern[j]);
+      s3 = fma(s3, z, c_bern3[j]);
+    }
+    const double x3 = z * x;
+    pq = kPlanckNorm * x3 * fma(z, s3, fma(-0.125, x, 1.0 / 3.0));
+    d = kPlanckNorm * x3 * fma(z, s1, fma(-0.5, x, 1.0));
+    low = true;
+  } else {
+    const double e1 = exp(-x);
+    int nmax = (int)(39.0 / x) + 1;
+    if (nmax > kNQ) nmax = kNQ;
+    const double x2 = x * x, x3 = x2 * x, sx = 6.0 * x, tx2 = 3.0 * x2;
+    double en = 1.0, sum = 0.0;
+    for (int n = 1; n <= nmax; ++n) {
+      en *= e1;
+      const double inv = c_invn[n];
+      double h = fma(6.0, inv, sx);
+      h = fma(h, inv, tx2);
+      h = fma(h, inv, x3);
+      sum = fma(en * inv, h, sum);
+    }
+    pq = kPlanckNorm * sum;
+    d = kPlanckNorm * x3 * x * e1 / (1.0 - e1);
+    low = false;
+  }
+}
+
+// Planck fraction of the band between a lower and an upper edge value.
+__device__ __forceinline__ double band_fp64(double pqL, bool lowL, double pqU, bool lowU) {
+  if (!lowL) return pqL - pqU;            // Q(x-) - Q(x+): no 1 - 1 cancellation
+  if (lowU) return pqU - pqL;             // P(x+) - P(x-)
+  return (1.0 - pqU) - pqL;               // edges straddle the split
+}
+
+// v . P_g for the closure P(E, F) applied to one group (Sec. 2.1).
+template <typename R>
+__device__ __forceinline__ void closure_vP(int closure, R c, R E, R F0, R F1, R F2, R v0, R v1,
+                                           R v2, R &o0, R &o1, R &o2) {
+  const R fn2 = F0 * F0 + F1 * F1 + F2 * F2;
+  R iso = R(1) / R(3), dir = R(0);
+  R n0 = R(0), n1 = R(0), n2 = R(0);
+  if (closure == RHD_M1 && E > R(0) && fn2 > R(0)) {
+    const R fn = sqrt(fn2);
+    R f = fn / (c * E);
+    if (f > R(1)) f = R(1);
+    const R f2 = f * f;
+    const R chi = (R(3) + R(4) * f2) / (R(5) + R(2) * sqrt(R(4) - R(3) * f2));
+    iso = R(0.5) * (R(1) - chi);
+    dir = R(0.5) * (R(3) * chi - R(1));
+    const R inv = R(1) / fn;
+    n0 = F0 * inv;
+    n1 = F1 * inv;
+    n2 = F2 * inv;
+  }
+  const R vn = (v0 * n0 + v1 * n1 + v2 * n2) * dir;
+  o0 = E * (iso * v0 + vn * n0);
+  o1 = E * (iso * v1 + vn * n1);
+  o2 = E * (iso * v2 + vn * n2);
+}
+
+}  // namespace rhd

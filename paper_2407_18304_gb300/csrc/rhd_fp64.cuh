@@ -1,0 +1,319 @@
+// rhd_fp64.cuh -- the FP64 passes of the per-cell implicit source-term update.
+//
+// One thread owns one cell (grid-stride loop).  The per-group arrays of a cell
+// live in thread-local storage; loads of the state are coalesced because the
+// cell index is the fastest index of every group array.  The algorithm is the
+// paper's (Sec. 3):
+//   outer pass k (v, F_g frozen at the k-th iterate):
+//     inner Newton-Raphson over x = (E_gas, R_1..R_Ng):
+//       residual F_G, F_R,g of eq. FGFR with R_g of eq. Rnew (c_hat/c factor
+//       included), Jacobian entries after eq. linear with
+//       d(chi_B/chi_E)/dT := 0 and the T-dependence of chi_F dropped,
+//       arrowhead elimination of eq. matrix, convergence test after eq. matrix,
+//       then each R_g from its own row at the converged T;
+//     conservative write-back E_g = E_g^t + R_g + S_g,
+//       E_gas = E_gas^t - (c/c_hat) sum_g R_g;
+//     flux update eq. numF1 with the outdated velocity v_k, P_g from the
+//       closure of (E_g^new, F_g^k);
+//     momentum update (rho v) = (rho v)^t - (c c_hat)^-1 sum_g (F_g^new - F_g^t);
+//     stop when the v,F-terms of R_g (and the kinetic energy, which sets T)
+//     changed by less than tol_outer E_tot.
+// The gas energy is carried as E_int = E_gas - E_kin (E_kin frozen within an
+// inner solve, so the Newton steps in E_gas and E_int are the same).
+#pragma once
+#include "rhd_common.cuh"
+
+namespace rhd {
+
+// eq. chiDiff as chi_F / chi_E, from b_g, (4pi/c)Delta_g(nu B_nu) = aT4 dD and
+// the edge values; held to [min, max] of chi_0 / chi_E over the group.
+template <typename R>
+__device__ __forceinline__ R chiF_ratio(R b, R aT4, R dD, R a, R rm, R rp, R dL, R dU) {
+  const R den = R(4.0 / 3.0) * b - R(1.0 / 3.0) * aT4 * dD;
+  R q = R(1);
+  if (den > R(0)) q = (R(4.0 / 3.0) * b + R(1.0 / 3.0) * (a * b - aT4 * (rp * dU - rm * dL))) / den;
+  return fmin(fmax(q, fmin(rm, rp)), fmax(rm, rp));
+}
+
+// Per-cell constants and the FP64 iterate of one cell.
+struct Cell {
+  int64_t i;
+  double rho, m0[3], eg0, chi0s, Etot, rcv, irc;
+  double m[3];     // momentum of the current outer iterate
+  double Eint;     // internal energy of the current inner iterate
+  double egas_new; // written-back total gas energy
+  double cs;       // rho kappa0 (T/T_ref)^p of the last evaluation
+  double its;      // 1 / (c_hat theta dt cs)
+  int nit, stat;
+};
+
+// Thread-local per-group arrays of the FP64 passes.
+template <int MAXG>
+struct Arr64 {
+  double R[MAXG], w[MAXG], FR[MAXG], dg[MAXG], qe[MAXG];
+  double bq[MAXG], dnx[MAXG], qF[MAXG];
+  double Fk[3 * MAXG];
+};
+
+// Load and validate one cell (step a1); false = invalid (status written).
+template <int MAXG>
+__device__ __forceinline__ bool load_cell(const KParams &P, int64_t i, Cell &C, Arr64<MAXG> &A) {
+  const int G = P.G;
+  C.i = i;
+  C.rho = P.rho[i];
+  C.m0[0] = P.mom[0][i];
+  C.m0[1] = P.mom[1][i];
+  C.m0[2] = P.mom[2][i];
+  C.eg0 = P.egas[i];
+  const double k0 = P.kappa0 ? P.kappa0[i] : 1.0;
+  bool valid = C.rho > 0.0 && isfinite(C.rho) && isfinite(C.eg0) && isfinite(k0) && k0 >= 0.0 &&
+               isfinite(C.m0[0]) && isfinite(C.m0[1]) && isfinite(C.m0[2]);
+  const double KE0 = 0.5 * (C.m0[0] * C.m0[0] + C.m0[1] * C.m0[1] + C.m0[2] * C.m0[2]) / C.rho;
+  valid = valid && (C.eg0 - KE0 > 0.0);
+  double sumE0 = 0.0, sumS = 0.0;
+  for (int g = 0; g < G; ++g) {
+    const int64_t o = (int64_t)g * P.gs + i;
+    const double e = P.erad[o], s = P.src ? P.src[o] : 0.0;
+    const double f0 = P.frad[0][o], f1 = P.frad[1][o], f2 = P.frad[2][o];
+    valid = valid && isfinite(e) && isfinite(s) && isfinite(f0) && isfinite(f1) && isfinite(f2);
+    sumE0 += e;
+    sumS += s;
+    A.Fk[3 * g] = f0;
+    A.Fk[3 * g + 1] = f1;
+    A.Fk[3 * g + 2] = f2;
+    A.R[g] = 0.0;
+  }
+  if (!valid) {
+    if (P.status) P.status[i] = RHD_STATUS_INVALID;
+    if (P.iters) P.iters[i] = 0;
+    return false;
+  }
+  C.chi0s = C.rho * k0;
+  C.Etot = C.eg0 + (P.c / P.c_hat) * (sumE0 + sumS);  // energy at the start (reading: c/c_hat)
+  C.rcv = C.rho * P.c_v;
+  C.irc = 1.0 / C.rcv;
+  C.m[0] = C.m0[0];
+  C.m[1] = C.m0[1];
+  C.m[2] = C.m0[2];
+  C.Eint = C.eg0 - KE0;
+  C.egas_new = C.eg0;
+  C.cs = C.chi0s;
+  C.nit = 0;
+  C.stat = RHD_STATUS_OK;
+  return true;
+}
+
+// 1/tau_E and -1/e_g = tau_E/(1 + tau_E) per group for opacity scale cs.
+template <int MAXG>
+__device__ __forceinline__ void set_tau(const KParams &P, const GroupTable &tab, Cell &C,
+                                        Arr64<MAXG> &A, double cs) {
+  const double tdt = P.c_hat * P.theta * P.dt;
+  C.cs = cs;
+  C.its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
+  for (int g = 0; g < P.G; ++g) {
+    const double it = C.its * tab.ikbar[g];  // 1/tau_E (0 marks an uncoupled group)
+    A.qe[g] = it > 0.0 ? 1.0 / (1.0 + it) : 0.0;
+  }
+}
+
+// FP64 outer loop (a3-a12) from the cell's current iterate (Eint, R, m, Fk);
+// at most max_outer passes.  Leaves egas_new, m, R, Fk for the store.
+template <int MAXG>
+__device__ __forceinline__ void fp64_outer(const KParams &P, const GroupTable &tab, Cell &C,
+                                           Arr64<MAXG> &A, int max_outer) {
+  const int G = P.G;
+  const int64_t i = C.i;
+  const double c = P.c, chat = P.c_hat, cr = c / chat;
+  const double tdt = chat * P.theta * P.dt;
+  const double inv_c2 = 1.0 / (c * c);
+  const double icc = 1.0 / (c * chat);
+  const double tol = P.tol, tol_out = P.tol_outer;
+  const bool tdep = P.temp_exp != 0.0;
+  const bool gtest = (P.flags & RHD_GROUP_TEST) != 0;
+  const double rho = C.rho;
+
+  for (int outer = 0; outer < max_outer; ++outer) {
+    // ---- a3: terms frozen for this outer pass
+    const double KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) / rho;
+    const double v[3] = {C.m[0] / rho, C.m[1] / rho, C.m[2] / rho};
+    for (int g = 0; g < G; ++g)
+      A.w[g] = (v[0] * A.Fk[3 * g] + v[1] * A.Fk[3 * g + 1] + v[2] * A.Fk[3 * g + 2]) * inv_c2;
+
+    // ---- inner Newton (a4-a8)
+    bool conv = false;
+    for (int it = 0; it <= P.max_newton; ++it) {
+      const double T = C.Eint * C.irc;
+      if (tdep) set_tau(P, tab, C, A, C.chi0s * pow(T / P.T_ref, P.temp_exp));
+      const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
+      const double invT = 1.0 / T;
+      double pqL, dL;
+      bool lowL;
+      edge_fp64(tab.xe[0] * invT, pqL, dL, lowL);
+      double sumR = 0.0, sFRe = 0.0, sde = 0.0, sabs = 0.0, grel = 0.0;
+      for (int g = 0; g < G; ++g) {
+        double pqU, dU;
+        bool lowU;
+        edge_fp64(tab.xe[g + 1] * invT, pqU, dU, lowU);
+        const int64_t o = (int64_t)g * P.gs + i;
+        const double dP = band_fp64(pqL, lowL, pqU, lowU);
+        const double dD = dU - dL;
+        const double b = aT4 * dP;
+        const double a = tab.alpha[g], rm = tab.rm[g], rp = tab.rp[g];
+        const double q = chiF_ratio<double>(b, aT4, dD, a, rm, rp, dL, dU);  // a5
+        A.bq[g] = b;
+        A.dnx[g] = aT4 * (rp * dU - rm * dL);  // (4pi/c) Delta_g(nu chi_0 B_nu) / chi_E
+        A.qF[g] = q;
+        // a6: F_R,g of eq. FGFR, E_g(T, R_g) from eq. Rnew solved for E_g
+        const double ie = A.qe[g];  // = -1/e_g
+        double fr, d;
+        if (ie > 0.0) {
+          const double Eg = b + (1.0 + a) * q * A.w[g] - A.R[g] * C.its * tab.ikbar[g];
+          const double s = P.src ? P.src[o] : 0.0;
+          const double e0 = P.erad[o];
+          fr = Eg - e0 - A.R[g] - s;
+          d = aT3 * (4.0 * dP - dD) * C.irc;  // a7: (1/C_v) d b_g / dT
+          if (gtest) grel = fmax(grel, fabs(fr) / (fabs(e0) + fabs(s) + fabs(Eg) + 1e-300));
+        } else {
+          fr = -A.R[g];  // uncoupled group: R_g = 0
+          d = 0.0;
+        }
+        const double iee = ie > 0.0 ? ie : 1.0;  // -1/e_g (e_g = -1 when uncoupled)
+        A.FR[g] = fr;
+        A.dg[g] = d;
+        sumR += A.R[g];
+        sFRe -= fr * iee;
+        sde -= d * iee;
+        sabs += fabs(fr);
+        pqL = pqU;
+        dL = dU;
+        lowL = lowU;
+      }
+      const double FG = C.Eint + KE - C.eg0 + cr * sumR;
+      // a8: convergence test
+      if (fabs(FG) < tol * C.Etot && cr * sabs < tol * C.Etot && grel < tol) {
+        conv = true;
+        // each R_g from its own row of eq. FGFR at the converged T (the
+        // arrowhead rows with dE = 0): groups far below E_tot, which the
+        // aggregate test cannot see, end consistent with T to round-off
+        for (int g = 0; g < G; ++g)
+          if (A.qe[g] > 0.0) A.R[g] += A.FR[g] * A.qe[g];
+        break;
+      }
+      if (it == P.max_newton) break;
+      // a7: arrowhead elimination of eq. matrix: dE from the reduced first row,
+      // then each dR_g from its own row
+      const double dE = (-FG + cr * sFRe) / (1.0 - cr * sde);
+      double lam = 1.0;
+      for (int k = 0; k < 40 && !(C.Eint + lam * dE > 0.0); ++k) lam *= 0.5;
+      C.Eint += lam * dE;
+      for (int g = 0; g < G; ++g) {
+        const double ie = A.qe[g] > 0.0 ? A.qe[g] : 1.0;
+        A.R[g] += lam * (A.FR[g] + A.dg[g] * dE) * ie;
+      }
+      ++C.nit;
+    }
+    if (!conv) C.stat = RHD_STATUS_MAXITER;
+
+    // ---- a9: conservative energy write-back
+    double sumR = 0.0;
+    for (int g = 0; g < G; ++g) sumR += A.R[g];
+    C.egas_new = C.eg0 - cr * sumR;
+
+    // ---- a10: flux update eq. numF1 (outdated velocity v_k)
+    double dF[3] = {0.0, 0.0, 0.0};
+    for (int g = 0; g < G; ++g) {
+      const int64_t o = (int64_t)g * P.gs + i;
+      const double s = P.src ? P.src[o] : 0.0;
+      const double Enew = P.erad[o] + A.R[g] + s;
+      const double chiB = C.cs * tab.kbar[g], a = tab.alpha[g];
+      double vp0, vp1, vp2;
+      closure_vP<double>(P.closure, c, Enew, A.Fk[3 * g], A.Fk[3 * g + 1], A.Fk[3 * g + 2], v[0],
+                         v[1], v[2], vp0, vp1, vp2);
+      const double srcg = chiB * (A.bq[g] - A.dnx[g] * (1.0 / 3.0));
+      const double kP = (1.0 + a) * chiB;
+      const double inv = 1.0 / (1.0 + tdt * chiB * A.qF[g]);
+      const double ft0 = P.frad[0][o], ft1 = P.frad[1][o], ft2 = P.frad[2][o];
+      const double n0 = (ft0 + tdt * (v[0] * srcg + kP * vp0)) * inv;
+      const double n1 = (ft1 + tdt * (v[1] * srcg + kP * vp1)) * inv;
+      const double n2 = (ft2 + tdt * (v[2] * srcg + kP * vp2)) * inv;
+      dF[0] += n0 - ft0;
+      dF[1] += n1 - ft1;
+      dF[2] += n2 - ft2;
+      A.Fk[3 * g] = n0;
+      A.Fk[3 * g + 1] = n1;
+      A.Fk[3 * g + 2] = n2;
+    }
+    // ---- a11: momentum update
+    const double mn[3] = {C.m0[0] - dF[0] * icc, C.m0[1] - dF[1] * icc, C.m0[2] - dF[2] * icc};
+    // ---- a12: outer test on the change of the v,F-terms of R_g, taken as
+    // their effect on R_g after the implicit energy solve (divided by
+    // 1 + c_hat theta dt chi_E), plus the change of the kinetic energy, which
+    // moves T = (E_gas - E_kin)/(rho c_v) and with it every term of R_g
+    const double vn[3] = {mn[0] / rho, mn[1] / rho, mn[2] / rho};
+    double chg = fabs(0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho - KE);
+    bool gok = true;
+    for (int g = 0; g < G; ++g) {
+      const double wn =
+          (vn[0] * A.Fk[3 * g] + vn[1] * A.Fk[3 * g + 1] + vn[2] * A.Fk[3 * g + 2]) * inv_c2;
+      const double tauE = tdt * C.cs * tab.kbar[g];
+      const double cg = fabs(tauE * (1.0 + tab.alpha[g]) * A.qF[g] * (wn - A.w[g])) / (1.0 + tauE);
+      chg += cg;
+      if (gtest) {
+        const int64_t o = (int64_t)g * P.gs + i;
+        const double s = P.src ? P.src[o] : 0.0;
+        gok = gok && cg <= tol_out * (fabs(P.erad[o]) + fabs(s) + fabs(P.erad[o] + A.R[g] + s));
+      }
+    }
+    C.m[0] = mn[0];
+    C.m[1] = mn[1];
+    C.m[2] = mn[2];
+    if (chg <= tol_out * C.Etot && gok) return;
+    if (outer == max_outer - 1) {
+      C.stat = RHD_STATUS_MAXITER;
+      return;
+    }
+    // warm start of the next inner solve from the written-back gas energy
+    C.Eint = C.egas_new - 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) / rho;
+    if (!(C.Eint > 0.0)) {
+      C.stat = RHD_STATUS_MAXITER;
+      return;
+    }
+  }
+}
+
+// Store the cell (a13).
+template <int MAXG>
+__device__ __forceinline__ void store_cell(const KParams &P, const Cell &C, const Arr64<MAXG> &A) {
+  const int64_t i = C.i;
+  for (int g = 0; g < P.G; ++g) {
+    const int64_t o = (int64_t)g * P.gs + i;
+    const double s = P.src ? P.src[o] : 0.0;
+    P.erad[o] = P.erad[o] + A.R[g] + s;
+    P.frad[0][o] = A.Fk[3 * g];
+    P.frad[1][o] = A.Fk[3 * g + 1];
+    P.frad[2][o] = A.Fk[3 * g + 2];
+  }
+  P.egas[i] = C.egas_new;
+  P.mom[0][i] = C.m[0];
+  P.mom[1][i] = C.m[1];
+  P.mom[2][i] = C.m[2];
+  if (P.status) P.status[i] = (uint8_t)C.stat;
+  if (P.iters) P.iters[i] = (uint8_t)(C.nit > 255 ? 255 : C.nit);
+}
+
+template <int MAXG>
+__global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__ KParams P) {
+  extern __shared__ double sm[];
+  const GroupTable tab = build_table(P, sm);
+  Arr64<MAXG> A;
+  Cell C;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
+    if (!load_cell(P, i, C, A)) continue;
+    set_tau(P, tab, C, A, C.chi0s);
+    fp64_outer(P, tab, C, A, P.max_outer);
+    store_cell(P, C, A);
+  }
+}
+
+}  // namespace rhd

@@ -1,0 +1,180 @@
+"""Python binding of the C ABI in ``include/rhd.h`` (argument marshalling only).
+
+Every step of the source-term update runs in the CUDA library; this module
+only turns torch tensors into the C structs and calls ``rhd_source_update``.
+There is no CPU path: if the library is missing, the call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import build as _build
+
+FP64, MIXED = 0, 1
+M1, EDDINGTON = 0, 1
+PPL_FIXED, PC = 0, 1
+STATUS_OK, STATUS_FALLBACK, STATUS_MAXITER, STATUS_INVALID = 0, 1, 2, 3
+GROUP_TEST = 1
+MAX_GROUPS = 256
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+
+
+class State(ctypes.Structure):
+    _fields_ = [("rho", _P), ("mom", _P * 3), ("egas", _P), ("kappa0", _P), ("erad", _P),
+                ("frad", _P * 3), ("src", _P), ("status", _P), ("iters", _P),
+                ("group_stride", ctypes.c_int64), ("c_v", _D), ("theta", _D), ("c", _D),
+                ("c_hat", _D), ("a_rad", _D), ("h", _D), ("k_B", _D), ("tol", _D),
+                ("tol_outer", _D), ("max_newton", ctypes.c_int32), ("max_outer", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("closure", ctypes.c_int32),
+                ("flags", ctypes.c_int32)]
+
+
+class Groups(ctypes.Structure):
+    _fields_ = [("n_groups", ctypes.c_int32), ("edges", ctypes.POINTER(_D))]
+
+
+class OpacityLaw(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("n_seg", ctypes.c_int32),
+                ("nu_break", ctypes.POINTER(_D)), ("seg_logk", ctypes.POINTER(_D)),
+                ("seg_beta", ctypes.POINTER(_D)), ("nu_ref", _D),
+                ("khat_gminus", ctypes.POINTER(_D)), ("alpha_g", ctypes.POINTER(_D)),
+                ("temp_exponent", _D), ("T_ref", _D)]
+
+
+class RhdError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rhd error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib() -> ctypes.CDLL:
+    """Load the in-tree CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"CUDA library not built: {path} is missing "
+                               "(run __graft_entry__.build() or python -m paper_2407_18304_gb300.build)")
+        _lib = ctypes.CDLL(path)
+        _lib.rhd_source_update.restype = ctypes.c_int
+        _lib.rhd_source_update.argtypes = [ctypes.POINTER(State), ctypes.POINTER(Groups),
+                                           ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _P]
+        _lib.rhd_strerror.restype = ctypes.c_char_p
+        _lib.rhd_strerror.argtypes = [ctypes.c_int]
+        _lib.rhd_version.restype = ctypes.c_int
+        _lib.rhd_version.argtypes = []
+    return _lib
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _dp(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(_D))
+
+
+def _check(t: torch.Tensor, name: str, shape, dtype=torch.float64):
+    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
+        raise ValueError(f"{name}: expected contiguous {dtype} {tuple(shape)}, got "
+                         f"{t.dtype} {tuple(t.shape)}")
+
+
+def make_law(law, mode: int = PPL_FIXED, khat_g=None, alpha_g=None, temp_exponent=0.0, T_ref=1.0):
+    """Pack an opacity law (nu_break, seg_logk, seg_beta, nu_ref) into the C struct.
+
+    Returns (struct, keep-alive list)."""
+    nb = np.ascontiguousarray(law.nu_break, dtype=np.float64)
+    lk = np.ascontiguousarray(law.seg_logk, dtype=np.float64)
+    be = np.ascontiguousarray(law.seg_beta, dtype=np.float64)
+    keep = [nb, lk, be]
+    s = OpacityLaw(mode, len(lk), _dp(nb) if len(nb) else None, _dp(lk), _dp(be),
+                   float(law.nu_ref), None, None, float(temp_exponent), float(T_ref))
+    if khat_g is not None:
+        kg = np.ascontiguousarray(khat_g, dtype=np.float64)
+        keep.append(kg)
+        s.khat_gminus = _dp(kg)
+        if alpha_g is not None:
+            ag = np.ascontiguousarray(alpha_g, dtype=np.float64)
+            keep.append(ag)
+            s.alpha_g = _dp(ag)
+    return s, keep
+
+
+def source_update(state: dict, edges, law, *, dt: float, c_v: float, consts: dict,
+                  theta: float = 1.0, precision: int = FP64, closure: int = M1,
+                  tol: float = 0.0, tol_outer: float = 0.0, max_newton: int = 0,
+                  max_outer: int = 0, status: torch.Tensor | None = None,
+                  iters: torch.Tensor | None = None, mode: int = PPL_FIXED, khat_g=None,
+                  alpha_g=None, temp_exponent: float = 0.0, T_ref: float = 1.0,
+                  stream: torch.cuda.Stream | None = None, n_cells: int | None = None,
+                  group_stride: int = 0, flags: int = 0) -> None:
+    """In-place implicit source-term update of one grid (see include/rhd.h).
+
+    ``state`` holds CUDA float64 tensors: rho [n], mom [3, n], egas [n],
+    kappa0 [n] or None, erad [G, n], frad [3, G, n], src [G, n] or None.
+    ``law`` has nu_break, seg_logk, seg_beta, nu_ref (piecewise powerlaw)."""
+    rho = state["rho"]
+    n = rho.shape[0] if n_cells is None else n_cells
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    G = len(e) - 1
+    gs = group_stride or rho.shape[0]
+    _check(rho, "rho", (rho.shape[0],))
+    _check(state["mom"], "mom", (3, rho.shape[0]))
+    _check(state["egas"], "egas", (rho.shape[0],))
+    _check(state["erad"], "erad", (G, gs))
+    _check(state["frad"], "frad", (3, G, gs))
+    if state.get("kappa0") is not None:
+        _check(state["kappa0"], "kappa0", (rho.shape[0],))
+    if state.get("src") is not None:
+        _check(state["src"], "src", (G, gs))
+    if status is not None:
+        _check(status, "status", (rho.shape[0],), torch.uint8)
+    if iters is not None:
+        _check(iters, "iters", (rho.shape[0],), torch.uint8)
+    mom, frad = state["mom"], state["frad"]
+    st = State()
+    st.rho = _ptr(rho)
+    for d in range(3):
+        st.mom[d] = _ptr(mom[d])
+        st.frad[d] = _ptr(frad[d])
+    st.egas = _ptr(state["egas"])
+    st.kappa0 = _ptr(state.get("kappa0"))
+    st.erad = _ptr(state["erad"])
+    st.src = _ptr(state.get("src"))
+    st.status = _ptr(status)
+    st.iters = _ptr(iters)
+    st.group_stride = gs
+    st.c_v, st.theta = float(c_v), float(theta)
+    st.c, st.c_hat, st.a_rad = float(consts["c"]), float(consts.get("c_hat", consts["c"])), float(consts["a_rad"])
+    st.h, st.k_B = float(consts["h"]), float(consts["k_B"])
+    st.tol, st.tol_outer = float(tol), float(tol_outer)
+    st.max_newton, st.max_outer = int(max_newton), int(max_outer)
+    st.precision, st.closure, st.flags = int(precision), int(closure), int(flags)
+    gr = Groups(G, _dp(e))
+    lw, keep = make_law(law, mode, khat_g, alpha_g, temp_exponent, T_ref)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().rhd_source_update(ctypes.byref(st), ctypes.byref(gr), ctypes.byref(lw), float(dt),
+                                 int(n), ctypes.c_void_p(s.cuda_stream))
+    del keep
+    if rc != 0:
+        raise RhdError(rc, lib().rhd_strerror(rc).decode())
+
+
+def strerror(code: int) -> str:
+    return lib().rhd_strerror(int(code)).decode()

@@ -1,0 +1,94 @@
+"""Shared helpers of the parity tests: run the CUDA library and the oracle on
+the same seeded state and measure the per-output differences."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle as O
+from paper_2407_18304_gb300 import rhd, synth
+
+
+def oracle_groups(w, mode=O.PPL_FIXED, khat_g=None, alpha_g=None):
+    if khat_g is not None:
+        al = np.zeros(len(khat_g)) if alpha_g is None else np.asarray(alpha_g, float)
+        return O.Groups(w.edges, np.asarray(khat_g, float), al)
+    km, al = O.group_table(w.edges, mode, w.law.nu_break, w.law.seg_logk, w.law.seg_beta,
+                           w.law.nu_ref)
+    return O.Groups(w.edges, km, al)
+
+
+def run_oracle(w, *, theta=1.0, closure=rhd.M1, c_hat=None, mode=O.PPL_FIXED, khat_g=None,
+               alpha_g=None, temp_exponent=0.0, T_ref=1.0, state=None, n_threads=0):
+    st = synth.to_numpy(w.state if state is None else state)
+    p = O.Params(c=w.consts["c"], c_hat=c_hat if c_hat is not None else w.consts["c_hat"],
+                 a_rad=w.consts["a_rad"], h=w.consts["h"], k_B=w.consts["k_B"], c_v=w.c_v,
+                 theta=theta, dt=w.dt, max_iter=200, closure=closure,
+                 temp_exponent=temp_exponent, T_ref=T_ref)
+    return O.source_update(st, p, oracle_groups(w, mode, khat_g, alpha_g), n_threads=n_threads)
+
+
+def run_gpu(w, *, precision=rhd.FP64, theta=1.0, closure=rhd.M1, c_hat=None, mode=rhd.PPL_FIXED,
+            khat_g=None, alpha_g=None, temp_exponent=0.0, T_ref=1.0, tol=0.0, tol_outer=0.0,
+            state=None, device="cuda", flags=0):
+    src = w.state if state is None else state
+    st = {k: (None if v is None else v.to(device).clone()) for k, v in src.items()}
+    n = st["rho"].shape[0]
+    status = torch.full((n,), 255, dtype=torch.uint8, device=device)
+    iters = torch.zeros(n, dtype=torch.uint8, device=device)
+    consts = dict(w.consts)
+    if c_hat is not None:
+        consts["c_hat"] = c_hat
+    rhd.source_update(st, w.edges, w.law, dt=w.dt, c_v=w.c_v, consts=consts, theta=theta,
+                      precision=precision, closure=closure, status=status, iters=iters, mode=mode,
+                      khat_g=khat_g, alpha_g=alpha_g, temp_exponent=temp_exponent, T_ref=T_ref,
+                      tol=tol, tol_outer=tol_outer, flags=flags)
+    torch.cuda.synchronize()
+    out = synth.to_numpy(st)
+    out["status"] = status.cpu().numpy().astype(np.int32)
+    out["iters"] = iters.cpu().numpy().astype(np.int32)
+    return out
+
+
+def gas_T(st, rho, c_v):
+    ke = 0.5 * (st["mom"] ** 2).sum(0) / rho
+    return (st["egas"] - ke) / (rho * c_v)
+
+
+def errors(a: dict, b: dict, st0: dict, c: float, c_v: float) -> dict:
+    """Per-output differences of result ``a`` against reference ``b``.
+
+    E_gas: relative to the reference value.  T = (E_gas - E_kin)/(rho c_v) is
+    derived by a cancellation that magnifies any error in E_gas by
+    E_tot/E_int, so its error is taken relative to T max(1, E_tot/E_int)
+    ("T"; the plain relative error is "T_plain").  E_g: relative to the
+    reference E_g.  F_g: relative to c E_g + |F_g| (|F| <= c E is the scale of
+    a group's flux).  rho v: relative to |rho v| + sum_g E_g / c (the gas plus
+    radiation momentum scale of the cell).  Returns the maximum over cells and
+    groups of each."""
+    rho = st0["rho"]
+    Ta, Tb = gas_T(a, rho, c_v), gas_T(b, rho, c_v)
+    src = 0.0 if st0.get("src") is None else st0["src"].sum(0)
+    etot = st0["egas"] + st0["erad"].sum(0) + src
+    cond = np.maximum(1.0, etot / (Tb * rho * c_v))
+    out = {"T": np.max(np.abs(Ta - Tb) / Tb / cond), "T_plain": np.max(np.abs(Ta - Tb) / Tb),
+           "egas": np.max(np.abs(a["egas"] - b["egas"]) / np.abs(b["egas"])),
+           "erad": np.max(np.abs(a["erad"] - b["erad"]) / np.abs(b["erad"]))}
+    fs = c * np.abs(b["erad"]) + np.linalg.norm(b["frad"], axis=0)
+    out["frad"] = np.max(np.abs(a["frad"] - b["frad"]) / fs[None])
+    ms = np.linalg.norm(b["mom"], axis=0) + b["erad"].sum(0) / c
+    out["mom"] = np.max(np.abs(a["mom"] - b["mom"]) / ms[None])
+    return out
+
+
+def conservation(a: dict, st0: dict, c: float, c_hat: float) -> tuple[float, float]:
+    """Relative change of total energy and momentum (should be round-off)."""
+    r = c / c_hat
+    src = 0.0 if st0.get("src") is None else st0["src"].sum(0)
+    e0 = st0["egas"] + r * (st0["erad"].sum(0) + src)
+    e1 = a["egas"] + r * a["erad"].sum(0)
+    scale = np.abs(st0["egas"]) + r * (np.abs(st0["erad"]).sum(0) + np.abs(a["erad"]).sum(0))
+    m0 = st0["mom"] + st0["frad"].sum(1) / (c * c_hat)
+    m1 = a["mom"] + a["frad"].sum(1) / (c * c_hat)
+    ms = np.abs(st0["mom"]) + (np.abs(st0["frad"]).sum(1) + np.abs(a["frad"]).sum(1)) / (c * c_hat)
+    return float(np.max(np.abs(e1 - e0) / scale)), float(np.max(np.abs(m1 - m0) / ms))

@@ -1,0 +1,69 @@
+"""The C ABI without a GPU: the library loads, exports every function that
+include/rhd.h declares, and rejects bad arguments before touching a device."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2407_18304_gb300 import build, rhd, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(rhd_[a-z0-9_]+)\s*\(", txt))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build_lib()
+    return rhd.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert "rhd_source_update" in names
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def _call(lib, edges, law=None, n_cells=0, **fields):
+    w = synth.preset("tiny", n_cells=1)
+    st = rhd.State()
+    st.c_v, st.theta = w.c_v, 1.0
+    st.c, st.c_hat, st.a_rad, st.h, st.k_B = (w.consts[k] for k in ("c", "c_hat", "a_rad", "h", "k_B"))
+    for k, v in fields.items():
+        setattr(st, k, v)
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    gr = rhd.Groups(len(e) - 1, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    lw, keep = rhd.make_law(law if law is not None else w.law)
+    return lib.rhd_source_update(ctypes.byref(st), ctypes.byref(gr), ctypes.byref(lw), w.dt,
+                                 n_cells, None)
+
+
+def test_argument_checks_without_a_device(lib):
+    edges = synth.log_edges(4)
+    assert _call(lib, edges) == 0  # zero cells: validated, nothing launched
+    bad = edges.copy()
+    bad[2] = bad[1]
+    assert _call(lib, bad) == -2
+    assert _call(lib, np.concatenate([[0.0], edges[1:]])) == -2  # PPL needs nu > 0
+    assert _call(lib, synth.log_edges(300)) == -6
+    assert _call(lib, edges, c_v=-1.0) == -1
+    assert _call(lib, edges, precision=7) == -1
+    assert _call(lib, edges, flags=8) == -1
+    law = synth.OpacityLaw(np.array([2.0, 1.0]), np.zeros(3), np.zeros(3), synth.NU0)
+    assert _call(lib, edges, law=law) == -3  # breakpoints must increase
+    # pointers missing with cells to do
+    assert _call(lib, edges, n_cells=5) == -1
+    assert rhd.strerror(-2) == "invalid group edges"
+    assert lib.rhd_version() >= 100
