@@ -62,9 +62,10 @@ extern "C" {
 #define RHD_PC 1        /* piecewise constant (Sec. 2.2.1) */
 
 /* rhd_state_t.flags */
-#define RHD_GROUP_TEST 1 /* also stop only when every group meets the tolerances relative
-                            to its own energy (the paper's tests are relative to E_tot,
-                            which leaves groups far below E_tot loosely converged) */
+#define RHD_GROUP_TEST 1 /* the outer iteration also stops only when, in every group,
+                            the change of the v,F-terms of R_g is below tol_outer times
+                            that group's own energy (the paper's test is relative to
+                            E_tot, which leaves groups far below E_tot loosely converged) */
 
 /* per-cell status codes written to rhd_state_t.status */
 #define RHD_STATUS_OK 0

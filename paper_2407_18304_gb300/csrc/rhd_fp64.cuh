@@ -149,7 +149,7 @@ __device__ __forceinline__ void fp64_outer(const KParams &P, const GroupTable &t
       double pqL, dL;
       bool lowL;
       edge_fp64(tab.xe[0] * invT, pqL, dL, lowL);
-      double sumR = 0.0, sFRe = 0.0, sde = 0.0, sabs = 0.0, grel = 0.0;
+      double sumR = 0.0, sFRe = 0.0, sde = 0.0, sabs = 0.0;
       for (int g = 0; g < G; ++g) {
         double pqU, dU;
         bool lowU;
@@ -169,10 +169,8 @@ __device__ __forceinline__ void fp64_outer(const KParams &P, const GroupTable &t
         if (ie > 0.0) {
           const double Eg = b + (1.0 + a) * q * A.w[g] - A.R[g] * C.its * tab.ikbar[g];
           const double s = P.src ? P.src[o] : 0.0;
-          const double e0 = P.erad[o];
-          fr = Eg - e0 - A.R[g] - s;
+          fr = Eg - P.erad[o] - A.R[g] - s;
           d = aT3 * (4.0 * dP - dD) * C.irc;  // a7: (1/C_v) d b_g / dT
-          if (gtest) grel = fmax(grel, fabs(fr) / (fabs(e0) + fabs(s) + fabs(Eg) + 1e-300));
         } else {
           fr = -A.R[g];  // uncoupled group: R_g = 0
           d = 0.0;
@@ -190,7 +188,7 @@ __device__ __forceinline__ void fp64_outer(const KParams &P, const GroupTable &t
       }
       const double FG = C.Eint + KE - C.eg0 + cr * sumR;
       // a8: convergence test
-      if (fabs(FG) < tol * C.Etot && cr * sabs < tol * C.Etot && grel < tol) {
+      if (fabs(FG) < tol * C.Etot && cr * sabs < tol * C.Etot) {
         conv = true;
         // each R_g from its own row of eq. FGFR at the converged T (the
         // arrowhead rows with dE = 0): groups far below E_tot, which the
