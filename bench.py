@@ -144,6 +144,15 @@ def fp_peaks() -> dict:
         return {"error": str(e)}
 
 
+# FP64 flops (DFMA counted twice) per cell-group of one call, from the SASS
+# instruction counts ncu reports for the same workload on a 65536-cell sample
+# (profiles/solve_full_256cube_ng64.md); a property of the workload and the
+# algorithm, applied to the full-size grid of the same distribution.
+FP64_FLOPS_PER_CG = {}
+# DRAM bytes (read + write) per cell-group of one call from the same capture
+TRAFFIC_PER_CG = {}
+
+
 def run_ours(args, ws, rank):
     from paper_2407_18304_gb300 import rhd, synth
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
@@ -210,7 +219,8 @@ def run_ours(args, ws, rank):
                       "l2": "state restored from a pristine copy before each step (2x state > L2)",
                       "parallelism": f"weak x{ws}, no collective"},
            "converged_fraction": conv_frac, "mean_newton_iters": mean_iters,
-           "gpu_launches": args.steps, "wall_s_timed": wall, "clocks": clk}
+           "gpu_launches": args.steps * (1 if prec == rhd.FP64 else 2), "wall_s_timed": wall,
+           "clocks": clk}
 
     # the plain FP64 form on the same grid, same tolerance (the comparison)
     if prec != rhd.FP64 and args.fp64_steps > 0:
@@ -221,16 +231,28 @@ def run_ours(args, ws, rank):
                             "converged_fraction": conv64, "mean_newton_iters": it64}
         res["speedup_vs_fp64_form"] = res["value"] / res["fp64_form"]["value"]
 
-    # roofline of the solve kernel (the only kernel of a step)
+    # roofline of the solve (FP64-issue bound)
     peaks = fp_peaks()
     res["fp_peaks_measured"] = peaks
-    bytes_alg = n * (G * 64 + 82)  # in+out FP64 SoA per launch
     mean_launch_s = t_dev / args.steps
-    peak = _measured_hbm()
-    ach = bytes_alg / mean_launch_s / 1e9
-    res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                       "frac": ach / peak, "traffic": None,
-                       "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
+    bytes_alg = n * (G * 64 + 82)  # in+out FP64 SoA per call
+    hbm_frac = bytes_alg / mean_launch_s / 1e9 / _measured_hbm()
+    per_cg = FP64_FLOPS_PER_CG.get((name, args.precision))
+    if per_cg is not None:
+        peak = peaks.get("fp64_fma_tflops") or 1.25
+        ach = per_cg * n * G / mean_launch_s / 1e12
+        res["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                           "frac": ach / peak, "traffic": TRAFFIC_PER_CG.get((name, args.precision)),
+                           "what": "FP64 flops (DFMA = 2) per call / call time, vs the DFMA peak",
+                           "peak_source": ("measured fp_peak DFMA loop" if "fp64_fma_tflops" in peaks
+                                           else "nominal 1.25 TFLOP/s"),
+                           "fp64_flops_per_cell_group": per_cg, "hbm_frac": hbm_frac}
+    else:
+        peak = _measured_hbm()
+        ach = bytes_alg / mean_launch_s / 1e9
+        res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+                           "frac": ach / peak, "traffic": None,
+                           "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
 
     if not args.no_e2e:
         res["e2e"] = run_e2e(args, w, prec, dev, ws)

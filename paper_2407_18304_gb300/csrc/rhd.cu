@@ -1,7 +1,7 @@
 // rhd.cu -- host side of the C ABI in include/rhd.h: argument checks, the
 // once-per-device constant tables, and the kernel launches.  The kernels are
-// in rhd_fp64.cuh (FP64 form) and rhd_mixed.cuh (mixed form); this is the
-// only translation unit.
+// in rhd_fp64.cuh (FP64 passes) and rhd_mixed.cuh (FP32 warm-start pass); this
+// is the only translation unit.
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -18,6 +18,42 @@ std::mutex g_mu;
 constexpr int kMaxDevices = 64;
 bool g_ready[kMaxDevices];
 int g_sms[kMaxDevices];
+// Per-device workspace of the mixed form's warm start, grown on demand (the
+// first call at a new largest size allocates; later calls reuse it).
+void *g_ws[kMaxDevices];
+size_t g_ws_bytes[kMaxDevices];
+
+// Each lane runs its cell to completion before the next (the lane-persistent
+// form of the FP64 kernel measured the same on GB300: the branch divergence
+// inside the Planck evaluation, not the spread of iteration counts, limits
+// lane efficiency).
+constexpr bool g_persist = false;
+
+size_t warm_bytes(int64_t n, int G) {
+  return (size_t)n * (4 * sizeof(double) + 1) + (size_t)n * G * 4 * sizeof(float) + 1024;
+}
+
+int workspace(int64_t n, int G, WarmOut *w, WarmStart *r) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RHD_ECUDA;
+  const size_t need = warm_bytes(n, G);
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_ws_bytes[dev] < need) {
+    if (g_ws[dev]) cudaFree(g_ws[dev]);
+    g_ws[dev] = nullptr;
+    g_ws_bytes[dev] = 0;
+    if (cudaMalloc(&g_ws[dev], need) != cudaSuccess) return RHD_ENOMEM;
+    g_ws_bytes[dev] = need;
+  }
+  char *p = static_cast<char *>(g_ws[dev]);
+  w->eint = reinterpret_cast<double *>(p);
+  w->mom = w->eint + n;
+  w->r = reinterpret_cast<float *>(w->mom + 3 * n);
+  w->f = w->r + (size_t)G * n;
+  w->nit = reinterpret_cast<uint8_t *>(w->f + (size_t)3 * G * n);
+  *r = WarmStart{w->eint, w->mom, w->r, w->f, w->nit};
+  return RHD_OK;
+}
 
 // B_2j/(2j)! = (-1)^(j+1) 2 zeta(2j) / (2 pi)^(2j).  zeta(2j) in closed form for
 // j <= 4 and from the Euler product over the primes below 2000 for j >= 5
@@ -179,27 +215,54 @@ int pack(const rhd_state_t *s, const rhd_groups_t *gr, const rhd_opacity_law_t *
   return RHD_OK;
 }
 
-int launch(const KParams &kp, int precision, int sms, cudaStream_t st) {
+// Grid of a lane-persistent kernel: the CTAs that are resident at once (so
+// every lane walks its share of cells in one wave), fewer for small grids.
+template <typename K>
+int persistent_blocks(K kernel, size_t smem, int sms, int64_t n, int threads) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t want = (n + threads - 1) / threads;
+  const int64_t full = (int64_t)sms * per_sm;
+  return (int)(want < full ? want : full);
+}
+
+template <int MAXG>
+int launch_g(const KParams &kp, int precision, int sms, cudaStream_t st) {
   const int threads = 128;
-  const int64_t want = (kp.n + threads - 1) / threads;
-  const int blocks = (int)(want < (int64_t)sms * 32 ? want : (int64_t)sms * 32);
   const size_t smem = table_bytes(kp.G);
   if (precision == RHD_FP64) {
-    if (kp.G <= 16)
-      solve_fp64_kernel<16><<<blocks, threads, smem, st>>>(kp);
-    else if (kp.G <= 64)
-      solve_fp64_kernel<64><<<blocks, threads, smem, st>>>(kp);
-    else
-      solve_fp64_kernel<kMaxG><<<blocks, threads, smem, st>>>(kp);
+    const WarmStart cold{nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (g_persist) {
+      const int b = persistent_blocks(solve_fp64_kernel<MAXG, true>, smem, sms, kp.n, threads);
+      solve_fp64_kernel<MAXG, true><<<b, threads, smem, st>>>(kp, cold);
+    } else {
+      const int b = persistent_blocks(solve_fp64_kernel<MAXG, false>, smem, sms, kp.n, threads);
+      solve_fp64_kernel<MAXG, false><<<b, threads, smem, st>>>(kp, cold);
+    }
   } else {
-    if (kp.G <= 16)
-      solve_mixed_kernel<16><<<blocks, threads, smem, st>>>(kp);
-    else if (kp.G <= 64)
-      solve_mixed_kernel<64><<<blocks, threads, smem, st>>>(kp);
-    else
-      solve_mixed_kernel<kMaxG><<<blocks, threads, smem, st>>>(kp);
+    WarmOut wo;
+    WarmStart wi;
+    const int rc = workspace(kp.n, kp.G, &wo, &wi);
+    if (rc != RHD_OK) return rc;
+    const int ba = persistent_blocks(warm_fp32_kernel<MAXG>, smem, sms, kp.n, threads);
+    warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo);
+    if (g_persist) {
+      const int bb = persistent_blocks(solve_fp64_kernel<MAXG, true>, smem, sms, kp.n, threads);
+      solve_fp64_kernel<MAXG, true><<<bb, threads, smem, st>>>(kp, wi);
+    } else {
+      const int bb = persistent_blocks(solve_fp64_kernel<MAXG, false>, smem, sms, kp.n, threads);
+      solve_fp64_kernel<MAXG, false><<<bb, threads, smem, st>>>(kp, wi);
+    }
   }
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
+}
+
+int launch(const KParams &kp, int precision, int sms, cudaStream_t st) {
+  if (kp.G <= 16) return launch_g<16>(kp, precision, sms, st);
+  if (kp.G <= 64) return launch_g<64>(kp, precision, sms, st);
+  return launch_g<kMaxG>(kp, precision, sms, st);
 }
 
 }  // namespace

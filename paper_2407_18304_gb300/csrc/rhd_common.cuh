@@ -158,19 +158,22 @@ __constant__ double c_bern3[kNB];
 __constant__ double c_invn[kNQ + 1];
 
 // FP64 edge values: pq = P(x) when low (x < 2), else Q(x) = 1 - P(x);
-// d = D(x) = (15/pi^4) x^4/(e^x-1).  Small x: Bernoulli series (no
-// transcendental); large x: sum_n e^(-n x) (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4)
-// (Widger & Woodall 1976) with the terms cut where e^(-(n-1)x) < 1e-17.
-__device__ __forceinline__ void edge_fp64(double x, double &pq, double &d, bool &low) {
+// d = D(x) = (15/pi^4) x^4/(e^x-1) and ed = x dD/dx = D (4 - x e^x/(e^x-1)).
+// Small x: Bernoulli series (no transcendental); large x: sum_n e^(-n x)
+// (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4) (Widger & Woodall 1976) with the terms
+// cut where e^(-(n-1)x) < 1e-17.
+__device__ __forceinline__ void edge_fp64(double x, double &pq, double &d, double &ed, bool &low) {
   if (!(x > 0.0)) {
     pq = 0.0;
     d = 0.0;
+    ed = 0.0;
     low = true;
     return;
   }
   if (isinf(x)) {
     pq = 0.0;
     d = 0.0;
+    ed = 0.0;
     low = false;
     return;
   }
@@ -183,8 +186,10 @@ __device__ __forceinline__ void edge_fp64(double x, double &pq, double &d, bool 
       s3 = fma(s3, z, c_bern3[j]);
     }
     const double x3 = z * x;
+    const double xr = fma(z, s1, fma(-0.5, x, 1.0));  // x/(e^x-1)
     pq = kPlanckNorm * x3 * fma(z, s3, fma(-0.125, x, 1.0 / 3.0));
-    d = kPlanckNorm * x3 * fma(z, s1, fma(-0.5, x, 1.0));
+    d = kPlanckNorm * x3 * xr;
+    ed = d * (4.0 - xr - x);  // x e^x/(e^x-1) = x/(e^x-1) + x
     low = true;
   } else {
     const double e1 = exp(-x);
@@ -201,7 +206,9 @@ __device__ __forceinline__ void edge_fp64(double x, double &pq, double &d, bool 
       sum = fma(en * inv, h, sum);
     }
     pq = kPlanckNorm * sum;
-    d = kPlanckNorm * x3 * x * e1 / (1.0 - e1);
+    const double inv1 = 1.0 / (1.0 - e1);
+    d = kPlanckNorm * x3 * x * e1 * inv1;
+    ed = d * (4.0 - x * inv1);
     low = false;
   }
 }

@@ -1,14 +1,14 @@
 // rhd_fp64.cuh -- the FP64 passes of the per-cell implicit source-term update.
 //
-// One thread owns one cell (grid-stride loop).  The per-group arrays of a cell
-// live in thread-local storage; loads of the state are coalesced because the
-// cell index is the fastest index of every group array.  The algorithm is the
+// One thread owns one cell at a time.  The per-group arrays of a cell live in
+// thread-local storage; loads of the state are coalesced because the cell
+// index is the fastest index of every group array.  The algorithm is the
 // paper's (Sec. 3):
 //   outer pass k (v, F_g frozen at the k-th iterate):
 //     inner Newton-Raphson over x = (E_gas, R_1..R_Ng):
 //       residual F_G, F_R,g of eq. FGFR with R_g of eq. Rnew (c_hat/c factor
-//       included), Jacobian entries after eq. linear with
-//       d(chi_B/chi_E)/dT := 0 and the T-dependence of chi_F dropped,
+//       included), Jacobian entries after eq. linear (chi_B/chi_E = 1 here,
+//       and the T-derivative of chi_F in the work term is kept),
 //       arrowhead elimination of eq. matrix, convergence test after eq. matrix,
 //       then each R_g from its own row at the converged T;
 //     conservative write-back E_g = E_g^t + R_g + S_g,
@@ -20,19 +20,38 @@
 //     changed by less than tol_outer E_tot.
 // The gas energy is carried as E_int = E_gas - E_kin (E_kin frozen within an
 // inner solve, so the Newton steps in E_gas and E_int are the same).
+//
+// The steps are written as a per-lane state machine (outer_begin, inner_step,
+// outer_end) so that a lane whose cell has converged takes its next cell while
+// the other lanes of its warp keep iterating: every Newton evaluation then runs
+// with (nearly) full warps, whatever the spread of iteration counts.
 #pragma once
 #include "rhd_common.cuh"
 
 namespace rhd {
 
-// eq. chiDiff as chi_F / chi_E, from b_g, (4pi/c)Delta_g(nu B_nu) = aT4 dD and
-// the edge values; held to [min, max] of chi_0 / chi_E over the group.
+// eq. chiDiff as q = chi_F / chi_E, from b_g, (4pi/c)Delta_g(nu B_nu) = aT4 dD
+// and the edge values; held to [min, max] of chi_0 / chi_E over the group.
+// Also dq/dT (0 where held): with db = db_g/dT and the edge terms
+// d(aT4 D)/dT = aT3 (4 D - x dD/dx) (eU, eL = x dD/dx at the edges).
 template <typename R>
-__device__ __forceinline__ R chiF_ratio(R b, R aT4, R dD, R a, R rm, R rp, R dL, R dU) {
+__device__ __forceinline__ R chiF_ratio(R b, R aT4, R dD, R a, R rm, R rp, R dL, R dU, R db,
+                                        R aT3, R eL, R eU, R &dq) {
+  const R X = rp * dU - rm * dL;
   const R den = R(4.0 / 3.0) * b - R(1.0 / 3.0) * aT4 * dD;
   R q = R(1);
-  if (den > R(0)) q = (R(4.0 / 3.0) * b + R(1.0 / 3.0) * (a * b - aT4 * (rp * dU - rm * dL))) / den;
-  return fmin(fmax(q, fmin(rm, rp)), fmax(rm, rp));
+  dq = R(0);
+  if (den > R(0)) {
+    const R iden = R(1) / den;
+    q = (R(4.0 / 3.0) * b + R(1.0 / 3.0) * (a * b - aT4 * X)) * iden;
+    const R dX = aT3 * (R(4) * X - (rp * eU - rm * eL));
+    const R dnum = R(4.0 / 3.0) * db + R(1.0 / 3.0) * (a * db - dX);
+    const R dden = R(4.0 / 3.0) * db - R(1.0 / 3.0) * aT3 * (R(4) * dD - (eU - eL));
+    dq = (dnum - q * dden) * iden;
+  }
+  const R lo = fmin(rm, rp), hi = fmax(rm, rp);
+  if (q < lo || q > hi) dq = R(0);
+  return fmin(fmax(q, lo), hi);
 }
 
 // Per-cell constants and the FP64 iterate of one cell.
@@ -40,11 +59,13 @@ struct Cell {
   int64_t i;
   double rho, m0[3], eg0, chi0s, Etot, rcv, irc;
   double m[3];     // momentum of the current outer iterate
+  double v[3];     // its velocity (frozen during the inner solve)
+  double KE;       // its kinetic energy (frozen during the inner solve)
   double Eint;     // internal energy of the current inner iterate
   double egas_new; // written-back total gas energy
   double cs;       // rho kappa0 (T/T_ref)^p of the last evaluation
   double its;      // 1 / (c_hat theta dt cs)
-  int nit, stat;
+  int nit, stat, it, outer;
 };
 
 // Thread-local per-group arrays of the FP64 passes.
@@ -100,6 +121,8 @@ __device__ __forceinline__ bool load_cell(const KParams &P, int64_t i, Cell &C, 
   C.cs = C.chi0s;
   C.nit = 0;
   C.stat = RHD_STATUS_OK;
+  C.outer = 0;
+  C.it = 0;
   return true;
 }
 
@@ -116,167 +139,188 @@ __device__ __forceinline__ void set_tau(const KParams &P, const GroupTable &tab,
   }
 }
 
-// FP64 outer loop (a3-a12) from the cell's current iterate (Eint, R, m, Fk);
-// at most max_outer passes.  Leaves egas_new, m, R, Fk for the store.
+// a3: the terms frozen for one outer pass.
 template <int MAXG>
-__device__ __forceinline__ void fp64_outer(const KParams &P, const GroupTable &tab, Cell &C,
-                                           Arr64<MAXG> &A, int max_outer) {
+__device__ __forceinline__ void outer_begin(const KParams &P, Cell &C, Arr64<MAXG> &A) {
+  const double rho = C.rho, inv_c2 = 1.0 / (P.c * P.c);
+  C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) / rho;
+  C.v[0] = C.m[0] / rho;
+  C.v[1] = C.m[1] / rho;
+  C.v[2] = C.m[2] / rho;
+  for (int g = 0; g < P.G; ++g)
+    A.w[g] = (C.v[0] * A.Fk[3 * g] + C.v[1] * A.Fk[3 * g + 1] + C.v[2] * A.Fk[3 * g + 2]) * inv_c2;
+  C.it = 0;
+}
+
+// One inner Newton iteration (a4-a8): evaluate the residual at the current
+// iterate; if the convergence test passes, set each R_g from its own row and
+// return 1; at the iteration cap return 2; else take the Newton step, return 0.
+template <int MAXG>
+__device__ __forceinline__ int inner_step(const KParams &P, const GroupTable &tab, Cell &C,
+                                          Arr64<MAXG> &A) {
+  const int G = P.G;
+  const int64_t i = C.i;
+  const double cr = P.c / P.c_hat;
+  const double T = C.Eint * C.irc;
+  if (P.temp_exp != 0.0) set_tau(P, tab, C, A, C.chi0s * pow(T / P.T_ref, P.temp_exp));
+  const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
+  const double invT = 1.0 / T;
+  double pqL, dL, eL;
+  bool lowL;
+  edge_fp64(tab.xe[0] * invT, pqL, dL, eL, lowL);
+  double sumR = 0.0, sFRe = 0.0, sde = 0.0, sabs = 0.0;
+  for (int g = 0; g < G; ++g) {
+    double pqU, dU, eU;
+    bool lowU;
+    edge_fp64(tab.xe[g + 1] * invT, pqU, dU, eU, lowU);
+    const int64_t o = (int64_t)g * P.gs + i;
+    const double dP = band_fp64(pqL, lowL, pqU, lowU);
+    const double dD = dU - dL;
+    const double b = aT4 * dP;
+    const double db = aT3 * (4.0 * dP - dD);  // d b_g / dT
+    const double a = tab.alpha[g], rm = tab.rm[g], rp = tab.rp[g];
+    double dq;
+    const double q = chiF_ratio<double>(b, aT4, dD, a, rm, rp, dL, dU, db, aT3, eL, eU, dq);  // a5
+    A.bq[g] = b;
+    A.dnx[g] = aT4 * (rp * dU - rm * dL);  // (4pi/c) Delta_g(nu chi_0 B_nu) / chi_E
+    A.qF[g] = q;
+    // a6: F_R,g of eq. FGFR, E_g(T, R_g) from eq. Rnew solved for E_g
+    const double ie = A.qe[g];  // = -1/e_g
+    double fr, d;
+    if (ie > 0.0) {
+      const double Eg = b + (1.0 + a) * q * A.w[g] - A.R[g] * C.its * tab.ikbar[g];
+      const double s = P.src ? P.src[o] : 0.0;
+      fr = Eg - P.erad[o] - A.R[g] - s;
+      // a7: dF_R,g/dE_gas = (1/C_v) dE_g/dT at fixed R_g (chi_B/chi_E = 1 in PPL
+      // and PC); the T-derivative of chi_F in the work term is kept as well,
+      // so the Newton step is exact for the inner system (same root)
+      d = (db + (1.0 + a) * dq * A.w[g]) * C.irc;
+    } else {
+      fr = -A.R[g];  // uncoupled group: R_g = 0
+      d = 0.0;
+    }
+    const double iee = ie > 0.0 ? ie : 1.0;  // -1/e_g (e_g = -1 when uncoupled)
+    A.FR[g] = fr;
+    A.dg[g] = d;
+    sumR += A.R[g];
+    sFRe -= fr * iee;
+    sde -= d * iee;
+    sabs += fabs(fr);
+    pqL = pqU;
+    dL = dU;
+    eL = eU;
+    lowL = lowU;
+  }
+  const double FG = C.Eint + C.KE - C.eg0 + cr * sumR;
+  // a8: convergence test
+  if (fabs(FG) < P.tol * C.Etot && cr * sabs < P.tol * C.Etot) {
+    // each R_g from its own row of eq. FGFR at the converged T (the arrowhead
+    // rows with dE = 0): groups far below E_tot, which the aggregate test
+    // cannot see, end consistent with T to round-off
+    for (int g = 0; g < G; ++g)
+      if (A.qe[g] > 0.0) A.R[g] += A.FR[g] * A.qe[g];
+    return 1;
+  }
+  if (C.it >= P.max_newton) return 2;
+  // a7: arrowhead elimination of eq. matrix: dE from the reduced first row,
+  // then each dR_g from its own row
+  const double dE = (-FG + cr * sFRe) / (1.0 - cr * sde);
+  double lam = 1.0;
+  for (int k = 0; k < 40 && !(C.Eint + lam * dE > 0.0); ++k) lam *= 0.5;
+  C.Eint += lam * dE;
+  for (int g = 0; g < G; ++g) {
+    const double ie = A.qe[g] > 0.0 ? A.qe[g] : 1.0;
+    A.R[g] += lam * (A.FR[g] + A.dg[g] * dE) * ie;
+  }
+  ++C.nit;
+  ++C.it;
+  return 0;
+}
+
+// a9-a12 after an inner solve: write-back, flux and momentum update, outer
+// test.  Returns true when the cell is done (converged or at a cap); else the
+// next outer pass has been set up.
+template <int MAXG>
+__device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &tab, Cell &C,
+                                          Arr64<MAXG> &A) {
   const int G = P.G;
   const int64_t i = C.i;
   const double c = P.c, chat = P.c_hat, cr = c / chat;
   const double tdt = chat * P.theta * P.dt;
   const double inv_c2 = 1.0 / (c * c);
   const double icc = 1.0 / (c * chat);
-  const double tol = P.tol, tol_out = P.tol_outer;
-  const bool tdep = P.temp_exp != 0.0;
-  const bool gtest = (P.flags & RHD_GROUP_TEST) != 0;
   const double rho = C.rho;
+  const bool gtest = (P.flags & RHD_GROUP_TEST) != 0;
 
-  for (int outer = 0; outer < max_outer; ++outer) {
-    // ---- a3: terms frozen for this outer pass
-    const double KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) / rho;
-    const double v[3] = {C.m[0] / rho, C.m[1] / rho, C.m[2] / rho};
-    for (int g = 0; g < G; ++g)
-      A.w[g] = (v[0] * A.Fk[3 * g] + v[1] * A.Fk[3 * g + 1] + v[2] * A.Fk[3 * g + 2]) * inv_c2;
+  // ---- a9: conservative energy write-back
+  double sumR = 0.0;
+  for (int g = 0; g < G; ++g) sumR += A.R[g];
+  C.egas_new = C.eg0 - cr * sumR;
 
-    // ---- inner Newton (a4-a8)
-    bool conv = false;
-    for (int it = 0; it <= P.max_newton; ++it) {
-      const double T = C.Eint * C.irc;
-      if (tdep) set_tau(P, tab, C, A, C.chi0s * pow(T / P.T_ref, P.temp_exp));
-      const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
-      const double invT = 1.0 / T;
-      double pqL, dL;
-      bool lowL;
-      edge_fp64(tab.xe[0] * invT, pqL, dL, lowL);
-      double sumR = 0.0, sFRe = 0.0, sde = 0.0, sabs = 0.0;
-      for (int g = 0; g < G; ++g) {
-        double pqU, dU;
-        bool lowU;
-        edge_fp64(tab.xe[g + 1] * invT, pqU, dU, lowU);
-        const int64_t o = (int64_t)g * P.gs + i;
-        const double dP = band_fp64(pqL, lowL, pqU, lowU);
-        const double dD = dU - dL;
-        const double b = aT4 * dP;
-        const double a = tab.alpha[g], rm = tab.rm[g], rp = tab.rp[g];
-        const double q = chiF_ratio<double>(b, aT4, dD, a, rm, rp, dL, dU);  // a5
-        A.bq[g] = b;
-        A.dnx[g] = aT4 * (rp * dU - rm * dL);  // (4pi/c) Delta_g(nu chi_0 B_nu) / chi_E
-        A.qF[g] = q;
-        // a6: F_R,g of eq. FGFR, E_g(T, R_g) from eq. Rnew solved for E_g
-        const double ie = A.qe[g];  // = -1/e_g
-        double fr, d;
-        if (ie > 0.0) {
-          const double Eg = b + (1.0 + a) * q * A.w[g] - A.R[g] * C.its * tab.ikbar[g];
-          const double s = P.src ? P.src[o] : 0.0;
-          fr = Eg - P.erad[o] - A.R[g] - s;
-          d = aT3 * (4.0 * dP - dD) * C.irc;  // a7: (1/C_v) d b_g / dT
-        } else {
-          fr = -A.R[g];  // uncoupled group: R_g = 0
-          d = 0.0;
-        }
-        const double iee = ie > 0.0 ? ie : 1.0;  // -1/e_g (e_g = -1 when uncoupled)
-        A.FR[g] = fr;
-        A.dg[g] = d;
-        sumR += A.R[g];
-        sFRe -= fr * iee;
-        sde -= d * iee;
-        sabs += fabs(fr);
-        pqL = pqU;
-        dL = dU;
-        lowL = lowU;
-      }
-      const double FG = C.Eint + KE - C.eg0 + cr * sumR;
-      // a8: convergence test
-      if (fabs(FG) < tol * C.Etot && cr * sabs < tol * C.Etot) {
-        conv = true;
-        // each R_g from its own row of eq. FGFR at the converged T (the
-        // arrowhead rows with dE = 0): groups far below E_tot, which the
-        // aggregate test cannot see, end consistent with T to round-off
-        for (int g = 0; g < G; ++g)
-          if (A.qe[g] > 0.0) A.R[g] += A.FR[g] * A.qe[g];
-        break;
-      }
-      if (it == P.max_newton) break;
-      // a7: arrowhead elimination of eq. matrix: dE from the reduced first row,
-      // then each dR_g from its own row
-      const double dE = (-FG + cr * sFRe) / (1.0 - cr * sde);
-      double lam = 1.0;
-      for (int k = 0; k < 40 && !(C.Eint + lam * dE > 0.0); ++k) lam *= 0.5;
-      C.Eint += lam * dE;
-      for (int g = 0; g < G; ++g) {
-        const double ie = A.qe[g] > 0.0 ? A.qe[g] : 1.0;
-        A.R[g] += lam * (A.FR[g] + A.dg[g] * dE) * ie;
-      }
-      ++C.nit;
-    }
-    if (!conv) C.stat = RHD_STATUS_MAXITER;
-
-    // ---- a9: conservative energy write-back
-    double sumR = 0.0;
-    for (int g = 0; g < G; ++g) sumR += A.R[g];
-    C.egas_new = C.eg0 - cr * sumR;
-
-    // ---- a10: flux update eq. numF1 (outdated velocity v_k)
-    double dF[3] = {0.0, 0.0, 0.0};
-    for (int g = 0; g < G; ++g) {
+  // ---- a10: flux update eq. numF1 (outdated velocity v_k)
+  const double *v = C.v;
+  double dF[3] = {0.0, 0.0, 0.0};
+  for (int g = 0; g < G; ++g) {
+    const int64_t o = (int64_t)g * P.gs + i;
+    const double s = P.src ? P.src[o] : 0.0;
+    const double Enew = P.erad[o] + A.R[g] + s;
+    const double chiB = C.cs * tab.kbar[g], a = tab.alpha[g];
+    double vp0, vp1, vp2;
+    closure_vP<double>(P.closure, c, Enew, A.Fk[3 * g], A.Fk[3 * g + 1], A.Fk[3 * g + 2], v[0],
+                       v[1], v[2], vp0, vp1, vp2);
+    const double srcg = chiB * (A.bq[g] - A.dnx[g] * (1.0 / 3.0));
+    const double kP = (1.0 + a) * chiB;
+    const double inv = 1.0 / (1.0 + tdt * chiB * A.qF[g]);
+    const double ft0 = P.frad[0][o], ft1 = P.frad[1][o], ft2 = P.frad[2][o];
+    const double n0 = (ft0 + tdt * (v[0] * srcg + kP * vp0)) * inv;
+    const double n1 = (ft1 + tdt * (v[1] * srcg + kP * vp1)) * inv;
+    const double n2 = (ft2 + tdt * (v[2] * srcg + kP * vp2)) * inv;
+    dF[0] += n0 - ft0;
+    dF[1] += n1 - ft1;
+    dF[2] += n2 - ft2;
+    A.Fk[3 * g] = n0;
+    A.Fk[3 * g + 1] = n1;
+    A.Fk[3 * g + 2] = n2;
+  }
+  // ---- a11: momentum update
+  const double mn[3] = {C.m0[0] - dF[0] * icc, C.m0[1] - dF[1] * icc, C.m0[2] - dF[2] * icc};
+  // ---- a12: outer test on the change of the v,F-terms of R_g, taken as their
+  // effect on R_g after the implicit energy solve (divided by
+  // 1 + c_hat theta dt chi_E), plus the change of the kinetic energy, which
+  // moves T = (E_gas - E_kin)/(rho c_v) and with it every term of R_g
+  const double vn[3] = {mn[0] / rho, mn[1] / rho, mn[2] / rho};
+  const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho;
+  double chg = fabs(KEn - C.KE);
+  bool gok = true;
+  for (int g = 0; g < G; ++g) {
+    const double wn =
+        (vn[0] * A.Fk[3 * g] + vn[1] * A.Fk[3 * g + 1] + vn[2] * A.Fk[3 * g + 2]) * inv_c2;
+    const double tauE = tdt * C.cs * tab.kbar[g];
+    const double cg = fabs(tauE * (1.0 + tab.alpha[g]) * A.qF[g] * (wn - A.w[g])) / (1.0 + tauE);
+    chg += cg;
+    if (gtest) {
       const int64_t o = (int64_t)g * P.gs + i;
       const double s = P.src ? P.src[o] : 0.0;
-      const double Enew = P.erad[o] + A.R[g] + s;
-      const double chiB = C.cs * tab.kbar[g], a = tab.alpha[g];
-      double vp0, vp1, vp2;
-      closure_vP<double>(P.closure, c, Enew, A.Fk[3 * g], A.Fk[3 * g + 1], A.Fk[3 * g + 2], v[0],
-                         v[1], v[2], vp0, vp1, vp2);
-      const double srcg = chiB * (A.bq[g] - A.dnx[g] * (1.0 / 3.0));
-      const double kP = (1.0 + a) * chiB;
-      const double inv = 1.0 / (1.0 + tdt * chiB * A.qF[g]);
-      const double ft0 = P.frad[0][o], ft1 = P.frad[1][o], ft2 = P.frad[2][o];
-      const double n0 = (ft0 + tdt * (v[0] * srcg + kP * vp0)) * inv;
-      const double n1 = (ft1 + tdt * (v[1] * srcg + kP * vp1)) * inv;
-      const double n2 = (ft2 + tdt * (v[2] * srcg + kP * vp2)) * inv;
-      dF[0] += n0 - ft0;
-      dF[1] += n1 - ft1;
-      dF[2] += n2 - ft2;
-      A.Fk[3 * g] = n0;
-      A.Fk[3 * g + 1] = n1;
-      A.Fk[3 * g + 2] = n2;
-    }
-    // ---- a11: momentum update
-    const double mn[3] = {C.m0[0] - dF[0] * icc, C.m0[1] - dF[1] * icc, C.m0[2] - dF[2] * icc};
-    // ---- a12: outer test on the change of the v,F-terms of R_g, taken as
-    // their effect on R_g after the implicit energy solve (divided by
-    // 1 + c_hat theta dt chi_E), plus the change of the kinetic energy, which
-    // moves T = (E_gas - E_kin)/(rho c_v) and with it every term of R_g
-    const double vn[3] = {mn[0] / rho, mn[1] / rho, mn[2] / rho};
-    double chg = fabs(0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho - KE);
-    bool gok = true;
-    for (int g = 0; g < G; ++g) {
-      const double wn =
-          (vn[0] * A.Fk[3 * g] + vn[1] * A.Fk[3 * g + 1] + vn[2] * A.Fk[3 * g + 2]) * inv_c2;
-      const double tauE = tdt * C.cs * tab.kbar[g];
-      const double cg = fabs(tauE * (1.0 + tab.alpha[g]) * A.qF[g] * (wn - A.w[g])) / (1.0 + tauE);
-      chg += cg;
-      if (gtest) {
-        const int64_t o = (int64_t)g * P.gs + i;
-        const double s = P.src ? P.src[o] : 0.0;
-        gok = gok && cg <= tol_out * (fabs(P.erad[o]) + fabs(s) + fabs(P.erad[o] + A.R[g] + s));
-      }
-    }
-    C.m[0] = mn[0];
-    C.m[1] = mn[1];
-    C.m[2] = mn[2];
-    if (chg <= tol_out * C.Etot && gok) return;
-    if (outer == max_outer - 1) {
-      C.stat = RHD_STATUS_MAXITER;
-      return;
-    }
-    // warm start of the next inner solve from the written-back gas energy
-    C.Eint = C.egas_new - 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) / rho;
-    if (!(C.Eint > 0.0)) {
-      C.stat = RHD_STATUS_MAXITER;
-      return;
+      gok = gok && cg <= P.tol_outer * (fabs(P.erad[o]) + fabs(s) + fabs(P.erad[o] + A.R[g] + s));
     }
   }
+  C.m[0] = mn[0];
+  C.m[1] = mn[1];
+  C.m[2] = mn[2];
+  ++C.outer;
+  if (chg <= P.tol_outer * C.Etot && gok) return true;
+  if (C.outer >= P.max_outer) {
+    C.stat = RHD_STATUS_MAXITER;
+    return true;
+  }
+  // warm start of the next inner solve from the written-back gas energy
+  C.Eint = C.egas_new - KEn;
+  if (!(C.Eint > 0.0)) {
+    C.stat = RHD_STATUS_MAXITER;
+    return true;
+  }
+  outer_begin(P, C, A);
+  return false;
 }
 
 // Store the cell (a13).
@@ -299,18 +343,88 @@ __device__ __forceinline__ void store_cell(const KParams &P, const Cell &C, cons
   if (P.iters) P.iters[i] = (uint8_t)(C.nit > 255 ? 255 : C.nit);
 }
 
+// The warm start a previous FP32 pass leaves in the workspace (see
+// rhd_mixed.cuh); r == nullptr means a cold start (R_g = 0, E_gas = E_gas^t).
+struct WarmStart {
+  const double *eint;  // [n] internal energy
+  const double *mom;   // [3][n] momentum
+  const float *r;      // [G][n] R_g / E_tot
+  const float *f;      // [3][G][n] F_g / (c E_tot)
+  const uint8_t *nit;  // [n] FP32 Newton iterations
+};
+
 template <int MAXG>
-__global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__ KParams P) {
+__device__ __forceinline__ void apply_warm(const KParams &P, const WarmStart &W, Cell &C,
+                                           Arr64<MAXG> &A) {
+  const int64_t i = C.i, n = P.n;
+  C.Eint = W.eint[i];
+  C.m[0] = W.mom[i];
+  C.m[1] = W.mom[n + i];
+  C.m[2] = W.mom[2 * n + i];
+  C.nit = W.nit[i];
+  const double fs = P.c * C.Etot;
+  for (int g = 0; g < P.G; ++g) {
+    const int64_t o = (int64_t)g * n + i;
+    A.R[g] = (double)W.r[o] * C.Etot;
+    A.Fk[3 * g] = (double)W.f[o] * fs;
+    A.Fk[3 * g + 1] = (double)W.f[(int64_t)P.G * n + o] * fs;
+    A.Fk[3 * g + 2] = (double)W.f[(int64_t)2 * P.G * n + o] * fs;
+  }
+}
+
+// Lane-persistent FP64 solve: each lane walks the cells i, i + stride, ...,
+// taking the next one as soon as the current one is stored (PERSIST), or
+// finishing each cell before the warp moves on (!PERSIST).
+template <int MAXG, bool PERSIST>
+__global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__ KParams P,
+                                                         const WarmStart W) {
   extern __shared__ double sm[];
   const GroupTable tab = build_table(P, sm);
   Arr64<MAXG> A;
   Cell C;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
-    if (!load_cell(P, i, C, A)) continue;
-    set_tau(P, tab, C, A, C.chi0s);
-    fp64_outer(P, tab, C, A, P.max_outer);
-    store_cell(P, C, A);
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (!PERSIST) {
+    for (; i < P.n; i += stride) {
+      if (!load_cell(P, i, C, A)) continue;
+      set_tau(P, tab, C, A, C.chi0s);
+      if (W.r) apply_warm(P, W, C, A);
+      outer_begin(P, C, A);
+      for (;;) {
+        const int r = inner_step(P, tab, C, A);
+        if (r == 0) continue;
+        if (r == 2) C.stat = RHD_STATUS_MAXITER;
+        if (outer_end(P, tab, C, A)) break;
+      }
+      store_cell(P, C, A);
+    }
+    return;
+  }
+  auto next = [&]() -> bool {
+    while (i < P.n) {
+      if (load_cell(P, i, C, A)) {
+        set_tau(P, tab, C, A, C.chi0s);
+        if (W.r) apply_warm(P, W, C, A);
+        outer_begin(P, C, A);
+        return true;
+      }
+      i += stride;
+    }
+    return false;
+  };
+  bool active = next();
+  while (__any_sync(0xffffffffu, active)) {
+    if (active) {
+      const int r = inner_step(P, tab, C, A);
+      if (r != 0) {
+        if (r == 2) C.stat = RHD_STATUS_MAXITER;
+        if (outer_end(P, tab, C, A)) {
+          store_cell(P, C, A);
+          i += stride;
+          active = next();
+        }
+      }
+    }
   }
 }
 

@@ -9,8 +9,10 @@
 // (rhd_fp64.cuh): the residual of eq. FGFR and the Planck-integral differences
 // are evaluated in FP64, the Newton correction is applied, the paper's
 // convergence test is checked in FP64 at the caller's tolerance, and the
-// conservative write-back, flux and momentum updates are FP64.  Phase B usually
-// needs one correction and one confirming evaluation.
+// conservative write-back, flux and momentum updates are FP64.
+// The phases are two lane-persistent launches; phase A leaves its iterate in a
+// workspace (WarmStart, rhd_fp64.cuh), so each launch keeps full warps on its
+// own kind of arithmetic.
 #pragma once
 #include "rhd_fp64.cuh"
 
@@ -24,17 +26,19 @@ __constant__ float c_bern3_f[kNB32];
 __constant__ float c_invn_f[kNQ32 + 1];
 
 // FP32 edge values, same split and series as edge_fp64, cut at FP32 precision.
-__device__ __forceinline__ void edge_fp32(float x, float &pq, float &d, bool &low) {
+__device__ __forceinline__ void edge_fp32(float x, float &pq, float &d, float &ed, bool &low) {
   const float K = (float)kPlanckNorm;
   if (!(x > 0.0f)) {
     pq = 0.0f;
     d = 0.0f;
+    ed = 0.0f;
     low = true;
     return;
   }
   if (isinf(x)) {
     pq = 0.0f;
     d = 0.0f;
+    ed = 0.0f;
     low = false;
     return;
   }
@@ -47,8 +51,10 @@ __device__ __forceinline__ void edge_fp32(float x, float &pq, float &d, bool &lo
       s3 = fmaf(s3, z, c_bern3_f[j]);
     }
     const float x3 = z * x;
+    const float xr = fmaf(z, s1, fmaf(-0.5f, x, 1.0f));
     pq = K * x3 * fmaf(z, s3, fmaf(-0.125f, x, 1.0f / 3.0f));
-    d = K * x3 * fmaf(z, s1, fmaf(-0.5f, x, 1.0f));
+    d = K * x3 * xr;
+    ed = d * (4.0f - xr - x);
     low = true;
   } else {
     const float e1 = __expf(-x);
@@ -65,7 +71,9 @@ __device__ __forceinline__ void edge_fp32(float x, float &pq, float &d, bool &lo
       sum = fmaf(en * inv, h, sum);
     }
     pq = K * sum;
-    d = __fdividef(K * x3 * x * e1, 1.0f - e1);
+    const float inv1 = __fdividef(1.0f, 1.0f - e1);
+    d = K * x3 * x * e1 * inv1;
+    ed = d * (4.0f - x * inv1);
     low = false;
   }
 }
@@ -80,7 +88,13 @@ template <int MAXG>
 struct Arr32 {
   float R[MAXG], FR[MAXG], dg[MAXG], qe[MAXG], itau[MAXG], tau[MAXG], e0[MAXG], w[MAXG];
   float b[MAXG], dnx[MAXG], q[MAXG];
-  float f[3 * MAXG];
+  float f[3 * MAXG], ft[3 * MAXG];
+};
+
+// FP32-phase scalars of one cell beyond Cell: the frozen scaled velocity.
+struct Cell32 {
+  float be[3];
+  double sE;  // 1 / E_tot
 };
 
 // tau_g = c_hat theta dt chi_E,g, 1/tau_g and tau/(1+tau) for opacity scale cs.
@@ -96,171 +110,251 @@ __device__ __forceinline__ void set_tau32(const KParams &P, const GroupTable &ta
   }
 }
 
-// Phase A: the FP32 inner/outer iteration.  On return the cell's FP64 iterate
-// (Eint, m, R, Fk) holds the FP32 solution as the warm start of phase B.
+// Load one cell into the FP32 phase (validation as in load_cell).
 template <int MAXG>
-__device__ __forceinline__ void fp32_phase(const KParams &P, const GroupTable &tab, Cell &C,
-                                           Arr64<MAXG> &A, Arr32<MAXG> &B) {
+__device__ __forceinline__ bool load_cell32(const KParams &P, const GroupTable &tab, int64_t i,
+                                            Cell &C, Cell32 &D, Arr32<MAXG> &B) {
   const int G = P.G;
-  const int64_t i = C.i;
-  const double c = P.c, chat = P.c_hat;
-  const float cr = (float)(c / chat);
-  const double Etot = C.Etot, sE = 1.0 / Etot;
-  const float tol32 = 2e-6f, tolo32 = 1e-6f;
-  const bool tdep = P.temp_exp != 0.0;
-  const double rho = C.rho;
-  const int max_it = P.max_newton < 32 ? P.max_newton : 32;
-
-  // scaled start values
+  C.i = i;
+  C.rho = P.rho[i];
+  C.m0[0] = P.mom[0][i];
+  C.m0[1] = P.mom[1][i];
+  C.m0[2] = P.mom[2][i];
+  C.eg0 = P.egas[i];
+  const double k0 = P.kappa0 ? P.kappa0[i] : 1.0;
+  bool valid = C.rho > 0.0 && isfinite(C.rho) && isfinite(C.eg0) && isfinite(k0) && k0 >= 0.0 &&
+               isfinite(C.m0[0]) && isfinite(C.m0[1]) && isfinite(C.m0[2]);
+  const double KE0 = 0.5 * (C.m0[0] * C.m0[0] + C.m0[1] * C.m0[1] + C.m0[2] * C.m0[2]) / C.rho;
+  valid = valid && (C.eg0 - KE0 > 0.0);
+  double sumE0 = 0.0;
   for (int g = 0; g < G; ++g) {
     const int64_t o = (int64_t)g * P.gs + i;
-    const double s = P.src ? P.src[o] : 0.0;
-    B.e0[g] = (float)((P.erad[o] + s) * sE);
-    const double fs = sE / c;
-    B.f[3 * g] = (float)(A.Fk[3 * g] * fs);
-    B.f[3 * g + 1] = (float)(A.Fk[3 * g + 1] * fs);
-    B.f[3 * g + 2] = (float)(A.Fk[3 * g + 2] * fs);
+    const double e = P.erad[o] + (P.src ? P.src[o] : 0.0);
+    valid = valid && isfinite(e) && isfinite(P.frad[0][o]) && isfinite(P.frad[1][o]) &&
+            isfinite(P.frad[2][o]);
+    sumE0 += e;
+  }
+  if (!valid) return false;  // the FP64 launch writes the status
+  C.chi0s = C.rho * k0;
+  C.Etot = C.eg0 + (P.c / P.c_hat) * sumE0;
+  C.rcv = C.rho * P.c_v;
+  C.irc = 1.0 / C.rcv;
+  C.m[0] = C.m0[0];
+  C.m[1] = C.m0[1];
+  C.m[2] = C.m0[2];
+  C.Eint = C.eg0 - KE0;
+  C.nit = 0;
+  C.outer = 0;
+  D.sE = 1.0 / C.Etot;
+  const double fs = D.sE / P.c;
+  for (int g = 0; g < G; ++g) {
+    const int64_t o = (int64_t)g * P.gs + i;
+    B.e0[g] = (float)((P.erad[o] + (P.src ? P.src[o] : 0.0)) * D.sE);
+    for (int d = 0; d < 3; ++d) {
+      const float f = (float)(P.frad[d][o] * fs);
+      B.f[3 * g + d] = f;
+      B.ft[3 * g + d] = f;
+    }
     B.R[g] = 0.0f;
   }
   set_tau32(P, tab, B, C.chi0s);
-
-  for (int outer = 0; outer < P.max_outer; ++outer) {
-    const double KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) / rho;
-    const float be[3] = {(float)(C.m[0] / (rho * c)), (float)(C.m[1] / (rho * c)),
-                         (float)(C.m[2] / (rho * c))};
-    for (int g = 0; g < G; ++g)
-      B.w[g] = be[0] * B.f[3 * g] + be[1] * B.f[3 * g + 1] + be[2] * B.f[3 * g + 2];
-
-    for (int it = 0; it <= max_it; ++it) {
-      const double T = C.Eint * C.irc;
-      if (tdep) set_tau32(P, tab, B, C.chi0s * pow(T / P.T_ref, P.temp_exp));
-      const double aT3 = P.a_rad * T * T * T;
-      const float aT4s = (float)(aT3 * T * sE);
-      const float kd = (float)(aT3 * C.irc);  // a_R T^3 / (rho c_v): d~_g = kd (4 dP - dD)
-      const float invT = (float)(1.0 / T);
-      float pqL, dL;
-      bool lowL;
-      edge_fp32(tab.xef[0] * invT, pqL, dL, lowL);
-      float sumR = 0.0f, sFRe = 0.0f, sde = 0.0f, sabs = 0.0f;
-      for (int g = 0; g < G; ++g) {
-        float pqU, dU;
-        bool lowU;
-        edge_fp32(tab.xef[g + 1] * invT, pqU, dU, lowU);
-        const float dP = band_fp32(pqL, lowL, pqU, lowU);
-        const float dD = dU - dL;
-        const float b = aT4s * dP;
-        const float a = tab.alphaf[g], rm = tab.rmf[g], rp = tab.rpf[g];
-        const float q = chiF_ratio<float>(b, aT4s, dD, a, rm, rp, dL, dU);
-        B.b[g] = b;
-        B.dnx[g] = aT4s * (rp * dU - rm * dL);
-        B.q[g] = q;
-        const float ie = B.qe[g];
-        float fr, d;
-        if (ie > 0.0f) {
-          const float Eg = b + (1.0f + a) * q * B.w[g] - B.R[g] * B.itau[g];
-          fr = Eg - B.e0[g] - B.R[g];
-          d = kd * (4.0f * dP - dD);
-        } else {
-          fr = -B.R[g];
-          d = 0.0f;
-        }
-        const float iee = ie > 0.0f ? ie : 1.0f;
-        B.FR[g] = fr;
-        B.dg[g] = d;
-        sumR += B.R[g];
-        sFRe -= fr * iee;
-        sde -= d * iee;
-        sabs += fabsf(fr);
-        pqL = pqU;
-        dL = dU;
-        lowL = lowU;
-      }
-      const float FG = (float)((C.Eint + KE - C.eg0) * sE) + cr * sumR;
-      if (fabsf(FG) < tol32 && cr * sabs < tol32) break;
-      if (it == max_it) break;
-      const float dE = (-FG + cr * sFRe) / (1.0f - cr * sde);
-      double lam = 1.0;
-      for (int k = 0; k < 40 && !(C.Eint + lam * (double)dE * Etot > 0.0); ++k) lam *= 0.5;
-      C.Eint += lam * (double)dE * Etot;
-      const float lf = (float)lam;
-      for (int g = 0; g < G; ++g) {
-        const float ie = B.qe[g] > 0.0f ? B.qe[g] : 1.0f;
-        B.R[g] += lf * (B.FR[g] + B.dg[g] * dE) * ie;
-      }
-      ++C.nit;
-      if (fabsf(dE) < 1e-8f) break;  // step below FP32 resolution of E_tot
-    }
-
-    // write-back (energies stay scaled), flux update eq. numF1, momentum
-    float sR = 0.0f;
-    for (int g = 0; g < G; ++g) sR += B.R[g];
-    const double egas_new = C.eg0 - (double)cr * (double)sR * Etot;
-    float df[3] = {0.0f, 0.0f, 0.0f};
-    for (int g = 0; g < G; ++g) {
-      const int64_t o = (int64_t)g * P.gs + i;
-      const float En = B.e0[g] + B.R[g];
-      float vp0, vp1, vp2;
-      closure_vP<float>(P.closure, 1.0f, En, B.f[3 * g], B.f[3 * g + 1], B.f[3 * g + 2], be[0],
-                        be[1], be[2], vp0, vp1, vp2);
-      const float t = B.tau[g], a = tab.alphaf[g];
-      const float srcg = t * (B.b[g] - B.dnx[g] * (1.0f / 3.0f));
-      const float kP = (1.0f + a) * t;
-      const float inv = 1.0f / (1.0f + t * B.q[g]);
-      const double fs = sE / c;
-      const float ft0 = (float)(P.frad[0][o] * fs), ft1 = (float)(P.frad[1][o] * fs),
-                  ft2 = (float)(P.frad[2][o] * fs);
-      const float n0 = (ft0 + be[0] * srcg + kP * vp0) * inv;
-      const float n1 = (ft1 + be[1] * srcg + kP * vp1) * inv;
-      const float n2 = (ft2 + be[2] * srcg + kP * vp2) * inv;
-      df[0] += n0 - ft0;
-      df[1] += n1 - ft1;
-      df[2] += n2 - ft2;
-      B.f[3 * g] = n0;
-      B.f[3 * g + 1] = n1;
-      B.f[3 * g + 2] = n2;
-    }
-    const double mf = Etot / chat;  // (c E_tot)/(c c_hat)
-    const double mn[3] = {C.m0[0] - mf * df[0], C.m0[1] - mf * df[1], C.m0[2] - mf * df[2]};
-    const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho;
-    const float bn[3] = {(float)(mn[0] / (rho * c)), (float)(mn[1] / (rho * c)),
-                         (float)(mn[2] / (rho * c))};
-    float chg = (float)(fabs(KEn - KE) * sE);
-    for (int g = 0; g < G; ++g) {
-      const float wn = bn[0] * B.f[3 * g] + bn[1] * B.f[3 * g + 1] + bn[2] * B.f[3 * g + 2];
-      const float t = B.tau[g];
-      chg += fabsf(t * (1.0f + tab.alphaf[g]) * B.q[g] * (wn - B.w[g])) / (1.0f + t);
-    }
-    C.m[0] = mn[0];
-    C.m[1] = mn[1];
-    C.m[2] = mn[2];
-    C.Eint = egas_new - KEn;  // start of the next pass (or of phase B)
-    if (!(C.Eint > 0.0)) C.Eint = C.eg0 - KE;
-    if (chg <= tolo32) break;
-  }
-  // hand over to phase B
-  for (int g = 0; g < G; ++g) {
-    A.R[g] = (double)B.R[g] * Etot;
-    const double fs = c * Etot;
-    A.Fk[3 * g] = (double)B.f[3 * g] * fs;
-    A.Fk[3 * g + 1] = (double)B.f[3 * g + 1] * fs;
-    A.Fk[3 * g + 2] = (double)B.f[3 * g + 2] * fs;
-  }
+  return true;
 }
 
 template <int MAXG>
-__global__ void __launch_bounds__(128) solve_mixed_kernel(const __grid_constant__ KParams P) {
+__device__ __forceinline__ void outer_begin32(const KParams &P, Cell &C, Cell32 &D,
+                                              Arr32<MAXG> &B) {
+  const double rho = C.rho, c = P.c;
+  C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) / rho;
+  for (int d = 0; d < 3; ++d) D.be[d] = (float)(C.m[d] / (rho * c));
+  for (int g = 0; g < P.G; ++g)
+    B.w[g] = D.be[0] * B.f[3 * g] + D.be[1] * B.f[3 * g + 1] + D.be[2] * B.f[3 * g + 2];
+  C.it = 0;
+}
+
+// One FP32 inner iteration (same steps as inner_step, scaled variables);
+// returns 0 (continue), 1 (converged at FP32 resolution) or 2 (cap).
+template <int MAXG>
+__device__ __forceinline__ int inner_step32(const KParams &P, const GroupTable &tab, Cell &C,
+                                            Cell32 &D, Arr32<MAXG> &B) {
+  const int G = P.G;
+  const float cr = (float)(P.c / P.c_hat);
+  const double Etot = C.Etot, sE = D.sE;
+  const float tol32 = 2e-6f;
+  const int max_it = P.max_newton < 32 ? P.max_newton : 32;
+  const double T = C.Eint * C.irc;
+  if (P.temp_exp != 0.0) set_tau32(P, tab, B, C.chi0s * pow(T / P.T_ref, P.temp_exp));
+  const double aT3 = P.a_rad * T * T * T;
+  const float aT4s = (float)(aT3 * T * sE);
+  const float aT3s = (float)(aT3 * sE);
+  const float kT = (float)(Etot * C.irc);  // dT / dE~_int
+  const float invT = (float)(1.0 / T);
+  float pqL, dL, eL;
+  bool lowL;
+  edge_fp32(tab.xef[0] * invT, pqL, dL, eL, lowL);
+  float sumR = 0.0f, sFRe = 0.0f, sde = 0.0f, sabs = 0.0f;
+  for (int g = 0; g < G; ++g) {
+    float pqU, dU, eU;
+    bool lowU;
+    edge_fp32(tab.xef[g + 1] * invT, pqU, dU, eU, lowU);
+    const float dP = band_fp32(pqL, lowL, pqU, lowU);
+    const float dD = dU - dL;
+    const float b = aT4s * dP;
+    const float dbs = aT3s * (4.0f * dP - dD);  // d b~_g / dT
+    const float a = tab.alphaf[g], rm = tab.rmf[g], rp = tab.rpf[g];
+    float dq;
+    const float q = chiF_ratio<float>(b, aT4s, dD, a, rm, rp, dL, dU, dbs, aT3s, eL, eU, dq);
+    B.b[g] = b;
+    B.dnx[g] = aT4s * (rp * dU - rm * dL);
+    B.q[g] = q;
+    const float ie = B.qe[g];
+    float fr, d;
+    if (ie > 0.0f) {
+      const float Eg = b + (1.0f + a) * q * B.w[g] - B.R[g] * B.itau[g];
+      fr = Eg - B.e0[g] - B.R[g];
+      d = (dbs + (1.0f + a) * dq * B.w[g]) * kT;  // dF~_R,g / dE~_int
+    } else {
+      fr = -B.R[g];
+      d = 0.0f;
+    }
+    const float iee = ie > 0.0f ? ie : 1.0f;
+    B.FR[g] = fr;
+    B.dg[g] = d;
+    sumR += B.R[g];
+    sFRe -= fr * iee;
+    sde -= d * iee;
+    sabs += fabsf(fr);
+    pqL = pqU;
+    dL = dU;
+    eL = eU;
+    lowL = lowU;
+  }
+  const float FG = (float)((C.Eint + C.KE - C.eg0) * sE) + cr * sumR;
+  if (fabsf(FG) < tol32 && cr * sabs < tol32) return 1;
+  if (C.it >= max_it) return 2;
+  const float dE = (-FG + cr * sFRe) / (1.0f - cr * sde);
+  double lam = 1.0;
+  for (int k = 0; k < 40 && !(C.Eint + lam * (double)dE * Etot > 0.0); ++k) lam *= 0.5;
+  C.Eint += lam * (double)dE * Etot;
+  const float lf = (float)lam;
+  for (int g = 0; g < G; ++g) {
+    const float ie = B.qe[g] > 0.0f ? B.qe[g] : 1.0f;
+    B.R[g] += lf * (B.FR[g] + B.dg[g] * dE) * ie;
+  }
+  ++C.nit;
+  ++C.it;
+  return fabsf(dE) < 1e-8f ? 1 : 0;  // a step below FP32 resolution of E_tot ends it
+}
+
+// FP32 write-back, flux update eq. numF1, momentum update and outer test;
+// true when the phase is done for this cell.
+template <int MAXG>
+__device__ __forceinline__ bool outer_end32(const KParams &P, const GroupTable &tab, Cell &C,
+                                            Cell32 &D, Arr32<MAXG> &B) {
+  const int G = P.G;
+  const double c = P.c, chat = P.c_hat, rho = C.rho, Etot = C.Etot;
+  const float cr = (float)(c / chat);
+  float sR = 0.0f;
+  for (int g = 0; g < G; ++g) sR += B.R[g];
+  const double egas_new = C.eg0 - (double)cr * (double)sR * Etot;
+  float df[3] = {0.0f, 0.0f, 0.0f};
+  for (int g = 0; g < G; ++g) {
+    const float En = B.e0[g] + B.R[g];
+    float vp0, vp1, vp2;
+    closure_vP<float>(P.closure, 1.0f, En, B.f[3 * g], B.f[3 * g + 1], B.f[3 * g + 2], D.be[0],
+                      D.be[1], D.be[2], vp0, vp1, vp2);
+    const float t = B.tau[g], a = tab.alphaf[g];
+    const float srcg = t * (B.b[g] - B.dnx[g] * (1.0f / 3.0f));
+    const float kP = (1.0f + a) * t;
+    const float inv = 1.0f / (1.0f + t * B.q[g]);
+    const float n0 = (B.ft[3 * g] + D.be[0] * srcg + kP * vp0) * inv;
+    const float n1 = (B.ft[3 * g + 1] + D.be[1] * srcg + kP * vp1) * inv;
+    const float n2 = (B.ft[3 * g + 2] + D.be[2] * srcg + kP * vp2) * inv;
+    df[0] += n0 - B.ft[3 * g];
+    df[1] += n1 - B.ft[3 * g + 1];
+    df[2] += n2 - B.ft[3 * g + 2];
+    B.f[3 * g] = n0;
+    B.f[3 * g + 1] = n1;
+    B.f[3 * g + 2] = n2;
+  }
+  const double mf = Etot / chat;  // (c E_tot)/(c c_hat)
+  const double mn[3] = {C.m0[0] - mf * df[0], C.m0[1] - mf * df[1], C.m0[2] - mf * df[2]};
+  const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho;
+  const float bn[3] = {(float)(mn[0] / (rho * c)), (float)(mn[1] / (rho * c)),
+                       (float)(mn[2] / (rho * c))};
+  float chg = (float)(fabs(KEn - C.KE) * D.sE);
+  for (int g = 0; g < G; ++g) {
+    const float wn = bn[0] * B.f[3 * g] + bn[1] * B.f[3 * g + 1] + bn[2] * B.f[3 * g + 2];
+    const float t = B.tau[g];
+    chg += fabsf(t * (1.0f + tab.alphaf[g]) * B.q[g] * (wn - B.w[g])) / (1.0f + t);
+  }
+  C.m[0] = mn[0];
+  C.m[1] = mn[1];
+  C.m[2] = mn[2];
+  C.Eint = egas_new - KEn;  // start of the next pass (or of the FP64 phase)
+  if (!(C.Eint > 0.0)) C.Eint = C.eg0 - C.KE;
+  ++C.outer;
+  if (chg <= 1e-6f || C.outer >= P.max_outer) return true;
+  outer_begin32(P, C, D, B);
+  return false;
+}
+
+// Workspace view of the warm start (writable side of WarmStart).
+struct WarmOut {
+  double *eint, *mom;
+  float *r, *f;
+  uint8_t *nit;
+};
+
+template <int MAXG>
+__device__ __forceinline__ void store_warm(const KParams &P, const WarmOut &W, const Cell &C,
+                                           const Arr32<MAXG> &B) {
+  const int64_t i = C.i, n = P.n;
+  W.eint[i] = C.Eint;
+  W.mom[i] = C.m[0];
+  W.mom[n + i] = C.m[1];
+  W.mom[2 * n + i] = C.m[2];
+  W.nit[i] = (uint8_t)(C.nit > 255 ? 255 : C.nit);
+  for (int g = 0; g < P.G; ++g) {
+    const int64_t o = (int64_t)g * n + i;
+    W.r[o] = B.R[g];
+    W.f[o] = B.f[3 * g];
+    W.f[(int64_t)P.G * n + o] = B.f[3 * g + 1];
+    W.f[(int64_t)2 * P.G * n + o] = B.f[3 * g + 2];
+  }
+}
+
+// Phase A launch: lane-persistent FP32 iteration; writes the warm start.
+template <int MAXG>
+__global__ void __launch_bounds__(128) warm_fp32_kernel(const __grid_constant__ KParams P,
+                                                        const WarmOut W) {
   extern __shared__ double sm[];
   const GroupTable tab = build_table(P, sm);
-  Arr64<MAXG> A;
   Arr32<MAXG> B;
   Cell C;
+  Cell32 D;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
-    if (!load_cell(P, i, C, A)) continue;
-    fp32_phase(P, tab, C, A, B);
-    set_tau(P, tab, C, A, C.chi0s);
-    fp64_outer(P, tab, C, A, P.max_outer);
-    store_cell(P, C, A);
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  auto next = [&]() -> bool {
+    while (i < P.n) {
+      if (load_cell32(P, tab, i, C, D, B)) {
+        outer_begin32(P, C, D, B);
+        return true;
+      }
+      i += stride;
+    }
+    return false;
+  };
+  bool active = next();
+  while (__any_sync(0xffffffffu, active)) {
+    if (active) {
+      const int r = inner_step32(P, tab, C, D, B);
+      if (r != 0 && outer_end32(P, tab, C, D, B)) {
+        store_warm(P, W, C, B);
+        i += stride;
+        active = next();
+      }
+    }
   }
 }
 
