@@ -140,6 +140,29 @@ int rhd_source_update(rhd_state_t *state, const rhd_groups_t *groups,
                       const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
                       void *stream);
 
+/* The mixed-precision form without any device allocation.  Some callers
+ * cannot let a library call cudaMalloc: a host that hands every byte of HBM
+ * to its own memory pool up front, a latency-bound loop where a first-call
+ * allocation (which synchronizes the device) is not acceptable, or code that
+ * must never fail for lack of memory in the middle of a run.  This entry point
+ * computes the same result as rhd_source_update with precision = RHD_MIXED
+ * (state->precision is ignored) but keeps the FP32 pass's warm start in a
+ * file-scope device array of RHD_NOALLOC_BYTES that every GPU loading the
+ * library holds until process exit.  The caller still passes all inputs and
+ * outputs.  Size limit: n_cells * (16 * n_groups + 33) + 1024 <=
+ * RHD_NOALLOC_BYTES (64 MiB; e.g. 64K cells at 64 groups); larger calls return
+ * RHD_ESIZE and launch nothing.  The paper has no counterpart: this is a
+ * deployment variant of the same kernels.  The first call on a device looks up
+ * the array's device address (and initialises the constant tables), so make
+ * it before any stream capture.  All calls share the one array and nothing in
+ * it needs to start at zero (each call writes every slot it reads), but calls
+ * that overlap on the GPU (other streams, other threads) race on it: serialise
+ * them. */
+#define RHD_NOALLOC_BYTES ((int64_t)64 << 20)
+int rhd_source_update_noalloc(rhd_state_t *state, const rhd_groups_t *groups,
+                              const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
+                              void *stream);
+
 /* Text for a return code. */
 const char *rhd_strerror(int code);
 

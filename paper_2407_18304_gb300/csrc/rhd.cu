@@ -33,6 +33,16 @@ size_t warm_bytes(int64_t n, int G) {
   return (size_t)n * (4 * sizeof(double) + 1) + (size_t)n * G * 4 * sizeof(float) + 1024;
 }
 
+// Carve the warm-start arrays out of a workspace starting at p.
+void carve(char *p, int64_t n, int G, WarmOut *w, WarmStart *r) {
+  w->eint = reinterpret_cast<double *>(p);
+  w->mom = w->eint + n;
+  w->r = reinterpret_cast<float *>(w->mom + 3 * n);
+  w->f = w->r + (size_t)G * n;
+  w->nit = reinterpret_cast<uint8_t *>(w->f + (size_t)3 * G * n);
+  *r = WarmStart{w->eint, w->mom, w->r, w->f, w->nit};
+}
+
 int workspace(int64_t n, int G, WarmOut *w, WarmStart *r) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RHD_ECUDA;
@@ -45,13 +55,26 @@ int workspace(int64_t n, int G, WarmOut *w, WarmStart *r) {
     if (cudaMalloc(&g_ws[dev], need) != cudaSuccess) return RHD_ENOMEM;
     g_ws_bytes[dev] = need;
   }
-  char *p = static_cast<char *>(g_ws[dev]);
-  w->eint = reinterpret_cast<double *>(p);
-  w->mom = w->eint + n;
-  w->r = reinterpret_cast<float *>(w->mom + 3 * n);
-  w->f = w->r + (size_t)G * n;
-  w->nit = reinterpret_cast<uint8_t *>(w->f + (size_t)3 * G * n);
-  *r = WarmStart{w->eint, w->mom, w->r, w->f, w->nit};
+  carve(static_cast<char *>(g_ws[dev]), n, G, w, r);
+  return RHD_OK;
+}
+
+// Workspace of rhd_source_update_noalloc: a file-scope device array (every
+// device that loads the library holds it).  Host code must not use the symbol
+// as an address: noalloc_base() looks the device address up once per device.
+__device__ __align__(256) unsigned char g_noalloc_ws[RHD_NOALLOC_BYTES];
+char *g_noalloc_ptr[kMaxDevices];
+
+int noalloc_base(char **out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RHD_ECUDA;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_ws) != cudaSuccess || !ptr) return RHD_ECUDA;
+    g_noalloc_ptr[dev] = static_cast<char *>(ptr);
+  }
+  *out = g_noalloc_ptr[dev];
   return RHD_OK;
 }
 
@@ -229,6 +252,18 @@ int persistent_blocks(K kernel, size_t smem, int sms, int64_t n, int threads) {
 }
 
 template <int MAXG>
+int launch_mixed(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int sms,
+                 cudaStream_t st) {
+  const int threads = 128;
+  const size_t smem = table_bytes(kp.G);
+  const int ba = persistent_blocks(warm_fp32_kernel<MAXG>, smem, sms, kp.n, threads);
+  warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo);
+  const int bb = persistent_blocks(solve_fp64_kernel<MAXG, g_persist>, smem, sms, kp.n, threads);
+  solve_fp64_kernel<MAXG, g_persist><<<bb, threads, smem, st>>>(kp, wi);
+  return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
+}
+
+template <int MAXG>
 int launch_g(const KParams &kp, int precision, int sms, cudaStream_t st) {
   const int threads = 128;
   const size_t smem = table_bytes(kp.G);
@@ -279,6 +314,29 @@ extern "C" int rhd_source_update(rhd_state_t *state, const rhd_groups_t *groups,
   rc = rhd::ensure_device(&sms);
   if (rc != RHD_OK) return rc;
   return rhd::launch(kp, state->precision, sms, (cudaStream_t)stream);
+}
+
+extern "C" int rhd_source_update_noalloc(rhd_state_t *state, const rhd_groups_t *groups,
+                                         const rhd_opacity_law_t *opacity_law, double dt,
+                                         int64_t n_cells, void *stream) {
+  static thread_local rhd::KParams kp;
+  int rc = rhd::pack(state, groups, opacity_law, dt, n_cells, &kp);
+  if (rc != RHD_OK) return rc;
+  if ((int64_t)rhd::warm_bytes(n_cells, kp.G) > RHD_NOALLOC_BYTES) return RHD_ESIZE;
+  if (n_cells == 0) return RHD_OK;
+  int sms = 0;
+  rc = rhd::ensure_device(&sms);
+  if (rc != RHD_OK) return rc;
+  char *base = nullptr;
+  rc = rhd::noalloc_base(&base);
+  if (rc != RHD_OK) return rc;
+  rhd::WarmOut wo;
+  rhd::WarmStart wi;
+  rhd::carve(base, n_cells, kp.G, &wo, &wi);
+  cudaStream_t st = (cudaStream_t)stream;
+  if (kp.G <= 16) return rhd::launch_mixed<16>(kp, wo, wi, sms, st);
+  if (kp.G <= 64) return rhd::launch_mixed<64>(kp, wo, wi, sms, st);
+  return rhd::launch_mixed<rhd::kMaxG>(kp, wo, wi, sms, st);
 }
 
 extern "C" const char *rhd_strerror(int code) {

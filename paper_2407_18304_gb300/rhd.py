@@ -20,6 +20,7 @@ PPL_FIXED, PC = 0, 1
 STATUS_OK, STATUS_FALLBACK, STATUS_MAXITER, STATUS_INVALID = 0, 1, 2, 3
 GROUP_TEST = 1
 MAX_GROUPS = 256
+NOALLOC_BYTES = 64 << 20
 
 _P = ctypes.c_void_p
 _D = ctypes.c_double
@@ -72,6 +73,10 @@ def lib() -> ctypes.CDLL:
         _lib.rhd_source_update.restype = ctypes.c_int
         _lib.rhd_source_update.argtypes = [ctypes.POINTER(State), ctypes.POINTER(Groups),
                                            ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _P]
+        _lib.rhd_source_update_noalloc.restype = ctypes.c_int
+        _lib.rhd_source_update_noalloc.argtypes = [ctypes.POINTER(State), ctypes.POINTER(Groups),
+                                                   ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64,
+                                                   _P]
         _lib.rhd_strerror.restype = ctypes.c_char_p
         _lib.rhd_strerror.argtypes = [ctypes.c_int]
         _lib.rhd_version.restype = ctypes.c_int
@@ -171,6 +176,61 @@ def source_update(state: dict, edges, law, *, dt: float, c_v: float, consts: dic
     s = stream if stream is not None else torch.cuda.current_stream()
     rc = lib().rhd_source_update(ctypes.byref(st), ctypes.byref(gr), ctypes.byref(lw), float(dt),
                                  int(n), ctypes.c_void_p(s.cuda_stream))
+    del keep
+    if rc != 0:
+        raise RhdError(rc, lib().rhd_strerror(rc).decode())
+
+
+def source_update_noalloc(state: dict, edges, law, *, dt: float, c_v: float, consts: dict,
+                          theta: float = 1.0, closure: int = M1, tol: float = 0.0,
+                          tol_outer: float = 0.0, max_newton: int = 0, max_outer: int = 0,
+                          status: torch.Tensor | None = None, iters: torch.Tensor | None = None,
+                          mode: int = PPL_FIXED, khat_g=None, alpha_g=None,
+                          temp_exponent: float = 0.0, T_ref: float = 1.0,
+                          stream: torch.cuda.Stream | None = None, flags: int = 0) -> None:
+    """The mixed form through ``rhd_source_update_noalloc`` (no device
+    allocation; the library's fixed 64 MiB device array holds the FP32 warm
+    start).  Same arguments and layout as ``source_update``."""
+    rho = state["rho"]
+    n = rho.shape[0]
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    G = len(e) - 1
+    _check(rho, "rho", (n,))
+    _check(state["mom"], "mom", (3, n))
+    _check(state["egas"], "egas", (n,))
+    _check(state["erad"], "erad", (G, n))
+    _check(state["frad"], "frad", (3, G, n))
+    if state.get("kappa0") is not None:
+        _check(state["kappa0"], "kappa0", (n,))
+    if state.get("src") is not None:
+        _check(state["src"], "src", (G, n))
+    if status is not None:
+        _check(status, "status", (n,), torch.uint8)
+    if iters is not None:
+        _check(iters, "iters", (n,), torch.uint8)
+    st = State()
+    st.rho = _ptr(rho)
+    for d in range(3):
+        st.mom[d] = _ptr(state["mom"][d])
+        st.frad[d] = _ptr(state["frad"][d])
+    st.egas = _ptr(state["egas"])
+    st.kappa0 = _ptr(state.get("kappa0"))
+    st.erad = _ptr(state["erad"])
+    st.src = _ptr(state.get("src"))
+    st.status = _ptr(status)
+    st.iters = _ptr(iters)
+    st.group_stride = n
+    st.c_v, st.theta = float(c_v), float(theta)
+    st.c, st.c_hat = float(consts["c"]), float(consts.get("c_hat", consts["c"]))
+    st.a_rad, st.h, st.k_B = float(consts["a_rad"]), float(consts["h"]), float(consts["k_B"])
+    st.tol, st.tol_outer = float(tol), float(tol_outer)
+    st.max_newton, st.max_outer = int(max_newton), int(max_outer)
+    st.precision, st.closure, st.flags = MIXED, int(closure), int(flags)
+    gr = Groups(G, _dp(e))
+    lw, keep = make_law(law, mode, khat_g, alpha_g, temp_exponent, T_ref)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().rhd_source_update_noalloc(ctypes.byref(st), ctypes.byref(gr), ctypes.byref(lw),
+                                         float(dt), int(n), ctypes.c_void_p(s.cuda_stream))
     del keep
     if rc != 0:
         raise RhdError(rc, lib().rhd_strerror(rc).decode())
