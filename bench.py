@@ -148,9 +148,11 @@ def fp_peaks() -> dict:
 # instruction counts ncu reports for the same workload on a 65536-cell sample
 # (profiles/solve_full_256cube_ng64.md); a property of the workload and the
 # algorithm, applied to the full-size grid of the same distribution.
-FP64_FLOPS_PER_CG = {}
+FP64_FLOPS_PER_CG = {("full_256cube_ng64", "mixed"): 17.7 + 1820.4,
+                     ("full_256cube_ng64", "fp64"): 3271.6}
 # DRAM bytes (read + write) per cell-group of one call from the same capture
-TRAFFIC_PER_CG = {}
+TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed"): 1639.0 + 2099.0,
+                  ("full_256cube_ng64", "fp64"): 3502.0}
 
 
 def run_ours(args, ws, rank):
@@ -242,7 +244,9 @@ def run_ours(args, ws, rank):
         peak = peaks.get("fp64_fma_tflops") or 1.25
         ach = per_cg * n * G / mean_launch_s / 1e12
         res["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                           "frac": ach / peak, "traffic": TRAFFIC_PER_CG.get((name, args.precision)),
+                           "frac": ach / peak,
+                           "traffic": (TRAFFIC_PER_CG[(name, args.precision)] * n * G
+                                       if (name, args.precision) in TRAFFIC_PER_CG else None),
                            "what": "FP64 flops (DFMA = 2) per call / call time, vs the DFMA peak",
                            "peak_source": ("measured fp_peak DFMA loop" if "fp64_fma_tflops" in peaks
                                            else "nominal 1.25 TFLOP/s"),
