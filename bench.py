@@ -265,6 +265,98 @@ def run_ours(args, ws, rank):
     return res
 
 
+BATCHED = "batched_64grids"
+
+
+def run_batched(args, ws, rank):
+    """64 uneven grids (16^3..96^3 cells, N_g in {4,..,64}, own opacity law
+    each) advanced by one rhd_source_update_batched call per step (persistent
+    launch, device work queue, replayed CUDA graph, autotuned shape); the same
+    grids one rhd_source_update call each are timed beside it."""
+    from paper_2407_18304_gb300 import rhd, synth
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    seed = 1000 * (18304 + 2) + 1000 * rank
+    grids = synth.batched_grids(64, seed=seed, device=dev)
+    prec = rhd.FP64 if args.precision == "fp64" else rhd.MIXED
+    pristine = [synth.clone_state(g.state) for g in grids]
+    units1 = float(sum(g.n_cells * g.n_groups for g in grids))
+    stream = torch.cuda.current_stream()
+    ctx = rhd.Context()
+    specs = [rhd.GridSpec(g.state, g.edges, g.law, dt=g.dt, c_v=g.c_v, consts=g.consts,
+                          precision=prec) for g in grids]
+
+    def restore():
+        for g, p in zip(grids, pristine):
+            for k in ("mom", "egas", "erad", "frad"):
+                g.state[k].copy_(p[k])
+
+    def batched():
+        ctx.update(specs, stream=stream)
+
+    def per_grid():
+        for g in grids:
+            rhd.source_update(g.state, g.edges, g.law, dt=g.dt, c_v=g.c_v, consts=g.consts,
+                              precision=prec, stream=stream)
+
+    def timed(f, steps, warmup, sample_clocks=False):
+        for _ in range(warmup):
+            restore()
+            f()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        clocks = ClockSampler(dev.index)
+        if sample_clocks:
+            clocks.start()
+        barrier(ws)
+        torch.cuda.synchronize()
+        for a, b in ev:
+            restore()
+            a.record(stream)
+            f()
+            b.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+        clk = clocks.stop() if sample_clocks else None
+        return [a.elapsed_time(b) for a, b in ev], clk
+
+    restore()
+    shape = ctx.autotune(specs, stream=stream)  # untimed; leaves the state unchanged
+    ms, clk = timed(batched, args.steps, args.warmup, True)
+    t_max = allmax(sum(ms) / 1e3, ws)
+    total = allsum(units1 * args.steps, ws)
+    res = {"metric": METRIC, "value": total / t_max, "unit": UNIT, "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None,
+           "dtype": "f64" if prec == rhd.FP64 else "f32+f64",
+           "data": "synthetic (seeded; recipe in DESIGN.md)",
+           "config": {"workload": BATCHED, "grids": len(grids),
+                      "cells": int(sum(g.n_cells for g in grids)), "cell_groups": int(units1),
+                      "precision": args.precision, "tol": 1e-11, "tol_outer": 1e-13,
+                      "shape": {"threads": shape[0], "cells_per_item": shape[1]},
+                      "l2": "state restored from a pristine copy before each step (2x state > L2)",
+                      "parallelism": f"weak x{ws}, no collective"},
+           "gpu_launches": args.steps * 2, "clocks": clk}
+    pg, _ = timed(per_grid, max(1, args.fp64_steps), 1)
+    t_pg = allmax(sum(pg) / 1e3, ws)
+    res["per_grid_form"] = {"value": allsum(units1 * len(pg), ws) / t_pg,
+                            "ms_per_step": 1e3 * t_pg / len(pg)}
+    res["speedup_vs_per_grid"] = res["value"] / res["per_grid_form"]["value"]
+    bytes_alg = float(sum(g.n_cells * (g.n_groups * 64 + 82) for g in grids))
+    mean_s = sum(ms) / 1e3 / args.steps
+    peak = _measured_hbm()
+    res["roofline"] = {"bound": "hbm", "achieved": bytes_alg / mean_s / 1e9, "peak": peak,
+                       "unit": "GB/s", "frac": bytes_alg / mean_s / 1e9 / peak, "traffic": None,
+                       "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+                       "note": "algorithmic in+out bytes; the solve is FP64-issue bound"}
+    res["e2e"] = None
+    if rank == 0 and ws == 1:
+        res["cpu_baseline"] = cpu_baseline(args, grids[0])
+    return res
+
+
 def _measured_hbm() -> float:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -344,7 +436,12 @@ def run_reference(args, ws, rank):
     import oracle as O
     from paper_2407_18304_gb300 import synth
     m = min(args.cpu_sample // 4, 512)
-    w = synth.preset(args.workload, n_cells=m)
+    if args.workload == BATCHED:
+        g = synth.batched_grids(1, seed=1000 * (18304 + 2), max_side=16)[0]
+        m = min(m, g.n_cells)
+        w = synth.Workload(g.name, synth.take_cells(g.state, slice(0, m)), g.edges, g.law)
+    else:
+        w = synth.preset(args.workload, n_cells=m)
     km, al = O.group_table(w.edges, O.PPL_FIXED, w.law.nu_break, w.law.seg_logk, w.law.seg_beta,
                            w.law.nu_ref)
     p = O.Params(c=w.consts["c"], c_hat=w.consts["c_hat"], a_rad=w.consts["a_rad"],
@@ -376,6 +473,8 @@ def main():
                                                              int(os.environ.get("RANK", "0")))
     if args.impl == "reference":
         res = run_reference(args, ws, rank)
+    elif args.workload == BATCHED:
+        res = run_batched(args, ws, rank)
     else:
         res = run_ours(args, ws, rank)
     if rank == 0 and res is not None:

@@ -66,6 +66,11 @@ extern "C" {
                             the change of the v,F-terms of R_g is below tol_outer times
                             that group's own energy (the paper's test is relative to
                             E_tot, which leaves groups far below E_tot loosely converged) */
+#define RHD_FLUX_TEST 2  /* the outer iteration also stops only when the change of the
+                            group fluxes, sum_g |F_g,new - F_g,old|_1 / c, is below
+                            tol_outer E_tot (the paper's test sees F_g only through the
+                            v.F terms of R_g, so flux components normal to v can still be
+                            moving when it passes) */
 
 /* per-cell status codes written to rhd_state_t.status */
 #define RHD_STATUS_OK 0
@@ -99,7 +104,7 @@ typedef struct {
   int32_t max_outer;    /* outer-iteration cap; <= 0 selects 16 */
   int32_t precision;    /* RHD_FP64 | RHD_MIXED */
   int32_t closure;      /* RHD_M1 | RHD_EDDINGTON */
-  int32_t flags;        /* 0 (the paper's tests) or RHD_GROUP_TEST */
+  int32_t flags;        /* 0 (the paper's tests) or RHD_GROUP_TEST | RHD_FLUX_TEST */
 } rhd_state_t;
 
 /* Lab-frame group edges (Sec. 2.1, eq. Qg: contiguous groups).  HOST array of
@@ -139,6 +144,57 @@ typedef struct {
 int rhd_source_update(rhd_state_t *state, const rhd_groups_t *groups,
                       const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
                       void *stream);
+
+/* ---- Batched uneven grids --------------------------------------------------
+ * Many independent grids (own cell count, N_g <= RHD_MAX_GROUPS_BATCHED, own
+ * opacity law, dt and parameters) in one persistent launch: a device work queue
+ * hands (grid, cell-tile) items to the CTAs, each CTA keeps the group table of
+ * its current grid in shared memory, and every cell is solved by the same
+ * per-cell algorithm as rhd_source_update (the mixed form runs its FP32 and
+ * FP64 phases in the same thread).  The call is recorded once as a CUDA graph
+ * (descriptor upload, queue reset, table setup, solve) and replayed while the
+ * number of grids and work items is unchanged.  A context owns the workspace
+ * (descriptors, tables, queue head), the graph and the tuned launch shape; it
+ * is not thread-safe, and a call waits (host side) for the previous call of
+ * the same context to finish reading its host staging buffer.  The operation
+ * on each cell is the implicit source update of Sec. 3 (the same as
+ * rhd_source_update); batching several grids into one launch has no
+ * counterpart in the paper, which updates one patch at a time.
+ * Errors: RHD_EINVAL (null context or grids, n_grids < 1, grids of mixed
+ * precision, or a per-grid check of rhd_source_update failing), RHD_ESIZE
+ * (n_grids > RHD_MAX_GRIDS or a grid with more than RHD_MAX_GROUPS_BATCHED
+ * groups), RHD_ENOMEM, RHD_ECUDA; on any error nothing was launched. */
+#define RHD_MAX_GROUPS_BATCHED 64
+#define RHD_MAX_GRIDS 4096
+
+typedef struct rhd_context rhd_context_t;
+
+typedef struct {
+  rhd_state_t state;               /* as for rhd_source_update (group_stride allowed) */
+  rhd_groups_t groups;
+  rhd_opacity_law_t opacity_law;
+  double dt;
+  int64_t n_cells;
+} rhd_grid_t;
+
+/* Create / destroy a context on the current device.  The first batched call
+ * allocates the workspace (make it before any stream capture). */
+int rhd_context_create(rhd_context_t **ctx);
+int rhd_context_destroy(rhd_context_t *ctx);
+
+/* Advance every grid (in place).  All grids must use the same precision. */
+int rhd_source_update_batched(rhd_context_t *ctx, const rhd_grid_t *grids, int32_t n_grids,
+                              void *stream);
+
+/* Time every candidate launch shape (CTA size x cells per work item) on these
+ * grids and keep the fastest in the context.  The grids' state is saved to a
+ * temporary device copy first and restored after each candidate, so it is
+ * unchanged on return; the call synchronizes the stream. */
+int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids, int32_t n_grids,
+                         void *stream);
+
+/* The launch shape the context uses (threads per CTA, cells per work item). */
+int rhd_context_shape(const rhd_context_t *ctx, int32_t *threads, int32_t *cells_per_item);
 
 /* The mixed-precision form without any device allocation.  Some callers
  * cannot let a library call cudaMalloc: a host that hands every byte of HBM

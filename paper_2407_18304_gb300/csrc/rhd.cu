@@ -1,15 +1,18 @@
 // rhd.cu -- host side of the C ABI in include/rhd.h: argument checks, the
 // once-per-device constant tables, and the kernel launches.  The kernels are
-// in rhd_fp64.cuh (FP64 passes) and rhd_mixed.cuh (FP32 warm-start pass); this
-// is the only translation unit.
+// in rhd_fp64.cuh (FP64 passes), rhd_mixed.cuh (FP32 warm-start pass) and
+// rhd_batched.cuh (many grids, one persistent launch); this is the only
+// translation unit.
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <vector>
 
 #include "rhd_common.cuh"
 #include "rhd_fp64.cuh"
 #include "rhd_mixed.cuh"
+#include "rhd_batched.cuh"
 
 namespace rhd {
 namespace {
@@ -160,7 +163,7 @@ int pack(const rhd_state_t *s, const rhd_groups_t *gr, const rhd_opacity_law_t *
   if (!std::isfinite(dt) || dt < 0.0) return RHD_EINVAL;
   if (s->precision != RHD_FP64 && s->precision != RHD_MIXED) return RHD_EINVAL;
   if (s->closure != RHD_M1 && s->closure != RHD_EDDINGTON) return RHD_EINVAL;
-  if (s->flags & ~RHD_GROUP_TEST) return RHD_EINVAL;
+  if (s->flags & ~(RHD_GROUP_TEST | RHD_FLUX_TEST)) return RHD_EINVAL;
   if (law->mode != RHD_PPL_FIXED && law->mode != RHD_PC) return RHD_ELAW;
   // edges: strictly increasing; PPL needs finite positive edges
   for (int e = 0; e <= G; ++e) {
@@ -337,6 +340,286 @@ extern "C" int rhd_source_update_noalloc(rhd_state_t *state, const rhd_groups_t 
   if (kp.G <= 16) return rhd::launch_mixed<16>(kp, wo, wi, sms, st);
   if (kp.G <= 64) return rhd::launch_mixed<64>(kp, wo, wi, sms, st);
   return rhd::launch_mixed<rhd::kMaxG>(kp, wo, wi, sms, st);
+}
+
+// ---------------------------------------------------------------------------
+// Batched uneven grids
+// ---------------------------------------------------------------------------
+struct rhd_context {
+  int device = -1;
+  int threads = 128, cpi = 512;  // launch shape (autotuned)
+  int cap_grids = 0;
+  rhd::KParams *h_grids = nullptr, *d_grids = nullptr;
+  int64_t *h_off = nullptr, *d_off = nullptr;
+  double *d_tables = nullptr;
+  unsigned long long *d_head = nullptr;
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int sig_grids = -1, sig_threads = 0, sig_cpi = 0, sig_prec = -1;
+  int64_t sig_items = -1;
+  cudaEvent_t done = nullptr;
+  bool pending = false;
+};
+
+namespace rhd {
+namespace {
+
+constexpr int kMaxGB = RHD_MAX_GROUPS_BATCHED;
+const int64_t kTableWords = (int64_t)(sizeof(double) * (kTableArrays * kMaxGB + 1) +
+                                      sizeof(float) * (4 * kMaxGB + 1)) / sizeof(double) + 2;
+
+void ctx_free(rhd_context *c) {
+  if (c->exec) cudaGraphExecDestroy(c->exec);
+  if (c->h_grids) cudaFreeHost(c->h_grids);
+  if (c->h_off) cudaFreeHost(c->h_off);
+  if (c->d_grids) cudaFree(c->d_grids);
+  if (c->d_off) cudaFree(c->d_off);
+  if (c->d_tables) cudaFree(c->d_tables);
+  if (c->d_head) cudaFree(c->d_head);
+  c->exec = nullptr;
+  c->h_grids = c->d_grids = nullptr;
+  c->h_off = c->d_off = nullptr;
+  c->d_tables = nullptr;
+  c->d_head = nullptr;
+  c->cap_grids = 0;
+}
+
+int ctx_reserve(rhd_context *c, int n_grids) {
+  if (n_grids <= c->cap_grids) return RHD_OK;
+  if (c->pending) cudaEventSynchronize(c->done);
+  ctx_free(c);
+  int cap = 64;
+  while (cap < n_grids) cap *= 2;
+  if (cudaHostAlloc(&c->h_grids, sizeof(KParams) * cap, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&c->h_off, sizeof(int64_t) * (cap + 1), cudaHostAllocDefault) != cudaSuccess ||
+      cudaMalloc(&c->d_grids, sizeof(KParams) * cap) != cudaSuccess ||
+      cudaMalloc(&c->d_off, sizeof(int64_t) * (cap + 1)) != cudaSuccess ||
+      cudaMalloc(&c->d_tables, sizeof(double) * kTableWords * cap) != cudaSuccess ||
+      cudaMalloc(&c->d_head, sizeof(unsigned long long)) != cudaSuccess) {
+    ctx_free(c);
+    return RHD_ENOMEM;
+  }
+  c->cap_grids = cap;
+  return RHD_OK;
+}
+
+// Pack the grids into the pinned staging buffers; total work items out.
+int pack_batch(rhd_context *c, const rhd_grid_t *grids, int n_grids, int cpi, int *prec,
+               int64_t *total) {
+  int64_t acc = 0;
+  *prec = -1;
+  for (int j = 0; j < n_grids; ++j) {
+    const rhd_grid_t &g = grids[j];
+    const int rc = pack(&g.state, &g.groups, &g.opacity_law, g.dt, g.n_cells, &c->h_grids[j]);
+    if (rc != RHD_OK) return rc;
+    if (g.groups.n_groups > kMaxGB) return RHD_ESIZE;
+    if (*prec < 0) *prec = g.state.precision;
+    if (g.state.precision != *prec) return RHD_EINVAL;
+    c->h_off[j] = acc;
+    acc += (g.n_cells + cpi - 1) / cpi;
+  }
+  c->h_off[n_grids] = acc;
+  *total = acc;
+  return RHD_OK;
+}
+
+template <bool MIXED>
+cudaError_t enqueue_batch(rhd_context *c, int n_grids, int threads, int cpi, int sms,
+                          cudaStream_t st) {
+  cudaMemcpyAsync(c->d_grids, c->h_grids, sizeof(KParams) * n_grids, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(c->d_off, c->h_off, sizeof(int64_t) * (n_grids + 1), cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(c->d_head, 0, sizeof(unsigned long long), st);
+  tables_kernel<<<n_grids, 128, table_bytes(kMaxGB) + 64, st>>>(c->d_grids, c->d_tables,
+                                                                   kTableWords);
+  const size_t smem = table_bytes(kMaxGB) + 64;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<kMaxGB, MIXED>, threads,
+                                                    smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  batched_kernel<kMaxGB, MIXED><<<sms * per_sm, threads, smem, st>>>(
+      c->d_grids, c->d_tables, kTableWords, c->d_off, n_grids, cpi, c->d_head);
+  return cudaGetLastError();
+}
+
+cudaError_t enqueue_any(rhd_context *c, int prec, int n_grids, int threads, int cpi, int sms,
+                        cudaStream_t st) {
+  return prec == RHD_MIXED ? enqueue_batch<true>(c, n_grids, threads, cpi, sms, st)
+                           : enqueue_batch<false>(c, n_grids, threads, cpi, sms, st);
+}
+
+}  // namespace
+}  // namespace rhd
+
+extern "C" int rhd_context_create(rhd_context_t **ctx) {
+  if (!ctx) return RHD_EINVAL;
+  rhd_context *c = new (std::nothrow) rhd_context();
+  if (!c) return RHD_ENOMEM;
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess) {
+    delete c;
+    return RHD_ECUDA;
+  }
+  *ctx = c;
+  return RHD_OK;
+}
+
+extern "C" int rhd_context_destroy(rhd_context_t *ctx) {
+  if (!ctx) return RHD_EINVAL;
+  if (ctx->pending) cudaEventSynchronize(ctx->done);
+  rhd::ctx_free(ctx);
+  if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  if (ctx->done) cudaEventDestroy(ctx->done);
+  delete ctx;
+  return RHD_OK;
+}
+
+extern "C" int rhd_context_shape(const rhd_context_t *ctx, int32_t *threads,
+                                 int32_t *cells_per_item) {
+  if (!ctx || !threads || !cells_per_item) return RHD_EINVAL;
+  *threads = ctx->threads;
+  *cells_per_item = ctx->cpi;
+  return RHD_OK;
+}
+
+extern "C" int rhd_source_update_batched(rhd_context_t *ctx, const rhd_grid_t *grids,
+                                         int32_t n_grids, void *stream) {
+  if (!ctx || !grids || n_grids < 1) return RHD_EINVAL;
+  if (n_grids > RHD_MAX_GRIDS) return RHD_ESIZE;
+  int sms = 0;
+  int rc = rhd::ensure_device(&sms);
+  if (rc != RHD_OK) return rc;
+  // the previous call of this context may still read the staging buffers
+  if (ctx->pending) {
+    cudaEventSynchronize(ctx->done);
+    ctx->pending = false;
+  }
+  rc = rhd::ctx_reserve(ctx, n_grids);
+  if (rc != RHD_OK) return rc;
+  int prec = 0;
+  int64_t total = 0;
+  rc = rhd::pack_batch(ctx, grids, n_grids, ctx->cpi, &prec, &total);
+  if (rc != RHD_OK) return rc;
+  if (total == 0) return RHD_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool same = ctx->exec && ctx->sig_grids == n_grids && ctx->sig_items == total &&
+                    ctx->sig_threads == ctx->threads && ctx->sig_cpi == ctx->cpi &&
+                    ctx->sig_prec == prec;
+  if (!same) {
+    if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
+    ctx->exec = nullptr;
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+      return RHD_ECUDA;
+    const cudaError_t le = rhd::enqueue_any(ctx, prec, n_grids, ctx->threads, ctx->cpi, sms, ctx->cap);
+    const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);
+    if (le != cudaSuccess || ce != cudaSuccess || !graph) {
+      if (graph) cudaGraphDestroy(graph);
+      return RHD_ECUDA;
+    }
+    const cudaError_t ie = cudaGraphInstantiate(&ctx->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) {
+      ctx->exec = nullptr;
+      return RHD_ECUDA;
+    }
+    ctx->sig_grids = n_grids;
+    ctx->sig_items = total;
+    ctx->sig_threads = ctx->threads;
+    ctx->sig_cpi = ctx->cpi;
+    ctx->sig_prec = prec;
+  }
+  if (cudaGraphLaunch(ctx->exec, st) != cudaSuccess) return RHD_ECUDA;
+  if (cudaEventRecord(ctx->done, st) != cudaSuccess) return RHD_ECUDA;
+  ctx->pending = true;
+  return RHD_OK;
+}
+
+extern "C" int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids, int32_t n_grids,
+                                    void *stream) {
+  if (!ctx || !grids || n_grids < 1) return RHD_EINVAL;
+  if (n_grids > RHD_MAX_GRIDS) return RHD_ESIZE;
+  cudaStream_t st = (cudaStream_t)stream;
+  int sms = 0;
+  int rc = rhd::ensure_device(&sms);
+  if (rc != RHD_OK) return rc;
+  if (ctx->pending) {
+    cudaEventSynchronize(ctx->done);
+    ctx->pending = false;
+  }
+  rc = rhd::ctx_reserve(ctx, n_grids);
+  if (rc != RHD_OK) return rc;
+  // save the in/out arrays of every grid
+  struct Buf {
+    void *dst;
+    const void *src;
+    size_t bytes;
+  };
+  std::vector<Buf> bufs;
+  size_t total_bytes = 0;
+  for (int j = 0; j < n_grids; ++j) {
+    const rhd_grid_t &g = grids[j];
+    if (g.n_cells <= 0) continue;
+    const int64_t gs = g.state.group_stride ? g.state.group_stride : g.n_cells;
+    const size_t per = sizeof(double) * g.n_cells;
+    const size_t pg = sizeof(double) * ((int64_t)(g.groups.n_groups - 1) * gs + g.n_cells);
+    if (!g.state.egas || !g.state.erad) return RHD_EINVAL;
+    bufs.push_back({nullptr, g.state.egas, per});
+    for (int d = 0; d < 3; ++d) bufs.push_back({nullptr, g.state.mom[d], per});
+    bufs.push_back({nullptr, g.state.erad, pg});
+    for (int d = 0; d < 3; ++d) bufs.push_back({nullptr, g.state.frad[d], pg});
+  }
+  for (auto &b : bufs) total_bytes += (b.bytes + 255) & ~size_t(255);
+  char *save = nullptr;
+  if (cudaMalloc(&save, total_bytes) != cudaSuccess) return RHD_ENOMEM;
+  size_t off = 0;
+  for (auto &b : bufs) {
+    b.dst = save + off;
+    off += (b.bytes + 255) & ~size_t(255);
+    cudaMemcpyAsync(b.dst, b.src, b.bytes, cudaMemcpyDeviceToDevice, st);
+  }
+  auto restore = [&]() {
+    for (auto &b : bufs) cudaMemcpyAsync(const_cast<void *>(b.src), b.dst, b.bytes,
+                                         cudaMemcpyDeviceToDevice, st);
+  };
+  const int cand_threads[3] = {64, 128, 256};
+  const int cand_mult[3] = {1, 4, 16};
+  float best = 1e30f;
+  int bt = ctx->threads, bc = ctx->cpi;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  rc = RHD_OK;
+  for (int a = 0; a < 3 && rc == RHD_OK; ++a) {
+    for (int b = 0; b < 3 && rc == RHD_OK; ++b) {
+      const int th = cand_threads[a], cpi = th * cand_mult[b];
+      int prec = 0;
+      int64_t total = 0;
+      rc = rhd::pack_batch(ctx, grids, n_grids, cpi, &prec, &total);
+      if (rc != RHD_OK || total == 0) break;
+      cudaEventRecord(e0, st);
+      if (rhd::enqueue_any(ctx, prec, n_grids, th, cpi, sms, st) != cudaSuccess) rc = RHD_ECUDA;
+      cudaEventRecord(e1, st);
+      restore();
+      if (cudaStreamSynchronize(st) != cudaSuccess) rc = RHD_ECUDA;
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rc == RHD_OK && ms < best) {
+        best = ms;
+        bt = th;
+        bc = cpi;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(st);
+  cudaFree(save);
+  if (rc != RHD_OK) return rc;
+  ctx->threads = bt;
+  ctx->cpi = bc;
+  return RHD_OK;
 }
 
 extern "C" const char *rhd_strerror(int code) {

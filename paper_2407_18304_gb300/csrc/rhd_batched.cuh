@@ -1,0 +1,133 @@
+// rhd_batched.cuh -- many uneven grids in one persistent launch.
+//
+// A work item is (grid j, tile t): cells [t*cpi, (t+1)*cpi) of grid j.  The
+// items of all grids are numbered consecutively (item_off[j] is grid j's
+// first item), and a CTA takes the next item from a device counter
+// (atomicAdd; no waiting, so nothing can spin).  Converged cells retire as
+// soon as they are stored; the queue balances the uneven grids and the
+// uneven per-cell iteration counts across the CTAs.  Each CTA keeps the group
+// table of its current grid in shared memory and reloads it only when the
+// grid changes.  Per cell the algorithm is the single-grid one
+// (rhd_fp64.cuh, rhd_mixed.cuh).
+#pragma once
+#include "rhd_fp64.cuh"
+#include "rhd_mixed.cuh"
+
+namespace rhd {
+
+// The table arrays of build_table for G groups starting at sm.
+__device__ __forceinline__ GroupTable table_view(const double *sm, int G) {
+  const double *xe = sm, *kbar = sm + G + 1, *ikbar = kbar + G, *rm = ikbar + G, *rp = rm + G,
+               *alp = rp + G;
+  const float *xef = reinterpret_cast<const float *>(alp + G), *rmf = xef + G + 1, *rpf = rmf + G,
+              *alf = rpf + G;
+  return GroupTable{xe, kbar, ikbar, rm, rp, alp, xef, rmf, rpf, alf};
+}
+
+// One CTA per grid: build its table and write it to tables + j * stride.
+__global__ void tables_kernel(const KParams *__restrict__ grids, double *tables, int64_t stride) {
+  extern __shared__ double sm[];
+  const KParams &P = grids[blockIdx.x];
+  build_table(P, sm);
+  const int words = (int)(table_bytes(P.G) / sizeof(double)) + 1;
+  double *dst = tables + (int64_t)blockIdx.x * stride;
+  for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = sm[k];
+}
+
+// One cell, start to finish.  MIXED: the FP32 pass runs first and its
+// result is handed to the FP64 passes exactly as the two-launch form hands it
+// over through the workspace (same rounding of R and F to FP32), so both forms
+// give identical results.
+template <int MAXG, bool MIXED>
+__device__ __forceinline__ void solve_cell(const KParams &P, const GroupTable &tab, int64_t i,
+                                           Cell &C, Arr64<MAXG> &A, Arr32<MAXG> &B, Cell32 &D) {
+  bool warm = false;
+  double eint = 0.0, m[3] = {0.0, 0.0, 0.0};
+  int nit = 0;
+  if (MIXED && load_cell32(P, tab, i, C, D, B)) {
+    outer_begin32(P, C, D, B);
+    for (;;) {
+      const int r = inner_step32(P, tab, C, D, B);
+      if (r != 0 && outer_end32(P, tab, C, D, B)) break;
+    }
+    warm = true;
+    eint = C.Eint;
+    m[0] = C.m[0];
+    m[1] = C.m[1];
+    m[2] = C.m[2];
+    nit = C.nit > 255 ? 255 : C.nit;
+  }
+  if (!load_cell(P, i, C, A)) return;
+  set_tau(P, tab, C, A, C.chi0s);
+  if (warm) {
+    C.Eint = eint;
+    C.m[0] = m[0];
+    C.m[1] = m[1];
+    C.m[2] = m[2];
+    C.nit = nit;
+    const double fs = P.c * C.Etot;
+    for (int g = 0; g < P.G; ++g) {
+      A.R[g] = (double)B.R[g] * C.Etot;
+      A.Fk[3 * g] = (double)B.f[3 * g] * fs;
+      A.Fk[3 * g + 1] = (double)B.f[3 * g + 1] * fs;
+      A.Fk[3 * g + 2] = (double)B.f[3 * g + 2] * fs;
+    }
+  }
+  outer_begin(P, C, A);
+  for (;;) {
+    const int r = inner_step(P, tab, C, A);
+    if (r == 0) continue;
+    if (r == 2) C.stat = RHD_STATUS_MAXITER;
+    if (outer_end(P, tab, C, A)) break;
+  }
+  store_cell(P, C, A);
+}
+
+template <int MAXG, bool MIXED>
+__global__ void batched_kernel(const KParams *__restrict__ grids, const double *__restrict__ tables,
+                               int64_t table_stride, const int64_t *__restrict__ item_off,
+                               int n_grids, int cpi, unsigned long long *head) {
+  extern __shared__ double sm[];
+  __shared__ long long s_item;
+  __shared__ int s_grid;
+  const long long total = item_off[n_grids];
+  int cur = -1;
+  GroupTable tab;
+  Arr64<MAXG> A;
+  Arr32<MAXG> B;
+  Cell C;
+  Cell32 D;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const long long it = (long long)atomicAdd(head, 1ULL);
+      int lo = 0, hi = n_grids;  // grid j with item_off[j] <= it < item_off[j+1]
+      while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (item_off[mid] <= it) lo = mid;
+        else hi = mid;
+      }
+      s_item = it;
+      s_grid = lo;
+    }
+    __syncthreads();
+    const long long item = s_item;
+    const int j = s_grid;
+    if (item >= total) break;
+    const KParams &P = grids[j];
+    if (j != cur) {
+      const int words = (int)(table_bytes(P.G) / sizeof(double)) + 1;
+      const double *src = tables + (int64_t)j * table_stride;
+      for (int k = threadIdx.x; k < words; k += blockDim.x) sm[k] = src[k];
+      cur = j;
+      tab = table_view(sm, P.G);
+    }
+    __syncthreads();
+    const int64_t c0 = (item - item_off[j]) * (int64_t)cpi;
+    const int64_t c1 = c0 + cpi < P.n ? c0 + cpi : P.n;
+    for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x)
+      solve_cell<MAXG, MIXED>(P, tab, i, C, A, B, D);
+    __syncthreads();  // s_item, s_grid and the table are reused by the next item
+  }
+}
+
+}  // namespace rhd

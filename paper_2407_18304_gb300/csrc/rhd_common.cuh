@@ -246,4 +246,120 @@ __device__ __forceinline__ void closure_vP(int closure, R c, R E, R F0, R F1, R 
   o2 = E * (iso * v2 + vn * n2);
 }
 
+// v . P_g and M = d(v . P_g)/dF_g at fixed E_g for the M1 closure of
+// closure_vP (Levermore's Eddington factor chi(f), f = |F|/(cE) held at 1):
+// with n = F/|F|, vn = v . n,
+//   v . P = E [iso v + dir vn n],  iso = (1 - chi)/2,  dir = (3 chi - 1)/2,
+//   M = (iso'/c) v n^T + (dir'/c) vn n n^T
+//       + (E dir/|F|) [n (v - vn n)^T + vn (I - n n^T)],
+// iso' = -chi'/2, dir' = 3 chi'/2 (chi' = 0 where f is held at 1).  F = 0
+// gives P = E/3 I and M = 0 (dir vanishes like f^2).
+template <typename R>
+__device__ __forceinline__ void closure_vP_jac(R c, R E, const R F[3], const R v[3], R vP[3],
+                                               R M[9]) {
+  const R fn2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+  if (!(E > R(0)) || !(fn2 > R(0))) {
+    for (int k = 0; k < 3; ++k) vP[k] = E * v[k] * (R(1) / R(3));
+    for (int k = 0; k < 9; ++k) M[k] = R(0);
+    return;
+  }
+  const R fn = sqrt(fn2), inv = R(1) / fn;
+  R f = fn / (c * E);
+  const bool held = f > R(1);
+  if (held) f = R(1);
+  const R f2 = f * f;
+  const R sq = sqrt(R(4) - R(3) * f2), num = R(3) + R(4) * f2, den = R(5) + R(2) * sq;
+  const R chi = num / den;
+  const R dchi = held ? R(0) : (R(8) * f * den + R(6) * f * num / sq) / (den * den);
+  const R iso = R(0.5) * (R(1) - chi), dir = R(0.5) * (R(3) * chi - R(1));
+  const R n[3] = {F[0] * inv, F[1] * inv, F[2] * inv};
+  const R vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  const R a = -R(0.5) * dchi / c, b = R(1.5) * dchi * vn / c, e = E * dir * inv;
+  for (int r = 0; r < 3; ++r) {
+    vP[r] = E * (iso * v[r] + dir * vn * n[r]);
+    for (int q = 0; q < 3; ++q) {
+      const R id = r == q ? R(1) : R(0);
+      M[3 * r + q] = a * v[r] * n[q] + b * n[r] * n[q] + e * (n[r] * (v[q] - vn * n[q]) +
+                                                               vn * (id - n[r] * n[q]));
+    }
+  }
+}
+
+template <typename R>
+struct Vec3 {
+  R x, y, z;
+};
+
+// Sum of the flux changes of a Newton flux pass (x, y, z) and of their
+// absolute values (l1).
+struct FluxDelta {
+  double x, y, z, l1;
+};
+
+// Newton steps of flux_update from F (kept out of line: taken by few groups,
+// and inlined it would raise the register count of the whole solve loop;
+// scalars in and out, so that nothing of the caller has to leave registers).
+template <typename R>
+__device__ __noinline__ Vec3<R> flux_newton(R c, R E, R kap, R b0, R b1, R b2, R v0, R v1, R v2,
+                                            R F0, R F1, R F2, R eps) {
+  const R base[3] = {b0, b1, b2}, v[3] = {v0, v1, v2};
+  R F[3] = {F0, F1, F2}, vP[3], M[9];
+  const Vec3<R> keep = {F0, F1, F2};
+  for (int it = 0; it < 8; ++it) {
+    closure_vP_jac<R>(c, E, F, v, vP, M);
+    const R r0 = F[0] - base[0] - kap * vP[0], r1 = F[1] - base[1] - kap * vP[1],
+            r2 = F[2] - base[2] - kap * vP[2];
+    // the scale includes the terms that cancel in r (base against kap v.P)
+    const R sc = c * E + fmax(fabs(F[0]), fmax(fabs(F[1]), fabs(F[2]))) +
+                 fmax(fabs(base[0]), fmax(fabs(base[1]), fabs(base[2]))) +
+                 fabs(kap) * fmax(fabs(vP[0]), fmax(fabs(vP[1]), fabs(vP[2])));
+    if (fmax(fabs(r0), fmax(fabs(r1), fabs(r2))) <= eps * sc) break;
+    // J = I - kap M; d = J^-1 r by the adjugate
+    const R j00 = R(1) - kap * M[0], j01 = -kap * M[1], j02 = -kap * M[2];
+    const R j10 = -kap * M[3], j11 = R(1) - kap * M[4], j12 = -kap * M[5];
+    const R j20 = -kap * M[6], j21 = -kap * M[7], j22 = R(1) - kap * M[8];
+    const R c00 = j11 * j22 - j12 * j21, c01 = j12 * j20 - j10 * j22, c02 = j10 * j21 - j11 * j20;
+    const R idet = R(1) / (j00 * c00 + j01 * c01 + j02 * c02);
+    const R d0 = (c00 * r0 + (j02 * j21 - j01 * j22) * r1 + (j01 * j12 - j02 * j11) * r2) * idet;
+    const R d1 = (c01 * r0 + (j00 * j22 - j02 * j20) * r1 + (j02 * j10 - j00 * j12) * r2) * idet;
+    const R d2 = (c02 * r0 + (j01 * j20 - j00 * j21) * r1 + (j00 * j11 - j01 * j10) * r2) * idet;
+    if (!(isfinite(d0) && isfinite(d1) && isfinite(d2))) return keep;  // the eq. numF1 value
+    F[0] -= d0;
+    F[1] -= d1;
+    F[2] -= d2;
+    if (fmax(fabs(d0), fmax(fabs(d1), fabs(d2))) <= eps * sc) break;  // quadratic: done
+  }
+  if (!(isfinite(F[0]) && isfinite(F[1]) && isfinite(F[2]))) return keep;
+  return Vec3<R>{F[0], F[1], F[2]};
+}
+
+// Flux update of one group, eq. fupdate with P_g at the new flux:
+//   F = base + kap (v . P_g(E, F)),
+//   base = (F^t + c_hat theta dt v src_g) / (1 + c_hat chi_F theta dt),
+//   kap = c_hat theta dt (1 + alpha) chi_E / (1 + c_hat chi_F theta dt).
+// F holds the lagged flux on entry.  The first step takes P_g at the lagged
+// flux (eq. numF1).  Repeating that step contracts by at most 5 |kap| |v| / c
+// per outer pass (|M| <= 5 |v| / c), and where v chi_E / chi_F is of order c
+// it oscillates around the solution for hundreds of passes; so in a cell whose
+// outer iteration has been seen to contract slowly (slow), for the groups
+// where the bound exceeds 1/2 (M1 closure only: the Eddington P_g does not
+// depend on F), Newton steps on the closure's dependence on F follow (flux_newton: at most
+// 8, stopped once the residual F - base - kap v.P or the last step is below
+// eps times the size of the terms; a non-finite step keeps the eq. numF1
+// value).  Both forms have the same fixed point.
+template <typename R>
+__device__ __forceinline__ void flux_update(int closure, R c, R E, R kap, const R base[3],
+                                            const R v[3], R vmag, R F[3], R eps, bool slow) {
+  R vP[3];
+  closure_vP<R>(closure, c, E, F[0], F[1], F[2], v[0], v[1], v[2], vP[0], vP[1], vP[2]);
+  for (int k = 0; k < 3; ++k) F[k] = base[k] + kap * vP[k];
+  if (slow && closure == RHD_M1 && R(10) * fabs(kap) * vmag > c) {
+    const Vec3<R> r = flux_newton<R>(c, E, kap, base[0], base[1], base[2], v[0], v[1], v[2],
+                                     F[0], F[1], F[2], eps);
+    F[0] = r.x;
+    F[1] = r.y;
+    F[2] = r.z;
+  }
+}
+
 }  // namespace rhd

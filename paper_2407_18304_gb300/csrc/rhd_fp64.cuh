@@ -65,7 +65,9 @@ struct Cell {
   double egas_new; // written-back total gas energy
   double cs;       // rho kappa0 (T/T_ref)^p of the last evaluation
   double its;      // 1 / (c_hat theta dt cs)
+  double chg_prev; // outer-test change of the previous pass
   int nit, stat, it, outer;
+  int slow;        // the outer iteration contracted slowly: Newton flux steps on
 };
 
 // Thread-local per-group arrays of the FP64 passes.
@@ -123,6 +125,8 @@ __device__ __forceinline__ bool load_cell(const KParams &P, int64_t i, Cell &C, 
   C.stat = RHD_STATUS_OK;
   C.outer = 0;
   C.it = 0;
+  C.chg_prev = HUGE_VAL;
+  C.slow = 0;
   return true;
 }
 
@@ -240,6 +244,42 @@ __device__ __forceinline__ int inner_step(const KParams &P, const GroupTable &ta
 // a9-a12 after an inner solve: write-back, flux and momentum update, outer
 // test.  Returns true when the cell is done (converged or at a cap); else the
 // next outer pass has been set up.
+// The Newton part of flux_update for the groups whose eq. numF1 step
+// contracts by less than 1/2 per outer pass.  Fk holds the eq. numF1 values
+// and is updated; returns the change of their sum and its l1 size.  Out of
+// line (few cells take it) with scalar and array arguments only, so that the
+// caller's cell state stays in registers.
+__device__ __noinline__ FluxDelta flux_newton_pass(
+    int G, int64_t i, int64_t gs, const double *erad, const double *src, const double *ft0p,
+    const double *ft1p, const double *ft2p, const double *kbar, const double *alpha,
+    const double *R, const double *bq, const double *dnx, const double *qF, double *Fk, double c,
+    double tdt, double cs, double v0, double v1, double v2) {
+  const double vmag = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
+  FluxDelta d = {0.0, 0.0, 0.0, 0.0};
+  for (int g = 0; g < G; ++g) {
+    const int64_t o = (int64_t)g * gs + i;
+    const double chiB = cs * kbar[g];
+    const double inv = 1.0 / (1.0 + tdt * chiB * qF[g]);
+    const double kap = tdt * (1.0 + alpha[g]) * chiB * inv;
+    if (!(10.0 * fabs(kap) * vmag > c)) continue;
+    const double s = src ? src[o] : 0.0;
+    const double Enew = erad[o] + R[g] + s;
+    const double srcg = chiB * (bq[g] - dnx[g] * (1.0 / 3.0));
+    const Vec3<double> F = flux_newton<double>(
+        c, Enew, kap, (ft0p[o] + tdt * v0 * srcg) * inv, (ft1p[o] + tdt * v1 * srcg) * inv,
+        (ft2p[o] + tdt * v2 * srcg) * inv, v0, v1, v2, Fk[3 * g], Fk[3 * g + 1], Fk[3 * g + 2],
+        1e-14);
+    d.x += F.x - Fk[3 * g];
+    d.y += F.y - Fk[3 * g + 1];
+    d.z += F.z - Fk[3 * g + 2];
+    d.l1 += fabs(F.x - Fk[3 * g]) + fabs(F.y - Fk[3 * g + 1]) + fabs(F.z - Fk[3 * g + 2]);
+    Fk[3 * g] = F.x;
+    Fk[3 * g + 1] = F.y;
+    Fk[3 * g + 2] = F.z;
+  }
+  return d;
+}
+
 template <int MAXG>
 __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &tab, Cell &C,
                                           Arr64<MAXG> &A) {
@@ -257,9 +297,14 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
   for (int g = 0; g < G; ++g) sumR += A.R[g];
   C.egas_new = C.eg0 - cr * sumR;
 
-  // ---- a10: flux update eq. numF1 (outdated velocity v_k)
+  // ---- a10: flux update, eq. fupdate (outdated velocity v_k): eq. numF1 for
+  // every group, then flux_newton_pass where the closure's dependence on F
+  // needs it (see flux_update)
   const double *v = C.v;
+  const double vmag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
   double dF[3] = {0.0, 0.0, 0.0};
+  double fchg = 0.0;  // sum_g |F_g,new - F_g,old|_1 (RHD_FLUX_TEST)
+  bool newton = false;
   for (int g = 0; g < G; ++g) {
     const int64_t o = (int64_t)g * P.gs + i;
     const double s = P.src ? P.src[o] : 0.0;
@@ -269,18 +314,29 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
     closure_vP<double>(P.closure, c, Enew, A.Fk[3 * g], A.Fk[3 * g + 1], A.Fk[3 * g + 2], v[0],
                        v[1], v[2], vp0, vp1, vp2);
     const double srcg = chiB * (A.bq[g] - A.dnx[g] * (1.0 / 3.0));
-    const double kP = (1.0 + a) * chiB;
     const double inv = 1.0 / (1.0 + tdt * chiB * A.qF[g]);
+    const double kap = tdt * (1.0 + a) * chiB * inv;
+    newton = newton || 10.0 * fabs(kap) * vmag > c;
     const double ft0 = P.frad[0][o], ft1 = P.frad[1][o], ft2 = P.frad[2][o];
-    const double n0 = (ft0 + tdt * (v[0] * srcg + kP * vp0)) * inv;
-    const double n1 = (ft1 + tdt * (v[1] * srcg + kP * vp1)) * inv;
-    const double n2 = (ft2 + tdt * (v[2] * srcg + kP * vp2)) * inv;
+    const double n0 = (ft0 + tdt * v[0] * srcg) * inv + kap * vp0;
+    const double n1 = (ft1 + tdt * v[1] * srcg) * inv + kap * vp1;
+    const double n2 = (ft2 + tdt * v[2] * srcg) * inv + kap * vp2;
     dF[0] += n0 - ft0;
     dF[1] += n1 - ft1;
     dF[2] += n2 - ft2;
+    fchg += fabs(n0 - A.Fk[3 * g]) + fabs(n1 - A.Fk[3 * g + 1]) + fabs(n2 - A.Fk[3 * g + 2]);
     A.Fk[3 * g] = n0;
     A.Fk[3 * g + 1] = n1;
     A.Fk[3 * g + 2] = n2;
+  }
+  if (newton && C.slow && P.closure == RHD_M1) {
+    const FluxDelta d =
+        flux_newton_pass(G, i, P.gs, P.erad, P.src, P.frad[0], P.frad[1], P.frad[2], tab.kbar,
+                         tab.alpha, A.R, A.bq, A.dnx, A.qF, A.Fk, c, tdt, C.cs, v[0], v[1], v[2]);
+    dF[0] += d.x;
+    dF[1] += d.y;
+    dF[2] += d.z;
+    fchg += d.l1;
   }
   // ---- a11: momentum update
   const double mn[3] = {C.m0[0] - dF[0] * icc, C.m0[1] - dF[1] * icc, C.m0[2] - dF[2] * icc};
@@ -290,7 +346,7 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
   // moves T = (E_gas - E_kin)/(rho c_v) and with it every term of R_g
   const double vn[3] = {mn[0] / rho, mn[1] / rho, mn[2] / rho};
   const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho;
-  double chg = fabs(KEn - C.KE);
+  double chg = fabs(KEn - C.KE) + ((P.flags & RHD_FLUX_TEST) ? fchg / c : 0.0);
   bool gok = true;
   for (int g = 0; g < G; ++g) {
     const double wn =
@@ -307,6 +363,10 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
   C.m[0] = mn[0];
   C.m[1] = mn[1];
   C.m[2] = mn[2];
+  // a pass that removed less than 3/4 of the previous change turns the
+  // Newton flux steps on for the rest of this cell's passes
+  if (C.outer >= 1 && chg > 0.25 * C.chg_prev) C.slow = 1;
+  C.chg_prev = chg;
   ++C.outer;
   if (chg <= P.tol_outer * C.Etot && gok) return true;
   if (C.outer >= P.max_outer) {

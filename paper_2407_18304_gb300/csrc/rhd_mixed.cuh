@@ -145,6 +145,8 @@ __device__ __forceinline__ bool load_cell32(const KParams &P, const GroupTable &
   C.Eint = C.eg0 - KE0;
   C.nit = 0;
   C.outer = 0;
+  C.chg_prev = HUGE_VAL;
+  C.slow = 0;
   D.sE = 1.0 / C.Etot;
   const double fs = D.sE / P.c;
   for (int g = 0; g < G; ++g) {
@@ -258,24 +260,24 @@ __device__ __forceinline__ bool outer_end32(const KParams &P, const GroupTable &
   for (int g = 0; g < G; ++g) sR += B.R[g];
   const double egas_new = C.eg0 - (double)cr * (double)sR * Etot;
   float df[3] = {0.0f, 0.0f, 0.0f};
+  const float bmag = sqrtf(D.be[0] * D.be[0] + D.be[1] * D.be[1] + D.be[2] * D.be[2]);
   for (int g = 0; g < G; ++g) {
     const float En = B.e0[g] + B.R[g];
-    float vp0, vp1, vp2;
-    closure_vP<float>(P.closure, 1.0f, En, B.f[3 * g], B.f[3 * g + 1], B.f[3 * g + 2], D.be[0],
-                      D.be[1], D.be[2], vp0, vp1, vp2);
     const float t = B.tau[g], a = tab.alphaf[g];
     const float srcg = t * (B.b[g] - B.dnx[g] * (1.0f / 3.0f));
-    const float kP = (1.0f + a) * t;
     const float inv = 1.0f / (1.0f + t * B.q[g]);
-    const float n0 = (B.ft[3 * g] + D.be[0] * srcg + kP * vp0) * inv;
-    const float n1 = (B.ft[3 * g + 1] + D.be[1] * srcg + kP * vp1) * inv;
-    const float n2 = (B.ft[3 * g + 2] + D.be[2] * srcg + kP * vp2) * inv;
-    df[0] += n0 - B.ft[3 * g];
-    df[1] += n1 - B.ft[3 * g + 1];
-    df[2] += n2 - B.ft[3 * g + 2];
-    B.f[3 * g] = n0;
-    B.f[3 * g + 1] = n1;
-    B.f[3 * g + 2] = n2;
+    const float base[3] = {(B.ft[3 * g] + D.be[0] * srcg) * inv,
+                           (B.ft[3 * g + 1] + D.be[1] * srcg) * inv,
+                           (B.ft[3 * g + 2] + D.be[2] * srcg) * inv};
+    const float kap = (1.0f + a) * t * inv;
+    float F[3] = {B.f[3 * g], B.f[3 * g + 1], B.f[3 * g + 2]};
+    flux_update<float>(P.closure, 1.0f, En, kap, base, D.be, bmag, F, 1e-6f, C.slow != 0);
+    df[0] += F[0] - B.ft[3 * g];
+    df[1] += F[1] - B.ft[3 * g + 1];
+    df[2] += F[2] - B.ft[3 * g + 2];
+    B.f[3 * g] = F[0];
+    B.f[3 * g + 1] = F[1];
+    B.f[3 * g + 2] = F[2];
   }
   const double mf = Etot / chat;  // (c E_tot)/(c c_hat)
   const double mn[3] = {C.m0[0] - mf * df[0], C.m0[1] - mf * df[1], C.m0[2] - mf * df[2]};
@@ -291,6 +293,8 @@ __device__ __forceinline__ bool outer_end32(const KParams &P, const GroupTable &
   C.m[0] = mn[0];
   C.m[1] = mn[1];
   C.m[2] = mn[2];
+  if (C.outer >= 1 && chg > 0.25f * (float)C.chg_prev) C.slow = 1;  // as in outer_end
+  C.chg_prev = chg;
   C.Eint = egas_new - KEn;  // start of the next pass (or of the FP64 phase)
   if (!(C.Eint > 0.0)) C.Eint = C.eg0 - C.KE;
   ++C.outer;

@@ -19,6 +19,7 @@ M1, EDDINGTON = 0, 1
 PPL_FIXED, PC = 0, 1
 STATUS_OK, STATUS_FALLBACK, STATUS_MAXITER, STATUS_INVALID = 0, 1, 2, 3
 GROUP_TEST = 1
+FLUX_TEST = 2
 MAX_GROUPS = 256
 NOALLOC_BYTES = 64 << 20
 
@@ -46,6 +47,11 @@ class OpacityLaw(ctypes.Structure):
                 ("seg_beta", ctypes.POINTER(_D)), ("nu_ref", _D),
                 ("khat_gminus", ctypes.POINTER(_D)), ("alpha_g", ctypes.POINTER(_D)),
                 ("temp_exponent", _D), ("T_ref", _D)]
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("state", State), ("groups", Groups), ("opacity_law", OpacityLaw), ("dt", _D),
+                ("n_cells", ctypes.c_int64)]
 
 
 class RhdError(RuntimeError):
@@ -77,6 +83,17 @@ def lib() -> ctypes.CDLL:
         _lib.rhd_source_update_noalloc.argtypes = [ctypes.POINTER(State), ctypes.POINTER(Groups),
                                                    ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64,
                                                    _P]
+        _lib.rhd_context_create.restype = ctypes.c_int
+        _lib.rhd_context_create.argtypes = [ctypes.POINTER(_P)]
+        _lib.rhd_context_destroy.restype = ctypes.c_int
+        _lib.rhd_context_destroy.argtypes = [_P]
+        _lib.rhd_source_update_batched.restype = ctypes.c_int
+        _lib.rhd_source_update_batched.argtypes = [_P, ctypes.POINTER(Grid), ctypes.c_int32, _P]
+        _lib.rhd_context_autotune.restype = ctypes.c_int
+        _lib.rhd_context_autotune.argtypes = [_P, ctypes.POINTER(Grid), ctypes.c_int32, _P]
+        _lib.rhd_context_shape.restype = ctypes.c_int
+        _lib.rhd_context_shape.argtypes = [_P, ctypes.POINTER(ctypes.c_int32),
+                                           ctypes.POINTER(ctypes.c_int32)]
         _lib.rhd_strerror.restype = ctypes.c_char_p
         _lib.rhd_strerror.argtypes = [ctypes.c_int]
         _lib.rhd_version.restype = ctypes.c_int
@@ -121,24 +138,11 @@ def make_law(law, mode: int = PPL_FIXED, khat_g=None, alpha_g=None, temp_exponen
     return s, keep
 
 
-def source_update(state: dict, edges, law, *, dt: float, c_v: float, consts: dict,
-                  theta: float = 1.0, precision: int = FP64, closure: int = M1,
-                  tol: float = 0.0, tol_outer: float = 0.0, max_newton: int = 0,
-                  max_outer: int = 0, status: torch.Tensor | None = None,
-                  iters: torch.Tensor | None = None, mode: int = PPL_FIXED, khat_g=None,
-                  alpha_g=None, temp_exponent: float = 0.0, T_ref: float = 1.0,
-                  stream: torch.cuda.Stream | None = None, n_cells: int | None = None,
-                  group_stride: int = 0, flags: int = 0) -> None:
-    """In-place implicit source-term update of one grid (see include/rhd.h).
-
-    ``state`` holds CUDA float64 tensors: rho [n], mom [3, n], egas [n],
-    kappa0 [n] or None, erad [G, n], frad [3, G, n], src [G, n] or None.
-    ``law`` has nu_break, seg_logk, seg_beta, nu_ref (piecewise powerlaw)."""
+def _state(state: dict, G: int, n: int, gs: int, *, c_v: float, consts: dict, theta: float,
+           precision: int, closure: int, tol: float, tol_outer: float, max_newton: int,
+           max_outer: int, status, iters, flags: int) -> State:
+    """Check the tensors of one grid and fill the C state struct."""
     rho = state["rho"]
-    n = rho.shape[0] if n_cells is None else n_cells
-    e = np.ascontiguousarray(edges, dtype=np.float64)
-    G = len(e) - 1
-    gs = group_stride or rho.shape[0]
     _check(rho, "rho", (rho.shape[0],))
     _check(state["mom"], "mom", (3, rho.shape[0]))
     _check(state["egas"], "egas", (rho.shape[0],))
@@ -171,6 +175,30 @@ def source_update(state: dict, edges, law, *, dt: float, c_v: float, consts: dic
     st.tol, st.tol_outer = float(tol), float(tol_outer)
     st.max_newton, st.max_outer = int(max_newton), int(max_outer)
     st.precision, st.closure, st.flags = int(precision), int(closure), int(flags)
+    return st
+
+
+def source_update(state: dict, edges, law, *, dt: float, c_v: float, consts: dict,
+                  theta: float = 1.0, precision: int = FP64, closure: int = M1,
+                  tol: float = 0.0, tol_outer: float = 0.0, max_newton: int = 0,
+                  max_outer: int = 0, status: torch.Tensor | None = None,
+                  iters: torch.Tensor | None = None, mode: int = PPL_FIXED, khat_g=None,
+                  alpha_g=None, temp_exponent: float = 0.0, T_ref: float = 1.0,
+                  stream: torch.cuda.Stream | None = None, n_cells: int | None = None,
+                  group_stride: int = 0, flags: int = 0) -> None:
+    """In-place implicit source-term update of one grid (see include/rhd.h).
+
+    ``state`` holds CUDA float64 tensors: rho [n], mom [3, n], egas [n],
+    kappa0 [n] or None, erad [G, n], frad [3, G, n], src [G, n] or None.
+    ``law`` has nu_break, seg_logk, seg_beta, nu_ref (piecewise powerlaw)."""
+    rho = state["rho"]
+    n = rho.shape[0] if n_cells is None else n_cells
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    G = len(e) - 1
+    gs = group_stride or rho.shape[0]
+    st = _state(state, G, n, gs, c_v=c_v, consts=consts, theta=theta, precision=precision,
+                closure=closure, tol=tol, tol_outer=tol_outer, max_newton=max_newton,
+                max_outer=max_outer, status=status, iters=iters, flags=flags)
     gr = Groups(G, _dp(e))
     lw, keep = make_law(law, mode, khat_g, alpha_g, temp_exponent, T_ref)
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -234,6 +262,87 @@ def source_update_noalloc(state: dict, edges, law, *, dt: float, c_v: float, con
     del keep
     if rc != 0:
         raise RhdError(rc, lib().rhd_strerror(rc).decode())
+
+
+MAX_GROUPS_BATCHED = 64
+MAX_GRIDS = 4096
+
+
+def _raise(rc: int) -> None:
+    if rc != 0:
+        raise RhdError(rc, lib().rhd_strerror(rc).decode())
+
+
+class GridSpec:
+    """One grid of a batched call: the C descriptor plus the host arrays it
+    points to (kept alive here)."""
+
+    def __init__(self, state: dict, edges, law, *, dt: float, c_v: float, consts: dict,
+                 theta: float = 1.0, precision: int = MIXED, closure: int = M1, tol: float = 0.0,
+                 tol_outer: float = 0.0, max_newton: int = 0, max_outer: int = 0,
+                 status: torch.Tensor | None = None, iters: torch.Tensor | None = None,
+                 mode: int = PPL_FIXED, khat_g=None, alpha_g=None, temp_exponent: float = 0.0,
+                 T_ref: float = 1.0, flags: int = 0):
+        n = state["rho"].shape[0]
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        G = len(e) - 1
+        st = _state(state, G, n, n, c_v=c_v, consts=consts, theta=theta, precision=precision,
+                    closure=closure, tol=tol, tol_outer=tol_outer, max_newton=max_newton,
+                    max_outer=max_outer, status=status, iters=iters, flags=flags)
+        lw, keep = make_law(law, mode, khat_g, alpha_g, temp_exponent, T_ref)
+        self.keep = keep + [e]
+        self.state = state
+        self.c = Grid(st, Groups(G, _dp(e)), lw, float(dt), int(n))
+
+
+class Context:
+    """A batched-update context (``rhd_context_t``): staging buffers, the
+    captured CUDA graph and the tuned launch shape, reused across calls."""
+
+    def __init__(self):
+        h = _P()
+        _raise(lib().rhd_context_create(ctypes.byref(h)))
+        self._h = h
+
+    def close(self) -> None:
+        if self._h is not None and self._h.value:
+            _raise(lib().rhd_context_destroy(self._h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _array(grids):
+        arr = (Grid * len(grids))()
+        for k, g in enumerate(grids):
+            arr[k] = g.c
+        return arr
+
+    def update(self, grids: list, stream: torch.cuda.Stream | None = None) -> None:
+        """In-place update of every grid in one persistent launch."""
+        s = stream if stream is not None else torch.cuda.current_stream()
+        arr = self._array(grids)
+        _raise(lib().rhd_source_update_batched(self._h, arr, len(grids),
+                                               ctypes.c_void_p(s.cuda_stream)))
+
+    def autotune(self, grids: list, stream: torch.cuda.Stream | None = None) -> tuple[int, int]:
+        """Time the launch shapes on these grids (their state is left as it
+        was) and keep the fastest; returns (threads, cells_per_item)."""
+        s = stream if stream is not None else torch.cuda.current_stream()
+        arr = self._array(grids)
+        _raise(lib().rhd_context_autotune(self._h, arr, len(grids),
+                                          ctypes.c_void_p(s.cuda_stream)))
+        return self.shape
+
+    @property
+    def shape(self) -> tuple[int, int]:
+        t, c = ctypes.c_int32(), ctypes.c_int32()
+        _raise(lib().rhd_context_shape(self._h, ctypes.byref(t), ctypes.byref(c)))
+        return t.value, c.value
 
 
 def strerror(code: int) -> str:

@@ -67,3 +67,21 @@ def test_argument_checks_without_a_device(lib):
     assert _call(lib, edges, n_cells=5) == -1
     assert rhd.strerror(-2) == "invalid group edges"
     assert lib.rhd_version() >= 100
+
+
+def test_batched_entry_points_reject_null_arguments_without_a_device(lib):
+    grids = (rhd.Grid * 1)()
+    assert lib.rhd_source_update_batched(None, grids, 1, None) == -1
+    assert lib.rhd_context_autotune(None, grids, 1, None) == -1
+    assert lib.rhd_context_destroy(None) == -1
+    assert lib.rhd_context_create(None) == -1
+    t, c = ctypes.c_int32(), ctypes.c_int32()
+    assert lib.rhd_context_shape(None, ctypes.byref(t), ctypes.byref(c)) == -1
+
+
+def test_grid_struct_matches_the_c_layout():
+    # rhd_grid_t = {rhd_state_t, rhd_groups_t, rhd_opacity_law_t, double, int64_t}
+    assert rhd.Grid.groups.offset == ctypes.sizeof(rhd.State)
+    assert rhd.Grid.opacity_law.offset == ctypes.sizeof(rhd.State) + ctypes.sizeof(rhd.Groups)
+    assert ctypes.sizeof(rhd.Grid) == (ctypes.sizeof(rhd.State) + ctypes.sizeof(rhd.Groups)
+                                       + ctypes.sizeof(rhd.OpacityLaw) + 16)

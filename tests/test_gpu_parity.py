@@ -239,3 +239,40 @@ def test_error_codes():
         rhd.source_update({k: (None if v is None else v.cuda()) for k, v in w.state.items()}, bad,
                           w.law, dt=w.dt, c_v=w.c_v, consts=w.consts)
     assert ei.value.code == -2
+
+
+def _slow_outer_workload(n=512, seed=36):
+    """Stiff cells (c kappa dt up to 1e6) with |v| up to 1e-2 c, c_hat = 0.3 c,
+    theta = 1/2 and in-group opacity slopes of a few: where (1 + alpha)
+    chi_E / chi_F |v| / c is of order one, the flux update with the closure
+    taken at the lagged flux oscillates and the outer iteration contracts by
+    ~0.9 per pass."""
+    edges = synth.log_edges(4)
+    law = synth.random_law(edges, np.random.default_rng(seed))
+    st = synth.make_state(n, edges, law, v_max=1e-2, tau_max=1e6, seed=seed)
+    w = synth.Workload("slow-outer", st, edges, law)
+    w.consts = dict(w.consts, c_hat=0.3 * w.consts["c"])
+    return w
+
+
+def test_fp64_slow_outer_iteration_cells_converge():
+    """Every cell converges (the Newton flux steps of slowly contracting cells),
+    and with RHD_FLUX_TEST every output matches the oracle to 1e-10."""
+    w = _slow_outer_workload()
+    o = run_oracle(w, theta=0.5)
+    st0 = synth.to_numpy(w.state)
+    plain = run_gpu(w, theta=0.5, **TIGHT)
+    print("paper's outer test: status", np.bincount(plain["status"], minlength=4))
+    assert (plain["status"] == 0).mean() >= 1 - MAX_UNCONVERGED
+    g = run_gpu(w, theta=0.5, flags=rhd.FLUX_TEST, **TIGHT)
+    assert (g["status"] == 0).all(), np.bincount(g["status"])
+    e = errors(g, o, st0, w.consts["c"], w.c_v, w.edges, floor=FLOOR)
+    _report("slow-outer flux-test", e)
+    ep = errors(select(plain, plain["status"] == 0), select(o, plain["status"] == 0),
+                select(st0, plain["status"] == 0), w.consts["c"], w.c_v, w.edges, floor=FLOOR)
+    _report("slow-outer paper test", ep)
+    for k, v in e.items():
+        if not k.endswith("_plain"):
+            assert v < FP64_TOL, (k, v)
+    for k in ("T", "egas", "erad"):
+        assert ep[k] < FP64_TOL, (k, ep[k])
