@@ -196,6 +196,72 @@ int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids, int32_t n_
 /* The launch shape the context uses (threads per CTA, cells per work item). */
 int rhd_context_shape(const rhd_context_t *ctx, int32_t *threads, int32_t *cells_per_item);
 
+/* ---- Learned warm start ----------------------------------------------------
+ * A small MLP (features 2 N_g + 4 -> 128 -> 128 -> 128 -> N_g + 1, GELU, BF16
+ * weights and activations, FP32 accumulation on the tensor cores; FP32 master
+ * parameters, Adam) that maps a cell's state to a guess of the result of the
+ * implicit update: ln(T_new / T) and ln(E_g,new / E_g).  The guess becomes the
+ * starting point of the Newton iteration of Sec. 3, which still runs to the
+ * caller's tolerance; a cell whose warm-started solve does not converge is
+ * solved again from the cold start (status RHD_STATUS_FALLBACK).  The paper
+ * has no counterpart: it always starts from the state at the beginning of the
+ * step.  Features of a cell: ln rho, ln T, ln(E_g / a_R T^4) (N_g),
+ * |F_g| / (c E_g) (N_g), |v| / c, ln(c rho kappa0 dt); both features and
+ * targets are standardised with moments fitted on the training set.
+ * All float pointers are DEVICE pointers, row-major [rows][columns].  A
+ * surrogate belongs to the device current at creation and is not thread-safe. */
+#define RHD_SURROGATE_MAX_GROUPS 64
+
+typedef struct rhd_surrogate rhd_surrogate_t;
+
+/* Create with random initial weights (seeded); 1 <= n_groups <= 64. */
+int rhd_surrogate_create(int32_t n_groups, uint64_t seed, rhd_surrogate_t **s);
+int rhd_surrogate_destroy(rhd_surrogate_t *s);
+/* n_features = 2 n_groups + 4, n_outputs = n_groups + 1, n_params = length of the flat
+ * parameter vector [W1 (128 x n_features), b1, W2, b2, W3, b3, W4 (n_outputs x 128), b4]. */
+int rhd_surrogate_dims(const rhd_surrogate_t *s, int32_t *n_features, int32_t *n_outputs,
+                       int64_t *n_params);
+/* Raw features x [n_cells][n_features] of a grid (state as for rhd_source_update). */
+int rhd_surrogate_features(const rhd_surrogate_t *s, const rhd_state_t *state,
+                           const rhd_groups_t *groups, const rhd_opacity_law_t *opacity_law,
+                           double dt, int64_t n_cells, float *x, void *stream);
+/* Raw targets y [n_cells][n_outputs] from the same grid before and after an update. */
+int rhd_surrogate_targets(const rhd_surrogate_t *s, const rhd_state_t *before,
+                          const rhd_state_t *after, const rhd_groups_t *groups,
+                          const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
+                          float *y, void *stream);
+/* Fit the standardisation (per-column mean and deviation) on n >= 2 samples. */
+int rhd_surrogate_fit_normalization(rhd_surrogate_t *s, const float *x, const float *y, int64_t n,
+                                    void *stream);
+/* Copy the flat FP32 parameters and/or the standardisation [x_mean, x_sd, y_mean, y_sd]
+ * out (set = 0) or in (set = 1; setting parameters resets the Adam state).  Either
+ * pointer may be NULL. */
+int rhd_surrogate_params(rhd_surrogate_t *s, float *params, float *normalization, int32_t set,
+                         void *stream);
+/* Mean squared error (standardised targets) and its gradient with respect to the
+ * flat parameters on rows [0, n) of raw x, y (n a multiple of 8); loss and grad
+ * may be NULL. */
+int rhd_surrogate_loss_grad(rhd_surrogate_t *s, const float *x, const float *y, int64_t n,
+                            float *loss, float *grad, void *stream);
+/* One Adam step (lr; beta 0.9, 0.999; eps 1e-8) on the batch of rows
+ * (perm_mult (first + j) + perm_add) mod n_rows, j < batch (batch a multiple of 8;
+ * perm_mult coprime with n_rows makes each epoch a permutation).  loss (device
+ * float, may be NULL) is incremented by the batch's mean squared error. */
+int rhd_surrogate_train_step(rhd_surrogate_t *s, const float *x, const float *y, int64_t n_rows,
+                             int64_t first, int64_t batch, int64_t perm_mult, int64_t perm_add,
+                             float lr, float *loss, void *stream);
+/* Raw outputs y [n][n_outputs] for raw features x [n][n_features]. */
+int rhd_surrogate_predict(rhd_surrogate_t *s, const float *x, int64_t n, float *y, void *stream);
+/* 1 if a tensor-core wait of this surrogate ever timed out (results then invalid). */
+int rhd_surrogate_error(rhd_surrogate_t *s, int32_t *flag);
+/* rhd_source_update (FP64 or mixed form, from state->precision) started from the
+ * surrogate's guess; groups->n_groups must equal the surrogate's.  Same results to
+ * the caller's tolerance; status RHD_STATUS_FALLBACK marks cells that needed the
+ * cold start.  Uses the library's per-device workspace like the mixed form. */
+int rhd_source_update_warm(rhd_surrogate_t *s, rhd_state_t *state, const rhd_groups_t *groups,
+                           const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
+                           void *stream);
+
 /* The mixed-precision form without any device allocation.  Some callers
  * cannot let a library call cudaMalloc: a host that hands every byte of HBM
  * to its own memory pool up front, a latency-bound loop where a first-call

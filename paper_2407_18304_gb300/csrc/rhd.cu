@@ -26,12 +26,6 @@ int g_sms[kMaxDevices];
 void *g_ws[kMaxDevices];
 size_t g_ws_bytes[kMaxDevices];
 
-// Each lane runs its cell to completion before the next (the lane-persistent
-// form of the FP64 kernel measured the same on GB300: the branch divergence
-// inside the Planck evaluation, not the spread of iteration counts, limits
-// lane efficiency).
-constexpr bool g_persist = false;
-
 size_t warm_bytes(int64_t n, int G) {
   return (size_t)n * (4 * sizeof(double) + 1) + (size_t)n * G * 4 * sizeof(float) + 1024;
 }
@@ -43,7 +37,7 @@ void carve(char *p, int64_t n, int G, WarmOut *w, WarmStart *r) {
   w->r = reinterpret_cast<float *>(w->mom + 3 * n);
   w->f = w->r + (size_t)G * n;
   w->nit = reinterpret_cast<uint8_t *>(w->f + (size_t)3 * G * n);
-  *r = WarmStart{w->eint, w->mom, w->r, w->f, w->nit};
+  *r = WarmStart{w->eint, w->mom, w->r, w->f, w->nit, 1};
 }
 
 int workspace(int64_t n, int G, WarmOut *w, WarmStart *r) {
@@ -260,10 +254,34 @@ int launch_mixed(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int 
   const int threads = 128;
   const size_t smem = table_bytes(kp.G);
   const int ba = persistent_blocks(warm_fp32_kernel<MAXG>, smem, sms, kp.n, threads);
-  warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo);
-  const int bb = persistent_blocks(solve_fp64_kernel<MAXG, g_persist>, smem, sms, kp.n, threads);
-  solve_fp64_kernel<MAXG, g_persist><<<bb, threads, smem, st>>>(kp, wi);
+  const WarmStart none{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+  warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo, none);
+  const int bb = persistent_blocks(solve_fp64_kernel<MAXG>, smem, sms, kp.n, threads);
+  solve_fp64_kernel<MAXG><<<bb, threads, smem, st>>>(kp, wi);
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
+}
+
+// Solve from a warm start already in the workspace (wo/wi view the same
+// arrays): FP64 form directly from it; mixed form FP32 passes from it (in
+// place), then the FP64 passes from their result.  Cold restart on failure.
+template <int MAXG>
+int launch_warm_g(const KParams &kp, int precision, const WarmOut &wo, const WarmStart &wi,
+                  int sms, cudaStream_t st) {
+  const int threads = 128;
+  const size_t smem = table_bytes(kp.G);
+  if (precision == RHD_MIXED) {
+    const int ba = persistent_blocks(warm_fp32_kernel<MAXG>, smem, sms, kp.n, threads);
+    warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo, wi);
+  }
+  const int bb = persistent_blocks(solve_fp64_kernel<MAXG>, smem, sms, kp.n, threads);
+  solve_fp64_kernel<MAXG><<<bb, threads, smem, st>>>(kp, wi);
+  return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
+}
+
+int launch_warm(const KParams &kp, int precision, const WarmOut &wo, const WarmStart &wi, int sms,
+                cudaStream_t st) {
+  if (kp.G <= 16) return launch_warm_g<16>(kp, precision, wo, wi, sms, st);
+  return launch_warm_g<64>(kp, precision, wo, wi, sms, st);
 }
 
 template <int MAXG>
@@ -271,28 +289,15 @@ int launch_g(const KParams &kp, int precision, int sms, cudaStream_t st) {
   const int threads = 128;
   const size_t smem = table_bytes(kp.G);
   if (precision == RHD_FP64) {
-    const WarmStart cold{nullptr, nullptr, nullptr, nullptr, nullptr};
-    if (g_persist) {
-      const int b = persistent_blocks(solve_fp64_kernel<MAXG, true>, smem, sms, kp.n, threads);
-      solve_fp64_kernel<MAXG, true><<<b, threads, smem, st>>>(kp, cold);
-    } else {
-      const int b = persistent_blocks(solve_fp64_kernel<MAXG, false>, smem, sms, kp.n, threads);
-      solve_fp64_kernel<MAXG, false><<<b, threads, smem, st>>>(kp, cold);
-    }
+    const WarmStart cold{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+    const int b = persistent_blocks(solve_fp64_kernel<MAXG>, smem, sms, kp.n, threads);
+    solve_fp64_kernel<MAXG><<<b, threads, smem, st>>>(kp, cold);
   } else {
     WarmOut wo;
     WarmStart wi;
     const int rc = workspace(kp.n, kp.G, &wo, &wi);
     if (rc != RHD_OK) return rc;
-    const int ba = persistent_blocks(warm_fp32_kernel<MAXG>, smem, sms, kp.n, threads);
-    warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo);
-    if (g_persist) {
-      const int bb = persistent_blocks(solve_fp64_kernel<MAXG, true>, smem, sms, kp.n, threads);
-      solve_fp64_kernel<MAXG, true><<<bb, threads, smem, st>>>(kp, wi);
-    } else {
-      const int bb = persistent_blocks(solve_fp64_kernel<MAXG, false>, smem, sms, kp.n, threads);
-      solve_fp64_kernel<MAXG, false><<<bb, threads, smem, st>>>(kp, wi);
-    }
+    return launch_mixed<MAXG>(kp, wo, wi, sms, st);
   }
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
 }
@@ -621,6 +626,8 @@ extern "C" int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids,
   ctx->cpi = bc;
   return RHD_OK;
 }
+
+#include "rhd_surrogate.cuh"
 
 extern "C" const char *rhd_strerror(int code) {
   switch (code) {

@@ -58,27 +58,39 @@ __device__ __forceinline__ void solve_cell(const KParams &P, const GroupTable &t
     nit = C.nit > 255 ? 255 : C.nit;
   }
   if (!load_cell(P, i, C, A)) return;
-  set_tau(P, tab, C, A, C.chi0s);
-  if (warm) {
-    C.Eint = eint;
-    C.m[0] = m[0];
-    C.m[1] = m[1];
-    C.m[2] = m[2];
-    C.nit = nit;
-    const double fs = P.c * C.Etot;
-    for (int g = 0; g < P.G; ++g) {
-      A.R[g] = (double)B.R[g] * C.Etot;
-      A.Fk[3 * g] = (double)B.f[3 * g] * fs;
-      A.Fk[3 * g + 1] = (double)B.f[3 * g + 1] * fs;
-      A.Fk[3 * g + 2] = (double)B.f[3 * g + 2] * fs;
+  for (int attempt = 0; attempt < 2; ++attempt) {  // as solve_fp64_kernel (fallback)
+    int nit0 = 0;
+    if (attempt == 1) {
+      if (!(warm && C.stat != RHD_STATUS_OK)) break;
+      nit0 = C.nit;
+      load_cell(P, i, C, A);
     }
-  }
-  outer_begin(P, C, A);
-  for (;;) {
-    const int r = inner_step(P, tab, C, A);
-    if (r == 0) continue;
-    if (r == 2) C.stat = RHD_STATUS_MAXITER;
-    if (outer_end(P, tab, C, A)) break;
+    set_tau(P, tab, C, A, C.chi0s);
+    if (warm && attempt == 0) {
+      C.Eint = eint;
+      C.m[0] = m[0];
+      C.m[1] = m[1];
+      C.m[2] = m[2];
+      C.nit = nit;
+      const double fs = P.c * C.Etot;
+      for (int g = 0; g < P.G; ++g) {
+        A.R[g] = (double)B.R[g] * C.Etot;
+        A.Fk[3 * g] = (double)B.f[3 * g] * fs;
+        A.Fk[3 * g + 1] = (double)B.f[3 * g + 1] * fs;
+        A.Fk[3 * g + 2] = (double)B.f[3 * g + 2] * fs;
+      }
+    }
+    outer_begin(P, C, A);
+    for (;;) {
+      const int r = inner_step(P, tab, C, A);
+      if (r == 0) continue;
+      if (r == 2) C.stat = RHD_STATUS_MAXITER;
+      if (outer_end(P, tab, C, A)) break;
+    }
+    if (attempt == 1) {
+      C.nit += nit0;
+      if (C.stat == RHD_STATUS_OK) C.stat = RHD_STATUS_FALLBACK;
+    }
   }
   store_cell(P, C, A);
 }

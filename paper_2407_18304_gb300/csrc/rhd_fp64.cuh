@@ -411,12 +411,14 @@ struct WarmStart {
   const float *r;      // [G][n] R_g / E_tot
   const float *f;      // [3][G][n] F_g / (c E_tot)
   const uint8_t *nit;  // [n] FP32 Newton iterations
+  int fallback;        // a cell whose warm-started solve fails is solved again from the cold start
 };
 
 template <int MAXG>
 __device__ __forceinline__ void apply_warm(const KParams &P, const WarmStart &W, Cell &C,
                                            Arr64<MAXG> &A) {
   const int64_t i = C.i, n = P.n;
+  if (!(W.eint[i] > 0.0)) return;  // no usable guess: the cold start stays
   C.Eint = W.eint[i];
   C.m[0] = W.mom[i];
   C.m[1] = W.mom[n + i];
@@ -432,10 +434,12 @@ __device__ __forceinline__ void apply_warm(const KParams &P, const WarmStart &W,
   }
 }
 
-// Lane-persistent FP64 solve: each lane walks the cells i, i + stride, ...,
-// taking the next one as soon as the current one is stored (PERSIST), or
-// finishing each cell before the warp moves on (!PERSIST).
-template <int MAXG, bool PERSIST>
+// FP64 solve, one cell per thread: each thread walks the cells i, i + stride,
+// ..., finishing each before the next.  With a warm start (W.r) the first
+// attempt starts from it; if that attempt does not converge and W.fallback is
+// set, the cell is solved again from the cold start (status FALLBACK if that
+// converges).
+template <int MAXG>
 __global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__ KParams P,
                                                          const WarmStart W) {
   extern __shared__ double sm[];
@@ -443,12 +447,18 @@ __global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__
   Arr64<MAXG> A;
   Cell C;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (!PERSIST) {
-    for (; i < P.n; i += stride) {
-      if (!load_cell(P, i, C, A)) continue;
+  const bool warm = W.r != nullptr;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
+    if (!load_cell(P, i, C, A)) continue;
+    for (int attempt = 0; attempt < 2; ++attempt) {
+      int nit0 = 0;
+      if (attempt == 1) {
+        if (!(warm && W.fallback && C.stat != RHD_STATUS_OK)) break;
+        nit0 = C.nit;
+        load_cell(P, i, C, A);
+      }
       set_tau(P, tab, C, A, C.chi0s);
-      if (W.r) apply_warm(P, W, C, A);
+      if (warm && attempt == 0) apply_warm(P, W, C, A);
       outer_begin(P, C, A);
       for (;;) {
         const int r = inner_step(P, tab, C, A);
@@ -456,35 +466,12 @@ __global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__
         if (r == 2) C.stat = RHD_STATUS_MAXITER;
         if (outer_end(P, tab, C, A)) break;
       }
-      store_cell(P, C, A);
-    }
-    return;
-  }
-  auto next = [&]() -> bool {
-    while (i < P.n) {
-      if (load_cell(P, i, C, A)) {
-        set_tau(P, tab, C, A, C.chi0s);
-        if (W.r) apply_warm(P, W, C, A);
-        outer_begin(P, C, A);
-        return true;
-      }
-      i += stride;
-    }
-    return false;
-  };
-  bool active = next();
-  while (__any_sync(0xffffffffu, active)) {
-    if (active) {
-      const int r = inner_step(P, tab, C, A);
-      if (r != 0) {
-        if (r == 2) C.stat = RHD_STATUS_MAXITER;
-        if (outer_end(P, tab, C, A)) {
-          store_cell(P, C, A);
-          i += stride;
-          active = next();
-        }
+      if (attempt == 1) {
+        C.nit += nit0;
+        if (C.stat == RHD_STATUS_OK) C.stat = RHD_STATUS_FALLBACK;
       }
     }
+    store_cell(P, C, A);
   }
 }
 

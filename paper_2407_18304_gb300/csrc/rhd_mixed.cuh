@@ -329,9 +329,12 @@ __device__ __forceinline__ void store_warm(const KParams &P, const WarmOut &W, c
 }
 
 // Phase A launch: lane-persistent FP32 iteration; writes the warm start.
+// S.r non-null: each cell starts from S (E_int and R_g / E_tot; a surrogate's
+// guess) instead of the cold start.  S may alias W (each thread reads its
+// cell's start before it writes that cell's result).
 template <int MAXG>
 __global__ void __launch_bounds__(128) warm_fp32_kernel(const __grid_constant__ KParams P,
-                                                        const WarmOut W) {
+                                                        const WarmOut W, const WarmStart S) {
   extern __shared__ double sm[];
   const GroupTable tab = build_table(P, sm);
   Arr32<MAXG> B;
@@ -342,6 +345,10 @@ __global__ void __launch_bounds__(128) warm_fp32_kernel(const __grid_constant__ 
   auto next = [&]() -> bool {
     while (i < P.n) {
       if (load_cell32(P, tab, i, C, D, B)) {
+        if (S.r && S.eint[i] > 0.0) {
+          C.Eint = S.eint[i];
+          for (int g = 0; g < P.G; ++g) B.R[g] = S.r[(int64_t)g * P.n + i];
+        }
         outer_begin32(P, C, D, B);
         return true;
       }

@@ -94,6 +94,32 @@ def lib() -> ctypes.CDLL:
         _lib.rhd_context_shape.restype = ctypes.c_int
         _lib.rhd_context_shape.argtypes = [_P, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32)]
+        _F = ctypes.c_void_p
+        sig = {
+            "rhd_surrogate_create": [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(_P)],
+            "rhd_surrogate_destroy": [_P],
+            "rhd_surrogate_dims": [_P, ctypes.POINTER(ctypes.c_int32),
+                                   ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int64)],
+            "rhd_surrogate_features": [_P, ctypes.POINTER(State), ctypes.POINTER(Groups),
+                                       ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _F, _P],
+            "rhd_surrogate_targets": [_P, ctypes.POINTER(State), ctypes.POINTER(State),
+                                      ctypes.POINTER(Groups), ctypes.POINTER(OpacityLaw), _D,
+                                      ctypes.c_int64, _F, _P],
+            "rhd_surrogate_fit_normalization": [_P, _F, _F, ctypes.c_int64, _P],
+            "rhd_surrogate_params": [_P, _F, _F, ctypes.c_int32, _P],
+            "rhd_surrogate_loss_grad": [_P, _F, _F, ctypes.c_int64, _F, _F, _P],
+            "rhd_surrogate_train_step": [_P, _F, _F, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                                         ctypes.c_float, _F, _P],
+            "rhd_surrogate_predict": [_P, _F, ctypes.c_int64, _F, _P],
+            "rhd_surrogate_error": [_P, ctypes.POINTER(ctypes.c_int32)],
+            "rhd_source_update_warm": [_P, ctypes.POINTER(State), ctypes.POINTER(Groups),
+                                       ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _P],
+        }
+        for name, args in sig.items():
+            f = getattr(_lib, name)
+            f.restype = ctypes.c_int
+            f.argtypes = args
         _lib.rhd_strerror.restype = ctypes.c_char_p
         _lib.rhd_strerror.argtypes = [ctypes.c_int]
         _lib.rhd_version.restype = ctypes.c_int
@@ -343,6 +369,131 @@ class Context:
         t, c = ctypes.c_int32(), ctypes.c_int32()
         _raise(lib().rhd_context_shape(self._h, ctypes.byref(t), ctypes.byref(c)))
         return t.value, c.value
+
+
+class Surrogate:
+    """The learned warm start (``rhd_surrogate_t``): a BF16 MLP on the tensor
+    cores mapping a cell's state to a guess of its updated temperature and
+    group energies.  All arrays are CUDA float32 tensors, row-major."""
+
+    def __init__(self, n_groups: int, seed: int = 0):
+        h = _P()
+        _raise(lib().rhd_surrogate_create(int(n_groups), int(seed), ctypes.byref(h)))
+        self._h = h
+        self.n_groups = int(n_groups)
+        nf, no, npar = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _raise(lib().rhd_surrogate_dims(h, ctypes.byref(nf), ctypes.byref(no), ctypes.byref(npar)))
+        self.n_features, self.n_outputs, self.n_params = nf.value, no.value, npar.value
+
+    def close(self) -> None:
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _raise(lib().rhd_surrogate_destroy(self._h))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _s(stream):
+        s = stream if stream is not None else torch.cuda.current_stream()
+        return ctypes.c_void_p(s.cuda_stream)
+
+    def _grid(self, state, edges, law, dt, c_v, consts, mode=PPL_FIXED):
+        n = state["rho"].shape[0]
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        st = _state(state, len(e) - 1, n, n, c_v=c_v, consts=consts, theta=1.0, precision=FP64,
+                    closure=M1, tol=0.0, tol_outer=0.0, max_newton=0, max_outer=0, status=None,
+                    iters=None, flags=0)
+        lw, keep = make_law(law, mode)
+        return st, Groups(len(e) - 1, _dp(e)), lw, keep + [e], n
+
+    def features(self, state, edges, law, *, dt, c_v, consts, stream=None) -> torch.Tensor:
+        st, gr, lw, keep, n = self._grid(state, edges, law, dt, c_v, consts)
+        x = torch.empty((n, self.n_features), dtype=torch.float32, device=state["rho"].device)
+        _raise(lib().rhd_surrogate_features(self._h, ctypes.byref(st), ctypes.byref(gr),
+                                            ctypes.byref(lw), float(dt), n, _ptr(x), self._s(stream)))
+        del keep
+        return x
+
+    def targets(self, before, after, edges, law, *, dt, c_v, consts, stream=None) -> torch.Tensor:
+        sa, gr, lw, keep, n = self._grid(before, edges, law, dt, c_v, consts)
+        sb, _, _, keep2, _ = self._grid(after, edges, law, dt, c_v, consts)
+        y = torch.empty((n, self.n_outputs), dtype=torch.float32, device=before["rho"].device)
+        _raise(lib().rhd_surrogate_targets(self._h, ctypes.byref(sa), ctypes.byref(sb),
+                                           ctypes.byref(gr), ctypes.byref(lw), float(dt), n,
+                                           _ptr(y), self._s(stream)))
+        del keep, keep2
+        return y
+
+    def fit_normalization(self, x, y, stream=None) -> None:
+        _check(x, "x", (x.shape[0], self.n_features), torch.float32)
+        _check(y, "y", (x.shape[0], self.n_outputs), torch.float32)
+        _raise(lib().rhd_surrogate_fit_normalization(self._h, _ptr(x), _ptr(y), x.shape[0],
+                                                     self._s(stream)))
+
+    def get_params(self, stream=None):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        p = torch.empty(self.n_params, dtype=torch.float32, device=dev)
+        nrm = torch.empty(2 * (self.n_features + self.n_outputs), dtype=torch.float32, device=dev)
+        _raise(lib().rhd_surrogate_params(self._h, _ptr(p), _ptr(nrm), 0, self._s(stream)))
+        return p, nrm
+
+    def set_params(self, params=None, normalization=None, stream=None) -> None:
+        if params is not None:
+            _check(params, "params", (self.n_params,), torch.float32)
+        if normalization is not None:
+            _check(normalization, "normalization", (2 * (self.n_features + self.n_outputs),),
+                   torch.float32)
+        _raise(lib().rhd_surrogate_params(self._h, _ptr(params), _ptr(normalization), 1,
+                                          self._s(stream)))
+
+    def loss_grad(self, x, y, stream=None):
+        _check(x, "x", (x.shape[0], self.n_features), torch.float32)
+        _check(y, "y", (x.shape[0], self.n_outputs), torch.float32)
+        loss = torch.zeros(1, dtype=torch.float32, device=x.device)
+        grad = torch.empty(self.n_params, dtype=torch.float32, device=x.device)
+        _raise(lib().rhd_surrogate_loss_grad(self._h, _ptr(x), _ptr(y), x.shape[0], _ptr(loss),
+                                             _ptr(grad), self._s(stream)))
+        return loss, grad
+
+    def train_step(self, x, y, first, batch, mult, add, lr, loss=None, stream=None) -> None:
+        _raise(lib().rhd_surrogate_train_step(self._h, _ptr(x), _ptr(y), x.shape[0], int(first),
+                                              int(batch), int(mult), int(add), float(lr),
+                                              _ptr(loss), self._s(stream)))
+
+    def predict(self, x, stream=None) -> torch.Tensor:
+        _check(x, "x", (x.shape[0], self.n_features), torch.float32)
+        y = torch.empty((x.shape[0], self.n_outputs), dtype=torch.float32, device=x.device)
+        _raise(lib().rhd_surrogate_predict(self._h, _ptr(x), x.shape[0], _ptr(y), self._s(stream)))
+        return y
+
+    def error_flag(self) -> int:
+        f = ctypes.c_int32()
+        _raise(lib().rhd_surrogate_error(self._h, ctypes.byref(f)))
+        return f.value
+
+    def source_update(self, state: dict, edges, law, *, dt: float, c_v: float, consts: dict,
+                      theta: float = 1.0, precision: int = MIXED, closure: int = M1,
+                      tol: float = 0.0, tol_outer: float = 0.0, max_newton: int = 0,
+                      max_outer: int = 0, status=None, iters=None, mode: int = PPL_FIXED,
+                      khat_g=None, alpha_g=None, temp_exponent: float = 0.0, T_ref: float = 1.0,
+                      stream=None, flags: int = 0) -> None:
+        """``rhd_source_update_warm``: the update of one grid started from this
+        surrogate's guess (same arguments as ``source_update``)."""
+        n = state["rho"].shape[0]
+        e = np.ascontiguousarray(edges, dtype=np.float64)
+        st = _state(state, len(e) - 1, n, n, c_v=c_v, consts=consts, theta=theta,
+                    precision=precision, closure=closure, tol=tol, tol_outer=tol_outer,
+                    max_newton=max_newton, max_outer=max_outer, status=status, iters=iters,
+                    flags=flags)
+        gr = Groups(len(e) - 1, _dp(e))
+        lw, keep = make_law(law, mode, khat_g, alpha_g, temp_exponent, T_ref)
+        _raise(lib().rhd_source_update_warm(self._h, ctypes.byref(st), ctypes.byref(gr),
+                                            ctypes.byref(lw), float(dt), n, self._s(stream)))
+        del keep
 
 
 def strerror(code: int) -> str:
