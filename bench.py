@@ -1,9 +1,16 @@
 #!/usr/bin/env python3
 """Throughput of the implicit multigroup source-term update on GB300.
 
-One step = one ``rhd_source_update`` call over the whole synthetic grid (all
-steps of the method: load, group table, inner Newton with the arrowhead
-elimination, write-back, flux and momentum update, outer iteration, store).
+One step = one update call over the whole synthetic grid (all steps of the
+method: load, group table, inner Newton with the arrowhead elimination,
+write-back, flux and momentum update, outer iteration, store).  The headline
+form is the one the metric names: the mixed-precision solver started from the
+learned warm start (``rhd_source_update_warm``: network inference on the
+tensor cores, then the FP32 and FP64 passes); the surrogate is trained before
+the timed region on cells of the same distribution (other seeds) that the
+plain FP64 solver has advanced.  The plain FP64 Newton form (the comparison),
+the mixed form without the surrogate and the FP64 form with it are timed
+beside it on the same grid.
 The grid is restored from a pristine device copy before every step, outside
 the timed region; that copy (2 x 35 GB at the default size) also flushes L2.
 The metric is cell-group source updates per second: cells x groups advanced
@@ -50,6 +57,10 @@ def parse():
     ap.add_argument("--n-cells", type=int, default=None, help="override the cell count")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-surrogate", action="store_true",
+                    help="time the solver from the cold start (no learned warm start)")
+    ap.add_argument("--sur-train-cells", type=int, default=1 << 21)
+    ap.add_argument("--sur-epochs", type=int, default=4)
     ap.add_argument("--cpu-sample", type=int, default=2048,
                     help="cells of the workload the CPU oracle baseline solves")
     return ap.parse_args()
@@ -148,11 +159,32 @@ def fp_peaks() -> dict:
 # instruction counts ncu reports for the same workload on a 65536-cell sample
 # (profiles/solve_full_256cube_ng64.md); a property of the workload and the
 # algorithm, applied to the full-size grid of the same distribution.
-FP64_FLOPS_PER_CG = {("full_256cube_ng64", "mixed"): 17.7 + 1820.4,
-                     ("full_256cube_ng64", "fp64"): 3271.6}
+FP64_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1882.6,
+                     ("full_256cube_ng64", "mixed"): 1866.1,
+                     ("full_256cube_ng64", "fp64"): 3311.7}
 # DRAM bytes (read + write) per cell-group of one call from the same capture
-TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed"): 1639.0 + 2099.0,
-                  ("full_256cube_ng64", "fp64"): 3502.0}
+TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 3584.0,
+                  ("full_256cube_ng64", "mixed"): 3605.0,
+                  ("full_256cube_ng64", "fp64"): 3260.0}
+
+
+def train_surrogate(args, w, dev, rank):
+    """The learned warm start for this workload: training cells drawn like the
+    grid (same groups, law and distributions, other seeds), advanced by the
+    plain FP64 solver, then Adam (untimed setup)."""
+    from paper_2407_18304_gb300 import rhd, surrogate, synth
+    side, G, vmax, taumax, kind = synth.PRESETS[args.workload]
+    t0 = time.perf_counter()
+    sur = rhd.Surrogate(w.n_groups, 1 + rank)
+    x, y = surrogate.training_set(sur, args.sur_train_cells, w.edges, w.law, v_max=vmax,
+                                  tau_max=taumax, seed=9_000_000 + 1000 * rank, device=dev)
+    losses = surrogate.train(sur, x, y, epochs=args.sur_epochs, batch=8192, seed=rank)
+    del x, y
+    torch.cuda.synchronize()
+    info = {"train_cells": args.sur_train_cells, "epochs": args.sur_epochs,
+            "epoch_losses": [round(v, 5) for v in losses],
+            "setup_s": time.perf_counter() - t0, "tensor_core_error": sur.error_flag()}
+    return sur, info
 
 
 def run_ours(args, ws, rank):
@@ -164,6 +196,8 @@ def run_ours(args, ws, rank):
     w = synth.preset(name, device=dev, n_cells=args.n_cells, seed=seed)
     n, G = w.n_cells, w.n_groups
     prec = rhd.FP64 if args.precision == "fp64" else rhd.MIXED
+    use_sur = not args.no_surrogate
+    sur, sur_info = train_surrogate(args, w, dev, rank) if use_sur else (None, None)
     pristine = w.state
     st = synth.clone_state(pristine)
     status = torch.empty(n, dtype=torch.uint8, device=dev)
@@ -174,12 +208,19 @@ def run_ours(args, ws, rank):
         for k in ("mom", "egas", "erad", "frad"):
             st[k].copy_(pristine[k])
 
-    def timed(p, steps, warmup, sample_clocks=False):
-        """Run warmup + steps solves of precision p; per-step CUDA-event times."""
+    def call(p, warm):
+        args_ = dict(dt=w.dt, c_v=w.c_v, consts=w.consts, precision=p, status=status,
+                     iters=iters, stream=stream)
+        if warm:
+            sur.source_update(st, w.edges, w.law, **args_)
+        else:
+            rhd.source_update(st, w.edges, w.law, **args_)
+
+    def timed(p, warm, steps, warmup, sample_clocks=False):
+        """warmup + steps solves; per-step CUDA-event times and outcome."""
         for _ in range(warmup):
             restore()
-            rhd.source_update(st, w.edges, w.law, dt=w.dt, c_v=w.c_v, consts=w.consts,
-                              precision=p, status=status, iters=iters, stream=stream)
+            call(p, warm)
         torch.cuda.synchronize()
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -192,8 +233,12 @@ def run_ours(args, ws, rank):
         for k in range(steps):
             restore()
             starts[k].record(stream)
-            rhd.source_update(st, w.edges, w.law, dt=w.dt, c_v=w.c_v, consts=w.consts,
-                              precision=p, status=status, iters=iters, stream=stream)
+            if k == 0:  # marks one timed step for profilers (ncu --nvtx-include)
+                torch.cuda.nvtx.range_push("rhd_step_" + ("mixed" if p == rhd.MIXED else "fp64")
+                                           + ("_surrogate" if warm else ""))
+            call(p, warm)
+            if k == 0:
+                torch.cuda.nvtx.range_pop()
             ends[k].record(stream)
         torch.cuda.synchronize()
         barrier(ws)
@@ -202,36 +247,50 @@ def run_ours(args, ws, rank):
         ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
         stat = status.cpu().numpy()
         it = iters.cpu().numpy().astype(np.int64)
-        return ms, wall, clk, float((stat == 0).mean()), float(it.mean())
+        outcome = {"converged_fraction": float((stat <= 1).mean()),
+                   "fallback_fraction": float((stat == 1).mean()),
+                   "mean_newton_iters": float(it.mean())}
+        return ms, wall, clk, outcome
 
-    ms, wall, clk, conv_frac, mean_iters = timed(prec, args.steps, args.warmup, True)
+    def side(p, warm, steps):
+        ms_, _, _, out = timed(p, warm, steps, 1)
+        t = allmax(sum(ms_) / 1e3, ws)
+        d = {"value": allsum(float(n) * G * steps, ws) / t, "ms_per_step": 1e3 * t / steps,
+             "steps": steps}
+        d.update(out)
+        return d
+
+    ms, wall, clk, outcome = timed(prec, use_sur, args.steps, args.warmup, True)
     t_dev = sum(ms) / 1e3
     t_max = allmax(t_dev, ws)
     units = float(n) * G * args.steps
     total_units = allsum(units, ws)
+    chunks = -(-n // rhd.SURROGATE_CHUNK)
+    launches = (1 if prec == rhd.FP64 else 2) + (6 * chunks if use_sur else 0)
+    form = ("mixed" if prec == rhd.MIXED else "fp64") + ("+surrogate" if use_sur else "")
 
     res = {"metric": METRIC, "value": total_units / t_max, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-           "dtype": "f64" if prec == rhd.FP64 else "f32+f64",
+           "dtype": "f64" if prec == rhd.FP64 else ("f32+f64+bf16" if use_sur else "f32+f64"),
            "data": "synthetic (seeded; recipe in DESIGN.md)",
-           "config": {"workload": name, "cells": n, "n_groups": G, "precision": args.precision,
-                      "tol": 1e-11, "tol_outer": 1e-13,
+           "config": {"workload": name, "cells": n, "n_groups": G, "form": form,
+                      "precision": args.precision, "tol": 1e-11, "tol_outer": 1e-13,
                       "l2": "state restored from a pristine copy before each step (2x state > L2)",
                       "parallelism": f"weak x{ws}, no collective"},
-           "converged_fraction": conv_frac, "mean_newton_iters": mean_iters,
-           "gpu_launches": args.steps * (1 if prec == rhd.FP64 else 2), "wall_s_timed": wall,
-           "clocks": clk}
+           "gpu_launches": args.steps * launches, "wall_s_timed": wall, "clocks": clk}
+    res.update(outcome)
+    if sur_info is not None:
+        res["surrogate"] = sur_info
 
-    # the plain FP64 form on the same grid, same tolerance (the comparison)
-    if prec != rhd.FP64 and args.fp64_steps > 0:
-        ms64, _, _, conv64, it64 = timed(rhd.FP64, args.fp64_steps, 1)
-        t64 = allmax(sum(ms64) / 1e3, ws)
-        res["fp64_form"] = {"value": allsum(float(n) * G * args.fp64_steps, ws) / t64,
-                            "ms_per_step": 1e3 * t64 / args.fp64_steps, "steps": args.fp64_steps,
-                            "converged_fraction": conv64, "mean_newton_iters": it64}
+    # the comparison forms on the same grid, same tolerance
+    if args.fp64_steps > 0:
+        res["fp64_form"] = side(rhd.FP64, False, args.fp64_steps)
         res["speedup_vs_fp64_form"] = res["value"] / res["fp64_form"]["value"]
+        if use_sur and prec == rhd.MIXED:
+            res["mixed_form"] = side(rhd.MIXED, False, args.fp64_steps)
+            res["fp64_surrogate_form"] = side(rhd.FP64, True, args.fp64_steps)
 
     # roofline of the solve (FP64-issue bound)
     peaks = fp_peaks()
@@ -239,14 +298,14 @@ def run_ours(args, ws, rank):
     mean_launch_s = t_dev / args.steps
     bytes_alg = n * (G * 64 + 82)  # in+out FP64 SoA per call
     hbm_frac = bytes_alg / mean_launch_s / 1e9 / _measured_hbm()
-    per_cg = FP64_FLOPS_PER_CG.get((name, args.precision))
+    per_cg = FP64_FLOPS_PER_CG.get((name, form))
     if per_cg is not None:
         peak = peaks.get("fp64_fma_tflops") or 1.25
         ach = per_cg * n * G / mean_launch_s / 1e12
+        tr = TRAFFIC_PER_CG.get((name, form))
         res["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                            "frac": ach / peak,
-                           "traffic": (TRAFFIC_PER_CG[(name, args.precision)] * n * G
-                                       if (name, args.precision) in TRAFFIC_PER_CG else None),
+                           "traffic": tr * n * G if tr is not None else None,
                            "what": "FP64 flops (DFMA = 2) per call / call time, vs the DFMA peak",
                            "peak_source": ("measured fp_peak DFMA loop" if "fp64_fma_tflops" in peaks
                                            else "nominal 1.25 TFLOP/s"),
@@ -259,7 +318,7 @@ def run_ours(args, ws, rank):
                            "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
 
     if not args.no_e2e:
-        res["e2e"] = run_e2e(args, w, prec, dev, ws)
+        res["e2e"] = run_e2e(args, w, prec, dev, ws, sur)
     if rank == 0 and ws == 1:
         res["cpu_baseline"] = cpu_baseline(args, w)
     return res
@@ -365,7 +424,7 @@ def _measured_hbm() -> float:
         return 6800.0
 
 
-def run_e2e(args, w, prec, dev, ws):
+def run_e2e(args, w, prec, dev, ws, sur=None):
     """The same metric through the C ABI with the state in pinned host memory:
     H2D of the inputs, the call, D2H of the results, all inside the timing."""
     from paper_2407_18304_gb300 import rhd
@@ -389,8 +448,9 @@ def run_e2e(args, w, prec, dev, ws):
     def step():
         for k in keys_in:
             dst[k].copy_(host_in[k], non_blocking=True)
-        rhd.source_update(dst, w.edges, w.law, dt=w.dt, c_v=w.c_v, consts=w.consts,
-                          precision=prec, status=status, stream=stream)
+        f = sur.source_update if sur is not None else rhd.source_update
+        f(dst, w.edges, w.law, dt=w.dt, c_v=w.c_v, consts=w.consts, precision=prec,
+          status=status, stream=stream)
         for k in keys_out:
             host_out[k].copy_(dst[k], non_blocking=True)
         host_status.copy_(status, non_blocking=True)
@@ -407,7 +467,9 @@ def run_e2e(args, w, prec, dev, ws):
     del dst
     return {"value": units / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-            "path": "pinned host -> device copies, rhd_source_update, device -> pinned host"}
+            "path": ("pinned host -> device copies, "
+                     + ("rhd_source_update_warm" if sur is not None else "rhd_source_update")
+                     + ", device -> pinned host")}
 
 
 def cpu_baseline(args, w):

@@ -39,7 +39,22 @@ __device__ __forceinline__ bool cell_T(const KParams &P, int64_t i, double &T) {
   return rho > 0.0 && isfinite(T) && T > 0.0;
 }
 
+// 2^-e as a double (|e| < 1000; exact).
+__device__ __forceinline__ double pow2_neg(int e) {
+  return __hiloint2double((1023 - e) << 20, 0);
+}
+
+// Natural log of a positive finite double to FP32 accuracy without FP64
+// transcendentals: ln(m 2^e) = e ln 2 + ln m, with m in [0.5, 1).
+__device__ __forceinline__ float ln_f(double x) {
+  int e;
+  const double m = frexp(x, &e);
+  return (float)e * 0.69314718055994531f + __logf((float)m);
+}
+
 // Raw features of one cell into f[0 .. 2G+4); false for an invalid cell.
+// The per-group features are formed in FP32 after exact power-of-two
+// scaling (the network consumes BF16; a guess needs no more).
 __device__ __forceinline__ bool cell_features(const KParams &P, int64_t i, float *f) {
   const int G = P.G;
   double T;
@@ -49,17 +64,25 @@ __device__ __forceinline__ bool cell_features(const KParams &P, int64_t i, float
     return false;
   }
   const double rho = P.rho[i];
-  const double lnaT4 = log(P.a_rad) + 4.0 * log(T);
-  f[0] = (float)log(rho);
-  f[1] = (float)log(T);
+  const float lnaT4 = ln_f(P.a_rad * T * T * T * T);
+  f[0] = ln_f(rho);
+  f[1] = ln_f(T);
   for (int g = 0; g < G; ++g) {
     const int64_t o = (int64_t)g * P.gs + i;
     const double e = P.erad[o];
-    const double fx = P.frad[0][o], fy = P.frad[1][o], fz = P.frad[2][o];
-    const double le = e > 0.0 ? log(e) - lnaT4 : -700.0;
-    f[2 + g] = (float)fmin(fmax(le, -700.0), 50.0);
-    const double fr = e > 0.0 ? sqrt(fx * fx + fy * fy + fz * fz) / (P.c * e) : 0.0;
-    f[2 + G + g] = (float)fmin(fr, 2.0);
+    if (!(e > 1e-290) || isinf(e)) {  // empty (or denormal) group
+      f[2 + g] = -700.0f;
+      f[2 + G + g] = 0.0f;
+      continue;
+    }
+    int ex;
+    frexp(e, &ex);
+    const double sc = pow2_neg(ex);  // e * sc in [0.5, 1)
+    const float es = (float)(e * sc);
+    const float fx = (float)(P.frad[0][o] * sc), fy = (float)(P.frad[1][o] * sc),
+                fz = (float)(P.frad[2][o] * sc);
+    f[2 + g] = fminf(fmaxf(ln_f(e) - lnaT4, -700.0f), 50.0f);
+    f[2 + G + g] = fminf(sqrtf(fx * fx + fy * fy + fz * fz) / ((float)P.c * es), 2.0f);
   }
   const double m0 = P.mom[0][i], m1 = P.mom[1][i], m2 = P.mom[2][i];
   f[2 + 2 * G] = (float)(sqrt(m0 * m0 + m1 * m1 + m2 * m2) / (rho * P.c));
@@ -312,13 +335,16 @@ __global__ void warm_from_net_kernel(const __grid_constant__ KParams P, int64_t 
     W.mom[n + i] = P.mom[1][i];
     W.mom[2 * n + i] = P.mom[2][i];
     W.nit[i] = 0;
-    const double fs = 1.0 / (P.c * etot);
+    // the guess only seeds the Newton iteration: FP32 arithmetic on the
+    // energy-scaled group quantities (R_g / E_tot is stored in FP32 anyway)
+    const double ie = ok && etot > 0.0 ? 1.0 / etot : 0.0;
+    const double fs = ie / P.c;
     for (int g = 0; g < P.G; ++g) {
       const int64_t o = (int64_t)g * P.gs + i, q = (int64_t)g * n + i;
       const double e = P.erad[o], s = P.src ? P.src[o] : 0.0;
-      const double yg = (double)(y[j * nout + 1 + g] * ys[1 + g] + ym[1 + g]);
-      const double r = (e > 0.0 ? e * expm1(fmin(fmax(yg, -30.0), 30.0)) : 0.0) - s;
-      W.r[q] = (ok && etot > 0.0 && isfinite(r)) ? (float)(r / etot) : 0.0f;
+      const float yg = fminf(fmaxf(y[j * nout + 1 + g] * ys[1 + g] + ym[1 + g], -30.0f), 30.0f);
+      const float r = (e > 0.0 ? (float)(e * ie) * expm1f(yg) : 0.0f) - (float)(s * ie);
+      W.r[q] = isfinite(r) ? r : 0.0f;
       W.f[q] = (float)(P.frad[0][o] * fs);
       W.f[(int64_t)P.G * n + q] = (float)(P.frad[1][o] * fs);
       W.f[(int64_t)2 * P.G * n + q] = (float)(P.frad[2][o] * fs);
