@@ -114,9 +114,17 @@ int ensure_device(int *sms) {
   if (!g_ready[dev]) {
     double b[kNB], b3[kNB], invn[kNQ + 1];
     series_tables(b, b3, invn);
-    if (cudaMemcpyToSymbol(c_bern, b, sizeof(b)) != cudaSuccess) return RHD_ECUDA;
-    if (cudaMemcpyToSymbol(c_bern3, b3, sizeof(b3)) != cudaSuccess) return RHD_ECUDA;
-    if (cudaMemcpyToSymbol(c_invn, invn, sizeof(invn)) != cudaSuccess) return RHD_ECUDA;
+    {
+      using namespace planck_table;
+      static double pt[kPlanckWords];
+      for (int k = 0; k <= kDeg; ++k)
+        for (int j = 0; j < kSeg; ++j) pt[k * kSeg + j] = kCoef[k][j];
+      for (int j = 0; j < kSeg; ++j) {
+        pt[(kDeg + 1) * kSeg + j] = kCentre[j];
+        pt[(kDeg + 2) * kSeg + j] = kInvHalf[j];
+      }
+      if (cudaMemcpyToSymbol(c_planck, pt, sizeof(pt)) != cudaSuccess) return RHD_ECUDA;
+    }
     float bf[kNB32], b3f[kNB32], invnf[kNQ32 + 1];
     for (int j = 0; j < kNB32; ++j) {
       bf[j] = (float)b[j];
@@ -370,8 +378,7 @@ namespace rhd {
 namespace {
 
 constexpr int kMaxGB = RHD_MAX_GROUPS_BATCHED;
-const int64_t kTableWords = (int64_t)(sizeof(double) * (kTableArrays * kMaxGB + 1) +
-                                      sizeof(float) * (4 * kMaxGB + 1)) / sizeof(double) + 2;
+const int64_t kTableWords = group_table_words(kMaxGB) + 1;
 
 void ctx_free(rhd_context *c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);

@@ -15,23 +15,28 @@
 
 namespace rhd {
 
-// The table arrays of build_table for G groups starting at sm.
-__device__ __forceinline__ GroupTable table_view(const double *sm, int G) {
+// The group-table arrays of build_table for G groups starting at sm, with
+// the Planck polynomials at pc.
+__device__ __forceinline__ GroupTable table_view(const double *sm, int G, const double *pc) {
   const double *xe = sm, *kbar = sm + G + 1, *ikbar = kbar + G, *rm = ikbar + G, *rp = rm + G,
                *alp = rp + G;
   const float *xef = reinterpret_cast<const float *>(alp + G), *rmf = xef + G + 1, *rpf = rmf + G,
               *alf = rpf + G;
-  return GroupTable{xe, kbar, ikbar, rm, rp, alp, xef, rmf, rpf, alf};
+  return GroupTable{xe, kbar, ikbar, rm, rp, alp, xef, rmf, rpf, alf, pc};
 }
 
-// One CTA per grid: build its table and write it to tables + j * stride.
+__host__ __device__ __forceinline__ int group_table_words(int G) {
+  return (int)(group_table_bytes(G) / sizeof(double)) + 1;
+}
+
+// One CTA per grid: build its group table and write it to tables + j * stride.
 __global__ void tables_kernel(const KParams *__restrict__ grids, double *tables, int64_t stride) {
   extern __shared__ double sm[];
   const KParams &P = grids[blockIdx.x];
   build_table(P, sm);
-  const int words = (int)(table_bytes(P.G) / sizeof(double)) + 1;
+  const int words = group_table_words(P.G);
   double *dst = tables + (int64_t)blockIdx.x * stride;
-  for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = sm[k];
+  for (int k = threadIdx.x; k < words; k += blockDim.x) dst[k] = sm[kPlanckWords + k];
 }
 
 // One cell, start to finish.  MIXED: the FP32 pass runs first and its
@@ -109,6 +114,7 @@ __global__ void batched_kernel(const KParams *__restrict__ grids, const double *
   Arr32<MAXG> B;
   Cell C;
   Cell32 D;
+  load_planck(sm);  // visible after the first __syncthreads below
   for (;;) {
     if (threadIdx.x == 0) {
       const long long it = (long long)atomicAdd(head, 1ULL);
@@ -127,11 +133,11 @@ __global__ void batched_kernel(const KParams *__restrict__ grids, const double *
     if (item >= total) break;
     const KParams &P = grids[j];
     if (j != cur) {
-      const int words = (int)(table_bytes(P.G) / sizeof(double)) + 1;
+      const int words = group_table_words(P.G);
       const double *src = tables + (int64_t)j * table_stride;
-      for (int k = threadIdx.x; k < words; k += blockDim.x) sm[k] = src[k];
+      for (int k = threadIdx.x; k < words; k += blockDim.x) sm[kPlanckWords + k] = src[k];
       cur = j;
-      tab = table_view(sm, P.G);
+      tab = table_view(sm + kPlanckWords, P.G, sm);
     }
     __syncthreads();
     const int64_t c0 = (item - item_off[j]) * (int64_t)cpi;

@@ -13,6 +13,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/rhd.h"
+#include "planck_table.h"
 
 namespace rhd {
 
@@ -63,11 +64,26 @@ struct KParams {
 struct GroupTable {
   const double *xe, *kbar, *ikbar, *rm, *rp, *alpha;
   const float *xef, *rmf, *rpf, *alphaf;
+  const double *pc;  // the Planck-integral polynomials (planck_table.h layout, see edge_tab)
 };
 
+// Shared-memory layout of a CTA's tables: the Planck polynomials first
+// (kPlanckWords doubles: coefficients [kDeg + 1][kSeg], centres [kSeg],
+// inverse half-widths [kSeg]), then the group table of the grid.
+constexpr int kPlanckWords = (planck_table::kDeg + 3) * planck_table::kSeg;
 constexpr int kTableArrays = 6;
-__host__ __device__ __forceinline__ size_t table_bytes(int G) {
+__host__ __device__ __forceinline__ size_t group_table_bytes(int G) {
   return sizeof(double) * (kTableArrays * G + 1) + sizeof(float) * (4 * G + 1);
+}
+__host__ __device__ __forceinline__ size_t table_bytes(int G) {
+  return sizeof(double) * kPlanckWords + group_table_bytes(G);
+}
+
+__constant__ double c_planck[kPlanckWords];
+
+// Copy the Planck polynomials to sm (all threads; the caller synchronises).
+__device__ __forceinline__ void load_planck(double *sm) {
+  for (int t = threadIdx.x; t < kPlanckWords; t += blockDim.x) sm[t] = c_planck[t];
 }
 
 // khat from the piecewise law; right = 1 takes the segment above a breakpoint
@@ -90,8 +106,10 @@ __device__ inline double ppl_mean_factor(double a, double lr) {
 
 // Build the group table in shared memory (step a2): all threads of the CTA
 // take part; ends with __syncthreads().
-__device__ inline GroupTable build_table(const KParams &P, double *sm) {
+__device__ inline GroupTable build_table(const KParams &P, double *smem) {
   const int G = P.G;
+  load_planck(smem);
+  double *sm = smem + kPlanckWords;
   double *xe = sm, *kbar = sm + G + 1, *ikbar = kbar + G, *rm = ikbar + G, *rp = rm + G,
          *alp = rp + G;
   for (int t = threadIdx.x; t <= G; t += blockDim.x) {
@@ -144,25 +162,22 @@ __device__ inline GroupTable build_table(const KParams &P, double *sm) {
     alf[t] = (float)alp[t];
   }
   __syncthreads();
-  return GroupTable{xe, kbar, ikbar, rm, rp, alp, xef, rmf, rpf, alf};
+  return GroupTable{xe, kbar, ikbar, rm, rp, alp, xef, rmf, rpf, alf, smem};
 }
 
-// Series coefficients (set once per device by the host):
-//   c_bern[j-1]  = B_2j / (2j)!          x/(e^x-1) = 1 - x/2 + sum_j c_bern x^(2j)
-//   c_bern3[j-1] = B_2j / ((2j)! (2j+3))  int_0^x t^3/(e^t-1) dt
-//                                          = x^3/3 - x^4/8 + x^3 sum_j c_bern3 x^(2j)
-//   c_invn[n]    = 1/n
 // (This header is compiled into exactly one translation unit, rhd.cu.)
-__constant__ double c_bern[kNB];
-__constant__ double c_bern3[kNB];
-__constant__ double c_invn[kNQ + 1];
 
 // FP64 edge values: pq = P(x) when low (x < 2), else Q(x) = 1 - P(x);
 // d = D(x) = (15/pi^4) x^4/(e^x-1) and ed = x dD/dx = D (4 - x e^x/(e^x-1)).
-// Small x: Bernoulli series (no transcendental); large x: sum_n e^(-n x)
-// (x^3/n + 3x^2/n^2 + 6x/n^3 + 6/n^4) (Widger & Woodall 1976) with the terms
-// cut where e^(-(n-1)x) < 1e-17.
-__device__ __forceinline__ void edge_fp64(double x, double &pq, double &d, double &ed, bool &low) {
+// One expm1 gives x/(e^x - 1) and e^-x = 1/(expm1(x) + 1); P and Q come from the
+// piecewise polynomials of planck_table.h (P = 15/pi^4 x^3 g(x) below x = 2,
+// Q = 15/pi^4 x^3 e^-x h(x) above), the segment read off the exponent and two
+// leading mantissa bits of x: every x takes the same instructions, so the
+// lanes of a warp never split on the value of x.  Beyond the table (x >= 1024)
+// e^-x is 0 in FP64 and the polynomial is evaluated at its centre.
+__device__ __forceinline__ void edge_tab(const double *pc, double x, double &pq, double &d,
+                                         double &ed, bool &low) {
+  using namespace planck_table;
   if (!(x > 0.0)) {
     pq = 0.0;
     d = 0.0;
@@ -177,40 +192,23 @@ __device__ __forceinline__ void edge_fp64(double x, double &pq, double &d, doubl
     low = false;
     return;
   }
-  if (x < kXSplit) {
-    const double z = x * x;
-    double s1 = c_bern[kNB - 1], s3 = c_bern3[kNB - 1];
+  const double em = expm1(x);
+  const double xr = x / em;          // x/(e^x - 1)
+  const double emx = 1.0 / (em + 1.0);  // e^-x
+  const double x3 = x * x * x;
+  d = kPlanckNorm * x3 * xr;
+  ed = d * (4.0 - xr - x);  // x e^x/(e^x-1) = x/(e^x-1) + x
+  const int hi = __double2hiint(x);
+  const int e = ((hi >> 20) & 0x7FF) - 1023;
+  int sg = 1 + (e - kEMin) * kSub + ((hi >> 18) & 3);
+  sg = e < kEMin ? 0 : (e > kEMax ? kSeg - 1 : sg);
+  const double *cen = pc + (kDeg + 1) * kSeg, *ih = cen + kSeg;
+  const double u = e > kEMax ? 0.0 : (x - cen[sg]) * ih[sg];
+  double p = pc[kDeg * kSeg + sg];
 #pragma unroll
-    for (int j = kNB - 2; j >= 0; --j) {
-      s1 = fma(s1, z, c_bern[j]);
-      s3 = fma(s3, z, c_bern3[j]);
-    }
-    const double x3 = z * x;
-    const double xr = fma(z, s1, fma(-0.5, x, 1.0));  // x/(e^x-1)
-    pq = kPlanckNorm * x3 * fma(z, s3, fma(-0.125, x, 1.0 / 3.0));
-    d = kPlanckNorm * x3 * xr;
-    ed = d * (4.0 - xr - x);  // x e^x/(e^x-1) = x/(e^x-1) + x
-    low = true;
-  } else {
-    const double e1 = exp(-x);
-    int nmax = (int)(39.0 / x) + 1;
-    if (nmax > kNQ) nmax = kNQ;
-    const double x2 = x * x, x3 = x2 * x, sx = 6.0 * x, tx2 = 3.0 * x2;
-    double en = 1.0, sum = 0.0;
-    for (int n = 1; n <= nmax; ++n) {
-      en *= e1;
-      const double inv = c_invn[n];
-      double h = fma(6.0, inv, sx);
-      h = fma(h, inv, tx2);
-      h = fma(h, inv, x3);
-      sum = fma(en * inv, h, sum);
-    }
-    pq = kPlanckNorm * sum;
-    const double inv1 = 1.0 / (1.0 - e1);
-    d = kPlanckNorm * x3 * x * e1 * inv1;
-    ed = d * (4.0 - x * inv1);
-    low = false;
-  }
+  for (int k = kDeg - 1; k >= 0; --k) p = fma(p, u, pc[k * kSeg + sg]);
+  low = x < kXSplit;
+  pq = kPlanckNorm * x3 * p * (low ? 1.0 : emx);
 }
 
 // Planck fraction of the band between a lower and an upper edge value.

@@ -171,12 +171,12 @@ __device__ __forceinline__ int inner_step(const KParams &P, const GroupTable &ta
   const double invT = 1.0 / T;
   double pqL, dL, eL;
   bool lowL;
-  edge_fp64(tab.xe[0] * invT, pqL, dL, eL, lowL);
+  edge_tab(tab.pc, tab.xe[0] * invT, pqL, dL, eL, lowL);
   double sumR = 0.0, sFRe = 0.0, sde = 0.0, sabs = 0.0;
   for (int g = 0; g < G; ++g) {
     double pqU, dU, eU;
     bool lowU;
-    edge_fp64(tab.xe[g + 1] * invT, pqU, dU, eU, lowU);
+    edge_tab(tab.pc, tab.xe[g + 1] * invT, pqU, dU, eU, lowU);
     const int64_t o = (int64_t)g * P.gs + i;
     const double dP = band_fp64(pqL, lowL, pqU, lowU);
     const double dD = dU - dL;
