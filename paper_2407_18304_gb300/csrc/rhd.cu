@@ -13,6 +13,7 @@
 #include "rhd_fp64.cuh"
 #include "rhd_mixed.cuh"
 #include "rhd_batched.cuh"
+#include "rhd_warp.cuh"
 
 namespace rhd {
 namespace {
@@ -256,6 +257,34 @@ int persistent_blocks(K kernel, size_t smem, int sms, int64_t n, int threads) {
   return (int)(want < full ? want : full);
 }
 
+template <int L, int GPL>
+void launch_warp(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
+  const int threads = 128;
+  const size_t smem = table_bytes(kp.G);
+  const int b = persistent_blocks(solve_warp_kernel<L, GPL>, smem, sms, kp.n * L, threads);
+  solve_warp_kernel<L, GPL><<<b, threads, smem, st>>>(kp, W);
+}
+
+template <int MAXG>
+void launch_thread(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
+  const int threads = 128;
+  const size_t smem = table_bytes(kp.G);
+  const int b = persistent_blocks(solve_fp64_kernel<MAXG>, smem, sms, kp.n, threads);
+  solve_fp64_kernel<MAXG><<<b, threads, smem, st>>>(kp, W);
+}
+
+// The FP64 passes (cold, or from the warm start in W): one cell per thread
+// up to 32 groups, a whole warp per cell from 33 to 128 groups
+// (rhd_warp.cuh; the split measured on GB300), one cell per thread again past
+// 128 groups, where a lane's share of the groups no longer fits in registers.
+void launch_fp64_passes(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
+  if (kp.G <= 16) launch_thread<16>(kp, W, sms, st);
+  else if (kp.G <= 32) launch_thread<32>(kp, W, sms, st);
+  else if (kp.G <= 64) launch_warp<32, 2>(kp, W, sms, st);
+  else if (kp.G <= 128) launch_warp<32, 4>(kp, W, sms, st);
+  else launch_thread<kMaxG>(kp, W, sms, st);
+}
+
 template <int MAXG>
 int launch_mixed(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int sms,
                  cudaStream_t st) {
@@ -264,8 +293,7 @@ int launch_mixed(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int 
   const int ba = persistent_blocks(warm_fp32_kernel<MAXG>, smem, sms, kp.n, threads);
   const WarmStart none{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
   warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo, none);
-  const int bb = persistent_blocks(solve_fp64_kernel<MAXG>, smem, sms, kp.n, threads);
-  solve_fp64_kernel<MAXG><<<bb, threads, smem, st>>>(kp, wi);
+  launch_fp64_passes(kp, wi, sms, st);
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
 }
 
@@ -281,8 +309,7 @@ int launch_warm_g(const KParams &kp, int precision, const WarmOut &wo, const War
     const int ba = persistent_blocks(warm_fp32_kernel<MAXG>, smem, sms, kp.n, threads);
     warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo, wi);
   }
-  const int bb = persistent_blocks(solve_fp64_kernel<MAXG>, smem, sms, kp.n, threads);
-  solve_fp64_kernel<MAXG><<<bb, threads, smem, st>>>(kp, wi);
+  launch_fp64_passes(kp, wi, sms, st);
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
 }
 
@@ -294,12 +321,9 @@ int launch_warm(const KParams &kp, int precision, const WarmOut &wo, const WarmS
 
 template <int MAXG>
 int launch_g(const KParams &kp, int precision, int sms, cudaStream_t st) {
-  const int threads = 128;
-  const size_t smem = table_bytes(kp.G);
   if (precision == RHD_FP64) {
     const WarmStart cold{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-    const int b = persistent_blocks(solve_fp64_kernel<MAXG>, smem, sms, kp.n, threads);
-    solve_fp64_kernel<MAXG><<<b, threads, smem, st>>>(kp, cold);
+    launch_fp64_passes(kp, cold, sms, st);
   } else {
     WarmOut wo;
     WarmStart wi;
