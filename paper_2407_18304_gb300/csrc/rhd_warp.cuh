@@ -2,8 +2,9 @@
 //
 // L lanes (a whole warp, or an aligned segment of 16 or 8 lanes) solve one
 // cell together: lane l owns the groups g = l + L j (j < GPL) and keeps all
-// their per-group quantities in registers (including E_g^t + S_g and F_g^t,
-// loaded once per cell), evaluates the edges e = l + L j (j <= GPL) and gets
+// their per-group quantities in registers (including E_g^t + S_g, loaded once
+// per cell; F_g^t is re-read from L2 by the outer step), evaluates the edges
+// e = l + L j (j <= GPL) and gets
 // the upper edge of each of its groups from the neighbouring lane by shuffle.
 // The sums over groups of eq. matrix's elimination, of the write-back and of
 // the momentum update are xor-butterflies inside the segment: every lane of
@@ -24,8 +25,7 @@ struct WCell {
   int nit, stat, it, outer, slow;
   double R[GPL], w[GPL], FR[GPL], dg[GPL], qe[GPL], bq[GPL], dnx[GPL], qF[GPL];
   double E0[GPL];     // E_g^t + S_g
-  double Fk[GPL][3];  // flux of the current outer iterate
-  double Ft[GPL][3];  // flux at the start of the step
+  double Fk[GPL][3];  // flux of the current outer iterate (F^t is re-read from global memory)
 };
 
 template <int L>
@@ -63,12 +63,11 @@ __device__ __forceinline__ bool wload(const KParams &P, int64_t i, int l, unsign
       valid = valid && isfinite(e) && isfinite(s) && isfinite(f0) && isfinite(f1) && isfinite(f2);
       C.E0[j] = e + s;
       sumE0 += e + s;
-      C.Ft[j][0] = C.Fk[j][0] = f0;
-      C.Ft[j][1] = C.Fk[j][1] = f1;
-      C.Ft[j][2] = C.Fk[j][2] = f2;
+      C.Fk[j][0] = f0;
+      C.Fk[j][1] = f1;
+      C.Fk[j][2] = f2;
     } else {
       C.E0[j] = 0.0;
-      C.Ft[j][0] = C.Ft[j][1] = C.Ft[j][2] = 0.0;
       C.Fk[j][0] = C.Fk[j][1] = C.Fk[j][2] = 0.0;
     }
   }
@@ -161,12 +160,29 @@ __device__ __forceinline__ int winner_step(const KParams &P, const GroupTable &t
   if (P.temp_exp != 0.0) wset_tau(P, tab, l, C, C.chi0s * pow(T / P.T_ref, P.temp_exp));
   const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
   const double invT = 1.0 / T;
-  // a4: the edges e = l + L jj
+  // a4: the edges e = l + L jj.  When the groups fill the lanes exactly the
+  // last slot holds only the top edge x_G (lane 0); x_G is the same for all
+  // lanes of the cell, and for 40 <= x_G < inf the n >= 2 terms of Q and the
+  // 1/(1 - e^-x) factor of D are below e^-40 = 4e-18 relative, so that slot
+  // takes the short exact forms Q = 15/pi^4 e^-x (x^3 + 3x^2 + 6x + 6),
+  // D = 15/pi^4 x^4 e^-x, x D' = D (4 - x) without splitting the lanes.
   double pqE[NE], dE_[NE], eE[NE];
   bool lowE[NE];
 #pragma unroll
   for (int jj = 0; jj < NE; ++jj) {
     const int e = l + L * jj;
+    if (jj == NE - 1 && G == L * GPL) {
+      const double xg = tab.xe[G] * invT;
+      if (xg >= 40.0 && xg < HUGE_VAL) {
+        const double em = exp(-xg);
+        const double x2 = xg * xg;
+        pqE[jj] = kPlanckNorm * em * (x2 * xg + 3.0 * x2 + 6.0 * xg + 6.0);
+        dE_[jj] = kPlanckNorm * em * x2 * x2;
+        eE[jj] = dE_[jj] * (4.0 - xg);
+        lowE[jj] = false;
+        continue;
+      }
+    }
     edge_tab(tab.pc, e <= G ? tab.xe[e] * invT : 1.0, pqE[jj], dE_[jj], eE[jj], lowE[jj]);
   }
   double sumR = 0.0, sFRe = 0.0, sde = 0.0, sabs = 0.0;
@@ -274,6 +290,8 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
     if (g >= G) continue;
     const double Enew = C.E0[j] + C.R[j];
     const double chiB = C.cs * tab.kbar[g], a = tab.alpha[g];
+    const int64_t o = (int64_t)g * P.gs + C.i;
+    const double ft[3] = {P.frad[0][o], P.frad[1][o], P.frad[2][o]};
     double vp0, vp1, vp2;
     closure_vP<double>(P.closure, c, Enew, C.Fk[j][0], C.Fk[j][1], C.Fk[j][2], v[0], v[1], v[2],
                        vp0, vp1, vp2);
@@ -281,12 +299,12 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
     const double inv = 1.0 / (1.0 + tdt * chiB * C.qF[j]);
     const double kap = tdt * (1.0 + a) * chiB * inv;
     newton = newton || 10.0 * fabs(kap) * vmag > c;
-    const double n0 = (C.Ft[j][0] + tdt * v[0] * srcg) * inv + kap * vp0;
-    const double n1 = (C.Ft[j][1] + tdt * v[1] * srcg) * inv + kap * vp1;
-    const double n2 = (C.Ft[j][2] + tdt * v[2] * srcg) * inv + kap * vp2;
-    dF[0] += n0 - C.Ft[j][0];
-    dF[1] += n1 - C.Ft[j][1];
-    dF[2] += n2 - C.Ft[j][2];
+    const double n0 = (ft[0] + tdt * v[0] * srcg) * inv + kap * vp0;
+    const double n1 = (ft[1] + tdt * v[1] * srcg) * inv + kap * vp1;
+    const double n2 = (ft[2] + tdt * v[2] * srcg) * inv + kap * vp2;
+    dF[0] += n0 - ft[0];
+    dF[1] += n1 - ft[1];
+    dF[2] += n2 - ft[2];
     fchg += fabs(n0 - C.Fk[j][0]) + fabs(n1 - C.Fk[j][1]) + fabs(n2 - C.Fk[j][2]);
     C.Fk[j][0] = n0;
     C.Fk[j][1] = n1;
@@ -303,9 +321,10 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
       const double kap = tdt * (1.0 + tab.alpha[g]) * chiB * inv;
       if (!(10.0 * fabs(kap) * vmag > c)) continue;
       const double srcg = chiB * (C.bq[j] - C.dnx[j] * (1.0 / 3.0));
+      const int64_t o = (int64_t)g * P.gs + C.i;
       const Vec3<double> F = flux_newton<double>(
-          c, C.E0[j] + C.R[j], kap, (C.Ft[j][0] + tdt * v[0] * srcg) * inv,
-          (C.Ft[j][1] + tdt * v[1] * srcg) * inv, (C.Ft[j][2] + tdt * v[2] * srcg) * inv, v[0],
+          c, C.E0[j] + C.R[j], kap, (P.frad[0][o] + tdt * v[0] * srcg) * inv,
+          (P.frad[1][o] + tdt * v[1] * srcg) * inv, (P.frad[2][o] + tdt * v[2] * srcg) * inv, v[0],
           v[1], v[2], C.Fk[j][0], C.Fk[j][1], C.Fk[j][2], 1e-14);
       dF[0] += F.x - C.Fk[j][0];
       dF[1] += F.y - C.Fk[j][1];
