@@ -226,14 +226,14 @@ __device__ __forceinline__ void closure_vP(int closure, R c, R E, R F0, R F1, R 
   R iso = R(1) / R(3), dir = R(0);
   R n0 = R(0), n1 = R(0), n2 = R(0);
   if (closure == RHD_M1 && E > R(0) && fn2 > R(0)) {
-    const R fn = sqrt(fn2);
+    const R inv = rsqrt(fn2);  // 1/|F|
+    const R fn = fn2 * inv;
     R f = fn / (c * E);
     if (f > R(1)) f = R(1);
     const R f2 = f * f;
     const R chi = (R(3) + R(4) * f2) / (R(5) + R(2) * sqrt(R(4) - R(3) * f2));
     iso = R(0.5) * (R(1) - chi);
     dir = R(0.5) * (R(3) * chi - R(1));
-    const R inv = R(1) / fn;
     n0 = F0 * inv;
     n1 = F1 * inv;
     n2 = F2 * inv;

@@ -54,6 +54,16 @@ __device__ __forceinline__ R chiF_ratio(R b, R aT4, R dD, R a, R rm, R rp, R dL,
   return fmin(fmax(q, lo), hi);
 }
 
+// eq. chiDiff alone (no T-derivative), held as in chiF_ratio.
+template <typename R>
+__device__ __forceinline__ R chiF_q(R b, R aT4, R dD, R a, R rm, R rp, R dL, R dU) {
+  const R X = rp * dU - rm * dL;
+  const R den = R(4.0 / 3.0) * b - R(1.0 / 3.0) * aT4 * dD;
+  R q = R(1);
+  if (den > R(0)) q = (R(4.0 / 3.0) * b + R(1.0 / 3.0) * (a * b - aT4 * X)) / den;
+  return fmin(fmax(q, fmin(rm, rp)), fmax(rm, rp));
+}
+
 // Per-cell constants and the FP64 iterate of one cell.
 struct Cell {
   int64_t i;
