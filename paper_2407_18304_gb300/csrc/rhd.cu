@@ -14,6 +14,7 @@
 #include "rhd_mixed.cuh"
 #include "rhd_batched.cuh"
 #include "rhd_warp.cuh"
+#include "rhd_warp32.cuh"
 
 namespace rhd {
 namespace {
@@ -285,14 +286,28 @@ void launch_fp64_passes(const KParams &kp, const WarmStart &W, int sms, cudaStre
   else launch_thread<kMaxG>(kp, W, sms, st);
 }
 
+// The FP32 passes of the mixed form (writing the warm start wo; starting
+// from S where S.r is set): one cell per thread up to 32 groups and past 64,
+// a warp per cell in between (rhd_warp32.cuh).
+template <int MAXG>
+void launch_fp32_passes(const KParams &kp, const WarmOut &wo, const WarmStart &S, int sms,
+                        cudaStream_t st) {
+  const int threads = 128;
+  const size_t smem = table_bytes(kp.G);
+  if (kp.G > 32 && kp.G <= 64) {
+    const int b = persistent_blocks(warm_warp32_kernel<32, 2>, smem, sms, kp.n * 32, threads);
+    warm_warp32_kernel<32, 2><<<b, threads, smem, st>>>(kp, wo, S);
+    return;
+  }
+  const int ba = persistent_blocks(warm_fp32_kernel<MAXG>, smem, sms, kp.n, threads);
+  warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo, S);
+}
+
 template <int MAXG>
 int launch_mixed(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int sms,
                  cudaStream_t st) {
-  const int threads = 128;
-  const size_t smem = table_bytes(kp.G);
-  const int ba = persistent_blocks(warm_fp32_kernel<MAXG>, smem, sms, kp.n, threads);
   const WarmStart none{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
-  warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo, none);
+  launch_fp32_passes<MAXG>(kp, wo, none, sms, st);
   launch_fp64_passes(kp, wi, sms, st);
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
 }
@@ -303,12 +318,7 @@ int launch_mixed(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int 
 template <int MAXG>
 int launch_warm_g(const KParams &kp, int precision, const WarmOut &wo, const WarmStart &wi,
                   int sms, cudaStream_t st) {
-  const int threads = 128;
-  const size_t smem = table_bytes(kp.G);
-  if (precision == RHD_MIXED) {
-    const int ba = persistent_blocks(warm_fp32_kernel<MAXG>, smem, sms, kp.n, threads);
-    warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo, wi);
-  }
+  if (precision == RHD_MIXED) launch_fp32_passes<MAXG>(kp, wo, wi, sms, st);
   launch_fp64_passes(kp, wi, sms, st);
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
 }

@@ -75,3 +75,27 @@ def test_segments_tile_the_line():
     assert lo[0] == 0.0 and hi[0] == 2.0 ** ints["kEMin"]
     assert np.all(np.abs(hi[:-1] - lo[1:]) <= 1e-15 * hi[:-1])
     assert hi[-1] == 2.0 ** (ints["kEMax"] + 1)
+
+
+def test_fp32_truncation_is_below_fp32_resolution():
+    """The FP32 passes use the same polynomials cut to degree 7 in FP32."""
+    ints, cen, ih, coef = _table()
+    f32 = np.float32
+    worst = 0.0
+    for x in np.logspace(-4, math.log10(80.0), 2001):
+        xf = f32(x)
+        hi = struct.unpack("<i", struct.pack("<f", xf))[0]
+        e = ((hi >> 23) & 0xFF) - 127
+        s = 1 + (e - ints["kEMin"]) * ints["kSub"] + ((hi >> 21) & 3)
+        s = 0 if e < ints["kEMin"] else (ints["kSeg"] - 1 if e > ints["kEMax"] else s)
+        u = (xf - f32(cen[s])) * f32(ih[s])
+        p = f32(coef[7, s])
+        for k in range(6, -1, -1):
+            p = f32(p * u + f32(coef[k, s]))
+        x = float(xf)
+        x3 = x * x * x
+        v = K * x3 * float(p) if x < 2.0 else K * x3 * float(p) * math.exp(-x)
+        ref = O.planck_P(x) if x < 2.0 else O.planck_Q(x)
+        worst = max(worst, abs(v - ref) / ref)
+    print(f"worst FP32 relative error {worst:.2e}")
+    assert worst < 1e-6
