@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--n-cells", type=int, default=None, help="override the cell count")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cell-per-thread", action="store_true",
+                    help="one cell per thread in every pass (the mapping whose operation "
+                         "counts define the algorithmic flops; slower at 33-128 groups)")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="time the solver from the cold start (no learned warm start)")
     ap.add_argument("--sur-train-cells", type=int, default=1 << 21)
@@ -155,17 +158,27 @@ def fp_peaks() -> dict:
         return {"error": str(e)}
 
 
-# FP64 flops (DFMA counted twice) per cell-group of one call, from the SASS
-# instruction counts ncu reports for the same workload on a 65536-cell sample
-# (profiles/solve_full_256cube_ng64.md); a property of the workload and the
-# algorithm, applied to the full-size grid of the same distribution.
-FP64_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1882.6,
-                     ("full_256cube_ng64", "mixed"): 1866.1,
-                     ("full_256cube_ng64", "fp64"): 3311.7}
-# DRAM bytes (read + write) per cell-group of one call from the same capture
-TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 3584.0,
-                  ("full_256cube_ng64", "mixed"): 3605.0,
-                  ("full_256cube_ng64", "fp64"): 3260.0}
+# Algorithmic FP64 flops (DFMA counted twice) per cell-group, from the SASS
+# instruction counts ncu reports on a 65536-cell sample of the same workload
+# with one cell per thread (RHD_CELL_PER_THREAD: every instruction is one
+# cell's own work; the default warp-per-cell mapping executes about 50 % more
+# FP64 instructions, replicated per-cell work); profiles/solve_full_256cube_ng64.md.
+# The FP64-pass kernel (the one that dominates a call, timed live below):
+FP64_PASS_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1635.9,
+                          ("full_256cube_ng64", "mixed"): 1641.3,
+                          ("full_256cube_ng64", "fp64"): 2926.0,
+                          ("full_256cube_ng64", "fp64+surrogate"): 2740.3}
+# ... and the whole call (inference, FP32 passes, FP64 passes)
+CALL_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1669.2,
+                     ("full_256cube_ng64", "mixed"): 1659.8,
+                     ("full_256cube_ng64", "fp64"): 2926.0,
+                     ("full_256cube_ng64", "fp64+surrogate"): 2755.9}
+# DRAM bytes (read + write) per cell-group of one launch of the FP64-pass
+# kernel in the default mapping, from the same capture
+FP64_PASS_TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 69.1,
+                            ("full_256cube_ng64", "mixed"): 69.4,
+                            ("full_256cube_ng64", "fp64"): 52.0,
+                            ("full_256cube_ng64", "fp64+surrogate"): 69.2}
 
 
 def train_surrogate(args, w, dev, rank):
@@ -208,13 +221,17 @@ def run_ours(args, ws, rank):
         for k in ("mom", "egas", "erad", "frad"):
             st[k].copy_(pristine[k])
 
+    flags = rhd.CELL_PER_THREAD if args.cell_per_thread else 0
+
     def call(p, warm):
         args_ = dict(dt=w.dt, c_v=w.c_v, consts=w.consts, precision=p, status=status,
-                     iters=iters, stream=stream)
+                     iters=iters, stream=stream, flags=flags)
         if warm:
             sur.source_update(st, w.edges, w.law, **args_)
         else:
             rhd.source_update(st, w.edges, w.law, **args_)
+
+    kernel_ms = [0.0, 0]  # mean FP64-pass kernel duration of the headline loop, launches
 
     def timed(p, warm, steps, warmup, sample_clocks=False):
         """warmup + steps solves; per-step CUDA-event times and outcome."""
@@ -229,6 +246,8 @@ def run_ours(args, ws, rank):
             clocks.start()
         barrier(ws)
         torch.cuda.synchronize()
+        if sample_clocks:
+            rhd.profile_start()  # events around the FP64-pass kernel of each call
         t0 = time.perf_counter()
         for k in range(steps):
             restore()
@@ -244,6 +263,9 @@ def run_ours(args, ws, rank):
         barrier(ws)
         wall = time.perf_counter() - t0
         clk = clocks.stop() if sample_clocks else None
+        if sample_clocks:
+            nl, kms = rhd.profile_stop()
+            kernel_ms[:] = [kms / max(1, nl), nl]
         ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
         stat = status.cpu().numpy()
         it = iters.cpu().numpy().astype(np.int64)
@@ -276,6 +298,7 @@ def run_ours(args, ws, rank):
            "dtype": "f64" if prec == rhd.FP64 else ("f32+f64+bf16" if use_sur else "f32+f64"),
            "data": "synthetic (seeded; recipe in DESIGN.md)",
            "config": {"workload": name, "cells": n, "n_groups": G, "form": form,
+                      "mapping": "cell per thread" if args.cell_per_thread else "warp per cell",
                       "precision": args.precision, "tol": 1e-11, "tol_outer": 1e-13,
                       "l2": "state restored from a pristine copy before each step (2x state > L2)",
                       "parallelism": f"weak x{ws}, no collective"},
@@ -292,27 +315,36 @@ def run_ours(args, ws, rank):
             res["mixed_form"] = side(rhd.MIXED, False, args.fp64_steps)
             res["fp64_surrogate_form"] = side(rhd.FP64, True, args.fp64_steps)
 
-    # roofline of the solve (FP64-issue bound)
+    # roofline of the dominant kernel (the FP64 passes; FP64-issue bound, see
+    # the design doc section 7), its duration measured live with CUDA events
     peaks = fp_peaks()
     res["fp_peaks_measured"] = peaks
-    mean_launch_s = t_dev / args.steps
+    mean_call_s = t_dev / args.steps
     bytes_alg = n * (G * 64 + 82)  # in+out FP64 SoA per call
-    hbm_frac = bytes_alg / mean_launch_s / 1e9 / _measured_hbm()
-    per_cg = FP64_FLOPS_PER_CG.get((name, form))
-    if per_cg is not None:
+    hbm_frac = bytes_alg / mean_call_s / 1e9 / _measured_hbm()
+    key = (name, form)
+    per_cg = FP64_PASS_FLOPS_PER_CG.get(key)
+    if per_cg is not None and kernel_ms[1] > 0:
         peak = peaks.get("fp64_fma_tflops") or 1.25
-        ach = per_cg * n * G / mean_launch_s / 1e12
-        tr = TRAFFIC_PER_CG.get((name, form))
-        res["roofline"] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                           "frac": ach / peak,
-                           "traffic": tr * n * G if tr is not None else None,
-                           "what": "FP64 flops (DFMA = 2) per call / call time, vs the DFMA peak",
-                           "peak_source": ("measured fp_peak DFMA loop" if "fp64_fma_tflops" in peaks
-                                           else "nominal 1.25 TFLOP/s"),
-                           "fp64_flops_per_cell_group": per_cg, "hbm_frac": hbm_frac}
+        k_s = kernel_ms[0] / 1e3
+        ach = per_cg * n * G / k_s / 1e12
+        tr = FP64_PASS_TRAFFIC_PER_CG.get(key)
+        res["roofline"] = {
+            "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "traffic": tr * n * G if tr is not None else None,
+            "kernel": "FP64 passes (solve_warp_kernel<32,2>)",
+            "kernel_ms": kernel_ms[0], "kernel_launches_timed": kernel_ms[1],
+            "what": "algorithmic FP64 flops (DFMA = 2) of the kernel per launch / its CUDA-event "
+                    "duration, vs the DFMA peak",
+            "peak_source": ("measured fp_peak DFMA loop (nominal 152 SMs x 4 flop/clk x 2.07 GHz "
+                            "= 1.26 TFLOP/s)" if "fp64_fma_tflops" in peaks
+                            else "nominal 1.25 TFLOP/s"),
+            "fp64_flops_per_cell_group": per_cg,
+            "call_fp64_tflops": CALL_FLOPS_PER_CG.get(key, 0.0) * n * G / mean_call_s / 1e12,
+            "hbm_frac_of_call": hbm_frac}
     else:
         peak = _measured_hbm()
-        ach = bytes_alg / mean_launch_s / 1e9
+        ach = bytes_alg / mean_call_s / 1e9
         res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
                            "frac": ach / peak, "traffic": None,
                            "peak_source": "MEASURED_PEAKS.json hbm_gbs"}

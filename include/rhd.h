@@ -66,6 +66,11 @@ extern "C" {
                             the change of the v,F-terms of R_g is below tol_outer times
                             that group's own energy (the paper's test is relative to
                             E_tot, which leaves groups far below E_tot loosely converged) */
+#define RHD_CELL_PER_THREAD 4 /* run every pass with one cell per thread (the other mapping
+                                 spreads a cell's 33..128 groups over a warp's lanes; same
+                                 equations and results to rounding, slower at those sizes;
+                                 for comparison and for counting the algorithm's operations
+                                 without the lane-replicated per-cell work) */
 #define RHD_FLUX_TEST 2  /* the outer iteration also stops only when the change of the
                             group fluxes, sum_g |F_g,new - F_g,old|_1 / c, is below
                             tol_outer E_tot (the paper's test sees F_g only through the
@@ -104,7 +109,7 @@ typedef struct {
   int32_t max_outer;    /* outer-iteration cap; <= 0 selects 16 */
   int32_t precision;    /* RHD_FP64 | RHD_MIXED */
   int32_t closure;      /* RHD_M1 | RHD_EDDINGTON */
-  int32_t flags;        /* 0 (the paper's tests) or RHD_GROUP_TEST | RHD_FLUX_TEST */
+  int32_t flags;        /* 0, or RHD_GROUP_TEST | RHD_FLUX_TEST | RHD_CELL_PER_THREAD */
 } rhd_state_t;
 
 /* Lab-frame group edges (Sec. 2.1, eq. Qg: contiguous groups).  HOST array of
@@ -261,6 +266,16 @@ int rhd_surrogate_error(rhd_surrogate_t *s, int32_t *flag);
 int rhd_source_update_warm(rhd_surrogate_t *s, rhd_state_t *state, const rhd_groups_t *groups,
                            const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
                            void *stream);
+
+/* ---- Benchmark support -------------------------------------------------------
+ * Time the FP64-pass kernel of every rhd_source_update / rhd_source_update_warm
+ * call this thread makes between rhd_profile_start and rhd_profile_stop, with
+ * CUDA events recorded on the call's stream right before and after that launch
+ * (the kernel that dominates a call).  rhd_profile_stop synchronizes those
+ * events and returns the number of timed launches and their summed duration in
+ * milliseconds.  Not part of the method; no counterpart in the paper. */
+int rhd_profile_start(void);
+int rhd_profile_stop(int32_t *launches, double *total_ms);
 
 /* The mixed-precision form without any device allocation.  Some callers
  * cannot let a library call cudaMalloc: a host that hands every byte of HBM

@@ -167,7 +167,7 @@ int pack(const rhd_state_t *s, const rhd_groups_t *gr, const rhd_opacity_law_t *
   if (!std::isfinite(dt) || dt < 0.0) return RHD_EINVAL;
   if (s->precision != RHD_FP64 && s->precision != RHD_MIXED) return RHD_EINVAL;
   if (s->closure != RHD_M1 && s->closure != RHD_EDDINGTON) return RHD_EINVAL;
-  if (s->flags & ~(RHD_GROUP_TEST | RHD_FLUX_TEST)) return RHD_EINVAL;
+  if (s->flags & ~(RHD_GROUP_TEST | RHD_FLUX_TEST | RHD_CELL_PER_THREAD)) return RHD_EINVAL;
   if (law->mode != RHD_PPL_FIXED && law->mode != RHD_PC) return RHD_ELAW;
   // edges: strictly increasing; PPL needs finite positive edges
   for (int e = 0; e <= G; ++e) {
@@ -274,11 +274,35 @@ void launch_thread(const KParams &kp, const WarmStart &W, int sms, cudaStream_t 
   solve_fp64_kernel<MAXG><<<b, threads, smem, st>>>(kp, W);
 }
 
+// rhd_profile_start/stop: event pairs around the FP64-pass launches of this thread.
+thread_local bool t_profiling = false;
+thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_events;
+
+void launch_fp64_passes_impl(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st);
+
+void launch_fp64_passes(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (t_profiling && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
+    cudaEventRecord(a, st);
+    launch_fp64_passes_impl(kp, W, sms, st);
+    cudaEventRecord(b, st);
+    t_events.emplace_back(a, b);
+    return;
+  }
+  launch_fp64_passes_impl(kp, W, sms, st);
+}
+
 // The FP64 passes (cold, or from the warm start in W): one cell per thread
 // up to 32 groups, a whole warp per cell from 33 to 128 groups
 // (rhd_warp.cuh; the split measured on GB300), one cell per thread again past
 // 128 groups, where a lane's share of the groups no longer fits in registers.
-void launch_fp64_passes(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
+void launch_fp64_passes_impl(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
+  if (kp.flags & RHD_CELL_PER_THREAD) {
+    if (kp.G <= 16) launch_thread<16>(kp, W, sms, st);
+    else if (kp.G <= 64) launch_thread<64>(kp, W, sms, st);
+    else launch_thread<kMaxG>(kp, W, sms, st);
+    return;
+  }
   if (kp.G <= 16) launch_thread<16>(kp, W, sms, st);
   else if (kp.G <= 32) launch_thread<32>(kp, W, sms, st);
   else if (kp.G <= 64) launch_warp<32, 2>(kp, W, sms, st);
@@ -294,7 +318,7 @@ void launch_fp32_passes(const KParams &kp, const WarmOut &wo, const WarmStart &S
                         cudaStream_t st) {
   const int threads = 128;
   const size_t smem = table_bytes(kp.G);
-  if (kp.G > 32 && kp.G <= 64) {
+  if (kp.G > 32 && kp.G <= 64 && !(kp.flags & RHD_CELL_PER_THREAD)) {
     const int b = persistent_blocks(warm_warp32_kernel<32, 2>, smem, sms, kp.n * 32, threads);
     warm_warp32_kernel<32, 2><<<b, threads, smem, st>>>(kp, wo, S);
     return;
@@ -669,6 +693,36 @@ extern "C" int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids,
 }
 
 #include "rhd_surrogate.cuh"
+
+extern "C" int rhd_profile_start(void) {
+  for (auto &e : rhd::t_events) {
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  rhd::t_events.clear();
+  rhd::t_profiling = true;
+  return RHD_OK;
+}
+
+extern "C" int rhd_profile_stop(int32_t *launches, double *total_ms) {
+  if (!launches || !total_ms) return RHD_EINVAL;
+  rhd::t_profiling = false;
+  double sum = 0.0;
+  int rc = RHD_OK;
+  for (auto &e : rhd::t_events) {
+    float ms = 0.0f;
+    if (cudaEventSynchronize(e.second) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, e.first, e.second) != cudaSuccess)
+      rc = RHD_ECUDA;
+    sum += ms;
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  *launches = (int32_t)rhd::t_events.size();
+  *total_ms = sum;
+  rhd::t_events.clear();
+  return rc;
+}
 
 extern "C" const char *rhd_strerror(int code) {
   switch (code) {

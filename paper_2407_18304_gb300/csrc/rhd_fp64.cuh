@@ -193,8 +193,9 @@ __device__ __forceinline__ int inner_step(const KParams &P, const GroupTable &ta
     const double b = aT4 * dP;
     const double db = aT3 * (4.0 * dP - dD);  // d b_g / dT
     const double a = tab.alpha[g], rm = tab.rm[g], rp = tab.rp[g];
-    double dq;
-    const double q = chiF_ratio<double>(b, aT4, dD, a, rm, rp, dL, dU, db, aT3, eL, eU, dq);  // a5
+    // a5: chi_F; its T-derivative is left out of the Jacobian (the paper's
+    // own simplification; the rate changes, not the root)
+    const double q = chiF_q<double>(b, aT4, dD, a, rm, rp, dL, dU);
     A.bq[g] = b;
     A.dnx[g] = aT4 * (rp * dU - rm * dL);  // (4pi/c) Delta_g(nu chi_0 B_nu) / chi_E
     A.qF[g] = q;
@@ -205,10 +206,9 @@ __device__ __forceinline__ int inner_step(const KParams &P, const GroupTable &ta
       const double Eg = b + (1.0 + a) * q * A.w[g] - A.R[g] * C.its * tab.ikbar[g];
       const double s = P.src ? P.src[o] : 0.0;
       fr = Eg - P.erad[o] - A.R[g] - s;
-      // a7: dF_R,g/dE_gas = (1/C_v) dE_g/dT at fixed R_g (chi_B/chi_E = 1 in PPL
-      // and PC); the T-derivative of chi_F in the work term is kept as well,
-      // so the Newton step is exact for the inner system (same root)
-      d = (db + (1.0 + a) * dq * A.w[g]) * C.irc;
+      // a7: dF_R,g/dE_gas = (1/C_v) db_g/dT at fixed R_g (chi_B/chi_E = 1 in
+      // PPL and PC)
+      d = db * C.irc;
     } else {
       fr = -A.R[g];  // uncoupled group: R_g = 0
       d = 0.0;

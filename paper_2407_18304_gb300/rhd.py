@@ -20,6 +20,7 @@ PPL_FIXED, PC = 0, 1
 STATUS_OK, STATUS_FALLBACK, STATUS_MAXITER, STATUS_INVALID = 0, 1, 2, 3
 GROUP_TEST = 1
 FLUX_TEST = 2
+CELL_PER_THREAD = 4
 MAX_GROUPS = 256
 NOALLOC_BYTES = 64 << 20
 
@@ -120,6 +121,11 @@ def lib() -> ctypes.CDLL:
             f = getattr(_lib, name)
             f.restype = ctypes.c_int
             f.argtypes = args
+        _lib.rhd_profile_start.restype = ctypes.c_int
+        _lib.rhd_profile_start.argtypes = []
+        _lib.rhd_profile_stop.restype = ctypes.c_int
+        _lib.rhd_profile_stop.argtypes = [ctypes.POINTER(ctypes.c_int32),
+                                          ctypes.POINTER(ctypes.c_double)]
         _lib.rhd_strerror.restype = ctypes.c_char_p
         _lib.rhd_strerror.argtypes = [ctypes.c_int]
         _lib.rhd_version.restype = ctypes.c_int
@@ -495,6 +501,18 @@ class Surrogate:
         _raise(lib().rhd_source_update_warm(self._h, ctypes.byref(st), ctypes.byref(gr),
                                             ctypes.byref(lw), float(dt), n, self._s(stream)))
         del keep
+
+
+def profile_start() -> None:
+    """Start timing the FP64-pass kernel of this thread's update calls."""
+    _raise(lib().rhd_profile_start())
+
+
+def profile_stop() -> tuple[int, float]:
+    """(launches timed, their summed duration in ms) since profile_start."""
+    n, ms = ctypes.c_int32(), ctypes.c_double()
+    _raise(lib().rhd_profile_stop(ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
 
 
 def strerror(code: int) -> str:

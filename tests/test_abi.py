@@ -85,3 +85,11 @@ def test_grid_struct_matches_the_c_layout():
     assert rhd.Grid.opacity_law.offset == ctypes.sizeof(rhd.State) + ctypes.sizeof(rhd.Groups)
     assert ctypes.sizeof(rhd.Grid) == (ctypes.sizeof(rhd.State) + ctypes.sizeof(rhd.Groups)
                                        + ctypes.sizeof(rhd.OpacityLaw) + 16)
+
+
+def test_profile_hooks_without_a_device(lib):
+    assert lib.rhd_profile_start() == 0
+    n, ms = ctypes.c_int32(-1), ctypes.c_double(-1.0)
+    assert lib.rhd_profile_stop(ctypes.byref(n), ctypes.byref(ms)) == 0
+    assert n.value == 0 and ms.value == 0.0
+    assert lib.rhd_profile_stop(None, None) == -1

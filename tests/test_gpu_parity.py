@@ -276,3 +276,31 @@ def test_fp64_slow_outer_iteration_cells_converge():
             assert v < FP64_TOL, (k, v)
     for k in ("T", "egas", "erad"):
         assert ep[k] < FP64_TOL, (k, ep[k])
+
+
+@pytest.mark.parametrize("precision", [rhd.FP64, rhd.MIXED])
+def test_both_cell_mappings_give_the_same_results(precision):
+    """64 groups: a warp per cell (default) and one cell per thread
+    (RHD_CELL_PER_THREAD) solve the same equations; both match the oracle and
+    each other."""
+    w = synth.preset("full_256cube_ng64", n_cells=300, seed=8)
+    kw = TIGHT if precision == rhd.FP64 else {}
+    a = run_gpu(w, precision=precision, **kw)
+    b = run_gpu(w, precision=precision, flags=rhd.CELL_PER_THREAD, **kw)
+    o = run_oracle(w)
+    st0 = synth.to_numpy(w.state)
+    ok = converged(a, b, o)
+    assert (~ok).mean() <= MAX_UNCONVERGED
+    floor = FLOOR if precision == rhd.FP64 else 10 * 1e-11 / 1e-6
+    bound = FP64_TOL if precision == rhd.FP64 else 1e-6
+    for x, label in ((a, "warp"), (b, "thread")):
+        e = errors(select(x, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, w.edges,
+                   floor=floor)
+        _report(f"{label} vs oracle", e)
+        for k in ("T", "egas", "erad"):
+            assert e[k] < bound, (label, k, e[k])
+    e = errors(select(a, ok), select(b, ok), select(st0, ok), w.consts["c"], w.c_v, w.edges,
+               floor=floor)
+    _report("warp vs thread", e)
+    for k in ("T", "egas", "erad"):
+        assert e[k] < bound, (k, e[k])
