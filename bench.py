@@ -86,22 +86,23 @@ def barrier(ws):
         dist.barrier()
 
 
-def allmax(x: float, ws: int) -> float:
+def _reduce(x: float, ws: int, op: str) -> float:
+    """x reduced over the ranks (max or sum); a host scalar on every rank."""
     if ws == 1:
         return x
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
     return float(t.item())
+
+
+def allmax(x: float, ws: int) -> float:
+    return _reduce(x, ws, "max")
 
 
 def allsum(x: float, ws: int) -> float:
-    if ws == 1:
-        return x
-    import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(x, ws, "sum")
 
 
 class ClockSampler:
