@@ -416,18 +416,26 @@ extern "C" int rhd_source_update_noalloc(rhd_state_t *state, const rhd_groups_t 
 // ---------------------------------------------------------------------------
 // Batched uneven grids
 // ---------------------------------------------------------------------------
+// Grids are split in two classes, each with its own work queue: one cell per
+// thread (up to 32 groups, or RHD_CELL_PER_THREAD) and one cell per warp
+// (33..64 groups).  Staging layout: offsets [2][cap + 1], selections [2][cap].
 struct rhd_context {
   int device = -1;
-  int threads = 128, cpi = 512;  // launch shape (autotuned)
+  int threads = 128, cpi = 512;  // thread-class launch shape (autotuned)
   int cap_grids = 0;
   rhd::KParams *h_grids = nullptr, *d_grids = nullptr;
   int64_t *h_off = nullptr, *d_off = nullptr;
+  int *h_sel = nullptr, *d_sel = nullptr;
+  int n_sel[2] = {0, 0};
   double *d_tables = nullptr;
-  unsigned long long *d_head = nullptr;
+  unsigned long long *d_head = nullptr;  // one counter per class
   cudaStream_t cap = nullptr;
+  cudaStream_t side = nullptr;       // the warp class runs here, forked from the main stream
+  cudaEvent_t fork = nullptr, join = nullptr;
   cudaGraphExec_t exec = nullptr;
   int sig_grids = -1, sig_threads = 0, sig_cpi = 0, sig_prec = -1;
-  int64_t sig_items = -1;
+  int64_t sig_items[2] = {-1, -1};
+  int sig_sel[2] = {-1, -1};
   cudaEvent_t done = nullptr;
   bool pending = false;
 };
@@ -437,18 +445,22 @@ namespace {
 
 constexpr int kMaxGB = RHD_MAX_GROUPS_BATCHED;
 const int64_t kTableWords = group_table_words(kMaxGB) + 1;
+constexpr int kCpiWarp = 64;  // cells per work item of the warp class
 
 void ctx_free(rhd_context *c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->h_grids) cudaFreeHost(c->h_grids);
   if (c->h_off) cudaFreeHost(c->h_off);
+  if (c->h_sel) cudaFreeHost(c->h_sel);
   if (c->d_grids) cudaFree(c->d_grids);
   if (c->d_off) cudaFree(c->d_off);
+  if (c->d_sel) cudaFree(c->d_sel);
   if (c->d_tables) cudaFree(c->d_tables);
   if (c->d_head) cudaFree(c->d_head);
   c->exec = nullptr;
   c->h_grids = c->d_grids = nullptr;
   c->h_off = c->d_off = nullptr;
+  c->h_sel = c->d_sel = nullptr;
   c->d_tables = nullptr;
   c->d_head = nullptr;
   c->cap_grids = 0;
@@ -461,11 +473,13 @@ int ctx_reserve(rhd_context *c, int n_grids) {
   int cap = 64;
   while (cap < n_grids) cap *= 2;
   if (cudaHostAlloc(&c->h_grids, sizeof(KParams) * cap, cudaHostAllocDefault) != cudaSuccess ||
-      cudaHostAlloc(&c->h_off, sizeof(int64_t) * (cap + 1), cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&c->h_off, sizeof(int64_t) * 2 * (cap + 1), cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&c->h_sel, sizeof(int) * 2 * cap, cudaHostAllocDefault) != cudaSuccess ||
       cudaMalloc(&c->d_grids, sizeof(KParams) * cap) != cudaSuccess ||
-      cudaMalloc(&c->d_off, sizeof(int64_t) * (cap + 1)) != cudaSuccess ||
+      cudaMalloc(&c->d_off, sizeof(int64_t) * 2 * (cap + 1)) != cudaSuccess ||
+      cudaMalloc(&c->d_sel, sizeof(int) * 2 * cap) != cudaSuccess ||
       cudaMalloc(&c->d_tables, sizeof(double) * kTableWords * cap) != cudaSuccess ||
-      cudaMalloc(&c->d_head, sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&c->d_head, 2 * sizeof(unsigned long long)) != cudaSuccess) {
     ctx_free(c);
     return RHD_ENOMEM;
   }
@@ -473,10 +487,14 @@ int ctx_reserve(rhd_context *c, int n_grids) {
   return RHD_OK;
 }
 
-// Pack the grids into the pinned staging buffers; total work items out.
+// Pack the grids into the pinned staging buffers and split them into the two
+// classes; work items per class out (items[0] thread class, items[1] warp class).
 int pack_batch(rhd_context *c, const rhd_grid_t *grids, int n_grids, int cpi, int *prec,
-               int64_t *total) {
-  int64_t acc = 0;
+               int64_t items[2]) {
+  int64_t acc[2] = {0, 0};
+  int ns[2] = {0, 0};
+  int64_t *off[2] = {c->h_off, c->h_off + c->cap_grids + 1};
+  int *sel[2] = {c->h_sel, c->h_sel + c->cap_grids};
   *prec = -1;
   for (int j = 0; j < n_grids; ++j) {
     const rhd_grid_t &g = grids[j];
@@ -485,37 +503,69 @@ int pack_batch(rhd_context *c, const rhd_grid_t *grids, int n_grids, int cpi, in
     if (g.groups.n_groups > kMaxGB) return RHD_ESIZE;
     if (*prec < 0) *prec = g.state.precision;
     if (g.state.precision != *prec) return RHD_EINVAL;
-    c->h_off[j] = acc;
-    acc += (g.n_cells + cpi - 1) / cpi;
+    const int cls = (g.groups.n_groups > 32 && !(g.state.flags & RHD_CELL_PER_THREAD)) ? 1 : 0;
+    const int per = cls ? kCpiWarp : cpi;
+    off[cls][ns[cls]] = acc[cls];
+    sel[cls][ns[cls]] = j;
+    ++ns[cls];
+    acc[cls] += (g.n_cells + per - 1) / per;
   }
-  c->h_off[n_grids] = acc;
-  *total = acc;
+  for (int k = 0; k < 2; ++k) {
+    off[k][ns[k]] = acc[k];
+    items[k] = acc[k];
+    c->n_sel[k] = ns[k];
+  }
   return RHD_OK;
 }
 
 template <bool MIXED>
 cudaError_t enqueue_batch(rhd_context *c, int n_grids, int threads, int cpi, int sms,
-                          cudaStream_t st) {
+                          const int64_t items[2], cudaStream_t st) {
+  const int cap = c->cap_grids;
   cudaMemcpyAsync(c->d_grids, c->h_grids, sizeof(KParams) * n_grids, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(c->d_off, c->h_off, sizeof(int64_t) * (n_grids + 1), cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(c->d_head, 0, sizeof(unsigned long long), st);
+  cudaMemcpyAsync(c->d_off, c->h_off, sizeof(int64_t) * 2 * (cap + 1), cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(c->d_sel, c->h_sel, sizeof(int) * 2 * cap, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(c->d_head, 0, 2 * sizeof(unsigned long long), st);
   tables_kernel<<<n_grids, 128, table_bytes(kMaxGB) + 64, st>>>(c->d_grids, c->d_tables,
                                                                    kTableWords);
   const size_t smem = table_bytes(kMaxGB) + 64;
-  int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<kMaxGB, MIXED>, threads,
-                                                    smem) != cudaSuccess ||
-      per_sm < 1)
-    per_sm = 1;
-  batched_kernel<kMaxGB, MIXED><<<sms * per_sm, threads, smem, st>>>(
-      c->d_grids, c->d_tables, kTableWords, c->d_off, n_grids, cpi, c->d_head);
+  const bool both = items[0] > 0 && items[1] > 0;
+  if (both) {
+    cudaEventRecord(c->fork, st);
+    cudaStreamWaitEvent(c->side, c->fork, 0);
+  }
+  if (items[0] > 0) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<kMaxGB, MIXED>,
+                                                      threads, smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    batched_kernel<kMaxGB, MIXED><<<sms * per_sm, threads, smem, st>>>(
+        c->d_grids, c->d_tables, kTableWords, c->d_sel, c->d_off, c->n_sel[0], cpi, c->d_head);
+  }
+  if (items[1] > 0) {
+    // the two classes run side by side (each one's tail overlaps the other's work)
+    cudaStream_t ws = both ? c->side : st;
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_warp_kernel<MIXED>, 128,
+                                                      smem) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+    batched_warp_kernel<MIXED><<<sms * per_sm, 128, smem, ws>>>(
+        c->d_grids, c->d_tables, kTableWords, c->d_sel + cap, c->d_off + cap + 1, c->n_sel[1],
+        kCpiWarp, c->d_head + 1);
+    if (ws != st) {
+      cudaEventRecord(c->join, ws);
+      cudaStreamWaitEvent(st, c->join, 0);
+    }
+  }
   return cudaGetLastError();
 }
 
 cudaError_t enqueue_any(rhd_context *c, int prec, int n_grids, int threads, int cpi, int sms,
-                        cudaStream_t st) {
-  return prec == RHD_MIXED ? enqueue_batch<true>(c, n_grids, threads, cpi, sms, st)
-                           : enqueue_batch<false>(c, n_grids, threads, cpi, sms, st);
+                        const int64_t items[2], cudaStream_t st) {
+  return prec == RHD_MIXED ? enqueue_batch<true>(c, n_grids, threads, cpi, sms, items, st)
+                           : enqueue_batch<false>(c, n_grids, threads, cpi, sms, items, st);
 }
 
 }  // namespace
@@ -527,7 +577,15 @@ extern "C" int rhd_context_create(rhd_context_t **ctx) {
   if (!c) return RHD_ENOMEM;
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess) {
+    if (c->cap) cudaStreamDestroy(c->cap);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->fork) cudaEventDestroy(c->fork);
+    if (c->join) cudaEventDestroy(c->join);
+    if (c->done) cudaEventDestroy(c->done);
     delete c;
     return RHD_ECUDA;
   }
@@ -540,6 +598,9 @@ extern "C" int rhd_context_destroy(rhd_context_t *ctx) {
   if (ctx->pending) cudaEventSynchronize(ctx->done);
   rhd::ctx_free(ctx);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->fork) cudaEventDestroy(ctx->fork);
+  if (ctx->join) cudaEventDestroy(ctx->join);
   if (ctx->done) cudaEventDestroy(ctx->done);
   delete ctx;
   return RHD_OK;
@@ -568,21 +629,23 @@ extern "C" int rhd_source_update_batched(rhd_context_t *ctx, const rhd_grid_t *g
   rc = rhd::ctx_reserve(ctx, n_grids);
   if (rc != RHD_OK) return rc;
   int prec = 0;
-  int64_t total = 0;
-  rc = rhd::pack_batch(ctx, grids, n_grids, ctx->cpi, &prec, &total);
+  int64_t items[2] = {0, 0};
+  rc = rhd::pack_batch(ctx, grids, n_grids, ctx->cpi, &prec, items);
   if (rc != RHD_OK) return rc;
-  if (total == 0) return RHD_OK;
+  if (items[0] + items[1] == 0) return RHD_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  const bool same = ctx->exec && ctx->sig_grids == n_grids && ctx->sig_items == total &&
-                    ctx->sig_threads == ctx->threads && ctx->sig_cpi == ctx->cpi &&
-                    ctx->sig_prec == prec;
+  const bool same = ctx->exec && ctx->sig_grids == n_grids && ctx->sig_items[0] == items[0] &&
+                    ctx->sig_items[1] == items[1] && ctx->sig_sel[0] == ctx->n_sel[0] &&
+                    ctx->sig_sel[1] == ctx->n_sel[1] && ctx->sig_threads == ctx->threads &&
+                    ctx->sig_cpi == ctx->cpi && ctx->sig_prec == prec;
   if (!same) {
     if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
     ctx->exec = nullptr;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return RHD_ECUDA;
-    const cudaError_t le = rhd::enqueue_any(ctx, prec, n_grids, ctx->threads, ctx->cpi, sms, ctx->cap);
+    const cudaError_t le =
+        rhd::enqueue_any(ctx, prec, n_grids, ctx->threads, ctx->cpi, sms, items, ctx->cap);
     const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);
     if (le != cudaSuccess || ce != cudaSuccess || !graph) {
       if (graph) cudaGraphDestroy(graph);
@@ -595,7 +658,10 @@ extern "C" int rhd_source_update_batched(rhd_context_t *ctx, const rhd_grid_t *g
       return RHD_ECUDA;
     }
     ctx->sig_grids = n_grids;
-    ctx->sig_items = total;
+    ctx->sig_items[0] = items[0];
+    ctx->sig_items[1] = items[1];
+    ctx->sig_sel[0] = ctx->n_sel[0];
+    ctx->sig_sel[1] = ctx->n_sel[1];
     ctx->sig_threads = ctx->threads;
     ctx->sig_cpi = ctx->cpi;
     ctx->sig_prec = prec;
@@ -665,11 +731,12 @@ extern "C" int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids,
     for (int b = 0; b < 3 && rc == RHD_OK; ++b) {
       const int th = cand_threads[a], cpi = th * cand_mult[b];
       int prec = 0;
-      int64_t total = 0;
-      rc = rhd::pack_batch(ctx, grids, n_grids, cpi, &prec, &total);
-      if (rc != RHD_OK || total == 0) break;
+      int64_t items[2] = {0, 0};
+      rc = rhd::pack_batch(ctx, grids, n_grids, cpi, &prec, items);
+      if (rc != RHD_OK || items[0] + items[1] == 0) break;
       cudaEventRecord(e0, st);
-      if (rhd::enqueue_any(ctx, prec, n_grids, th, cpi, sms, st) != cudaSuccess) rc = RHD_ECUDA;
+      if (rhd::enqueue_any(ctx, prec, n_grids, th, cpi, sms, items, st) != cudaSuccess)
+        rc = RHD_ECUDA;
       cudaEventRecord(e1, st);
       restore();
       if (cudaStreamSynchronize(st) != cudaSuccess) rc = RHD_ECUDA;

@@ -12,6 +12,8 @@
 #pragma once
 #include "rhd_fp64.cuh"
 #include "rhd_mixed.cuh"
+#include "rhd_warp.cuh"
+#include "rhd_warp32.cuh"
 
 namespace rhd {
 
@@ -100,14 +102,37 @@ __device__ __forceinline__ void solve_cell(const KParams &P, const GroupTable &t
   store_cell(P, C, A);
 }
 
+// Work items over the grids sel[0 .. n_sel): item_off[k] is grid sel[k]'s
+// first item, item_off[n_sel] the total.  Thread 0 takes the next item from
+// *head and finds its grid by binary search; the CTA then shares it.
+__device__ __forceinline__ bool next_item(const int64_t *item_off, int n_sel,
+                                          unsigned long long *head, long long &s_item,
+                                          int &s_k) {
+  if (threadIdx.x == 0) {
+    const long long it = (long long)atomicAdd(head, 1ULL);
+    int lo = 0, hi = n_sel;  // k with item_off[k] <= it < item_off[k+1]
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (item_off[mid] <= it) lo = mid;
+      else hi = mid;
+    }
+    s_item = it;
+    s_k = lo;
+  }
+  __syncthreads();
+  return s_item < item_off[n_sel];
+}
+
+// One cell per thread (grids of up to 32 groups, or that ask for it).
 template <int MAXG, bool MIXED>
 __global__ void batched_kernel(const KParams *__restrict__ grids, const double *__restrict__ tables,
-                               int64_t table_stride, const int64_t *__restrict__ item_off,
-                               int n_grids, int cpi, unsigned long long *head) {
+                               int64_t table_stride, const int *__restrict__ sel,
+                               const int64_t *__restrict__ item_off, int n_sel, int cpi,
+                               unsigned long long *head) {
   extern __shared__ double sm[];
   __shared__ long long s_item;
   __shared__ int s_grid;
-  const long long total = item_off[n_grids];
+  const long long total = item_off[n_sel];
   int cur = -1;
   GroupTable tab;
   Arr64<MAXG> A;
@@ -116,20 +141,9 @@ __global__ void batched_kernel(const KParams *__restrict__ grids, const double *
   Cell32 D;
   load_planck(sm);  // visible after the first __syncthreads below
   for (;;) {
-    if (threadIdx.x == 0) {
-      const long long it = (long long)atomicAdd(head, 1ULL);
-      int lo = 0, hi = n_grids;  // grid j with item_off[j] <= it < item_off[j+1]
-      while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (item_off[mid] <= it) lo = mid;
-        else hi = mid;
-      }
-      s_item = it;
-      s_grid = lo;
-    }
-    __syncthreads();
+    if (!next_item(item_off, n_sel, head, s_item, s_grid)) break;
     const long long item = s_item;
-    const int j = s_grid;
+    const int k = s_grid, j = sel[k];
     if (item >= total) break;
     const KParams &P = grids[j];
     if (j != cur) {
@@ -140,11 +154,125 @@ __global__ void batched_kernel(const KParams *__restrict__ grids, const double *
       tab = table_view(sm + kPlanckWords, P.G, sm);
     }
     __syncthreads();
-    const int64_t c0 = (item - item_off[j]) * (int64_t)cpi;
+    const int64_t c0 = (item - item_off[k]) * (int64_t)cpi;
     const int64_t c1 = c0 + cpi < P.n ? c0 + cpi : P.n;
     for (int64_t i = c0 + threadIdx.x; i < c1; i += blockDim.x)
       solve_cell<MAXG, MIXED>(P, tab, i, C, A, B, D);
     __syncthreads();  // s_item, s_grid and the table are reused by the next item
+  }
+}
+
+// One cell per warp (grids of 33..64 groups): the mixed form's FP32 passes
+// (rhd_warp32.cuh) and FP64 passes (rhd_warp.cuh) of a cell run in the same
+// warp; the FP32 result is handed over rounded exactly as the two-launch
+// form's workspace rounds it (R_g / E_tot and F_g / (c E_tot) in FP32, E_int
+// and rho v in FP64), then the FP64 passes with the cold restart on failure.
+template <bool MIXED>
+__device__ __forceinline__ void solve_cell_warp(const KParams &P, const GroupTable &tab,
+                                                const float *pf, int64_t i, int l,
+                                                WCell<32, 2> &C, WCell32<32, 2> &D) {
+  constexpr unsigned mask = 0xffffffffu;
+  bool warm = false;
+  double eint = 0.0, m[3] = {0.0, 0.0, 0.0};
+  int nit = 0;
+  float r32[2] = {0.0f, 0.0f}, f32[2][3] = {{0.0f, 0.0f, 0.0f}, {0.0f, 0.0f, 0.0f}};
+  if (MIXED && w32_load(P, tab, i, l, mask, D)) {
+    w32_outer_begin(P, D);
+    for (;;) {
+      const int r = w32_inner_step(P, tab, pf, l, 0, mask, D);
+      if (r != 0 && w32_outer_end(P, tab, l, mask, D)) break;
+    }
+    warm = D.Eint > 0.0;
+    eint = D.Eint;
+    m[0] = D.m[0];
+    m[1] = D.m[1];
+    m[2] = D.m[2];
+    nit = D.nit > 255 ? 255 : D.nit;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      r32[j] = D.R[j];
+      for (int d = 0; d < 3; ++d) f32[j][d] = D.f[j][d];
+    }
+  }
+  if (!wload(P, i, l, mask, C)) return;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    int nit0 = 0;
+    if (attempt == 1) {
+      if (!(warm && C.stat != RHD_STATUS_OK)) break;
+      nit0 = C.nit;
+      wload(P, i, l, mask, C);
+    }
+    wset_tau(P, tab, l, C, C.chi0s);
+    if (warm && attempt == 0) {
+      C.Eint = eint;
+      C.m[0] = m[0];
+      C.m[1] = m[1];
+      C.m[2] = m[2];
+      C.nit = nit;
+      const double fs = P.c * C.Etot;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (l + 32 * j >= P.G) continue;
+        C.R[j] = (double)r32[j] * C.Etot;
+        for (int d = 0; d < 3; ++d) C.Fk[j][d] = (double)f32[j][d] * fs;
+      }
+    }
+    wouter_begin(P, C);
+    for (;;) {
+      const int r = winner_step(P, tab, l, 0, mask, C);
+      if (r == 0) continue;
+      if (r == 2) C.stat = RHD_STATUS_MAXITER;
+      if (wouter_end(P, tab, l, mask, C)) break;
+    }
+    if (attempt == 1) {
+      C.nit += nit0;
+      if (C.stat == RHD_STATUS_OK) C.stat = RHD_STATUS_FALLBACK;
+    }
+  }
+  wstore(P, l, C);
+}
+
+template <bool MIXED>
+__global__ void __launch_bounds__(128) batched_warp_kernel(
+    const KParams *__restrict__ grids, const double *__restrict__ tables, int64_t table_stride,
+    const int *__restrict__ sel, const int64_t *__restrict__ item_off, int n_sel, int cpi,
+    unsigned long long *head) {
+  extern __shared__ double sm[];
+  __shared__ float pf[kPlanckF];
+  __shared__ long long s_item;
+  __shared__ int s_k;
+  load_planck(sm);
+  __syncthreads();
+  {
+    using namespace planck_table;
+    for (int t = threadIdx.x; t < kPlanckF; t += blockDim.x) {
+      const int k = t / kSeg, sg = t % kSeg;
+      const int src = k <= kDeg32 ? k * kSeg + sg : (kDeg + 1 + (k - kDeg32 - 1)) * kSeg + sg;
+      pf[t] = (float)sm[src];
+    }
+  }
+  const int l = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int cur = -1;
+  GroupTable tab;
+  WCell<32, 2> C;
+  WCell32<32, 2> D;
+  for (;;) {
+    if (!next_item(item_off, n_sel, head, s_item, s_k)) break;
+    const long long item = s_item;
+    const int k = s_k, j = sel[k];
+    const KParams &P = grids[j];
+    if (j != cur) {
+      const int words = group_table_words(P.G);
+      const double *src = tables + (int64_t)j * table_stride;
+      for (int t = threadIdx.x; t < words; t += blockDim.x) sm[kPlanckWords + t] = src[t];
+      cur = j;
+      tab = table_view(sm + kPlanckWords, P.G, sm);
+    }
+    __syncthreads();
+    const int64_t c0 = (item - item_off[k]) * (int64_t)cpi;
+    const int64_t c1 = c0 + cpi < P.n ? c0 + cpi : P.n;
+    for (int64_t i = c0 + wid; i < c1; i += nw) solve_cell_warp<MIXED>(P, tab, pf, i, l, C, D);
+    __syncthreads();  // s_item, s_k and the table are reused by the next item
   }
 }
 

@@ -304,3 +304,28 @@ def test_both_cell_mappings_give_the_same_results(precision):
     _report("warp vs thread", e)
     for k in ("T", "egas", "erad"):
         assert e[k] < bound, (k, e[k])
+
+
+@pytest.mark.parametrize("G", [33, 48, 97])
+@pytest.mark.parametrize("precision", [rhd.FP64, rhd.MIXED])
+def test_ragged_group_counts_in_the_warp_mapping(G, precision):
+    """Group counts that leave lanes with slots past the last group (33, 48:
+    one slot each for some lanes; 97: four slots); the FP32 warp passes cover
+    33..64 groups."""
+    w = synth.preset("mixed_128cube_ng16", n_cells=257, seed=300 + G, n_groups=G)
+    kw = TIGHT if precision == rhd.FP64 else {}
+    g = run_gpu(w, precision=precision, **kw)
+    o = run_oracle(w)
+    st0 = synth.to_numpy(w.state)
+    ok = converged(g, o)
+    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    floor = FLOOR if precision == rhd.FP64 else 10 * 1e-11 / 1e-6
+    e = errors(select(g, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, w.edges,
+               floor=floor)
+    _report(f"G={G} prec={precision}", e)
+    ce, cm = conservation(select(g, ok), select(st0, ok), w.consts["c"], w.consts["c_hat"])
+    assert ce < 64 * 2.0 ** -52 and cm < 64 * 2.0 ** -52
+    bound = FP64_TOL if precision == rhd.FP64 else 1e-6
+    keys = [k for k in e if not k.endswith("_plain")] if precision == rhd.FP64 else ["T", "egas", "erad"]
+    for k in keys:
+        assert e[k] < bound, (k, e[k])
