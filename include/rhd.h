@@ -150,6 +150,21 @@ int rhd_source_update(rhd_state_t *state, const rhd_groups_t *groups,
                       const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
                       void *stream);
 
+/* ---- One radiation step of the two-stage IMEX integrator -----------------------
+ * Sec. 3, eqs. imex1 and imex2, with the transport terms left out (a single
+ * zone, or a caller that applies transport elsewhere).  Stage 1 is the implicit
+ * source update of rhd_source_update over dt with theta = 1, from U^(n) to
+ * U^(n+1/2).  Stage 2's explicit part is then U^(n) + (dt/2) S(U^(n+1/2)), and
+ * with no transport dt S(U^(n+1/2)) = U^(n+1/2) - U^(n) (stage 1), so stage 2
+ * starts from (U^(n) + U^(n+1/2))/2 (E_gas, rho v, E_g, F_g) and makes the
+ * implicit update with theta = 1/2.  state->theta is ignored; state->src must
+ * be NULL (RHD_EINVAL otherwise: a per-stage source is the caller's to split).
+ * status is the worse of the two stages, iters their sum (held at 255).  The
+ * library keeps U^(n) in a per-device workspace (8 (4 + 4 N_g) + 2 bytes per
+ * cell, grown on demand); otherwise as rhd_source_update. */
+int rhd_imex_step(rhd_state_t *state, const rhd_groups_t *groups,
+                  const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells, void *stream);
+
 /* ---- Batched uneven grids --------------------------------------------------
  * Many independent grids (own cell count, N_g <= RHD_MAX_GROUPS_BATCHED, own
  * opacity law, dt and parameters) in one persistent launch: a device work queue

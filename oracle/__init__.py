@@ -22,6 +22,9 @@ Parity status of each function (what pins it; the pins live in
 * ``source_update`` -- conservation, v=0 equilibrium, grey reduction, linear
   relaxation closed form, the Doppler-test equilibrium temperature printed in
   Sec. 4.2.1, and the group flux spectrum against the angle integral eq. bbF.
+* ``imex_step`` -- two ``source_update`` calls composed as eqs. imex1/imex2
+  prescribe with no transport; pinned by the closed-form amplification
+  1/(1 + lambda dt) of a small grey disequilibrium and by conservation.
 """
 from __future__ import annotations
 
@@ -259,3 +262,22 @@ def source_update(state: dict, params: Params, groups: Groups, n_threads: int = 
         raise ValueError("orc_source_update rejected its arguments")
     return {"mom": mom, "egas": egas, "erad": erad, "frad": frad, "iters": iters,
             "resid": resid, "status": status}
+
+
+def imex_step(state: dict, p: "Params", g: "Groups", n_threads: int = 0) -> dict:
+    """One step of the two-stage IMEX integrator (Sec. 3, eqs. imex1, imex2)
+    without transport: stage 1 is the implicit source update over dt with
+    theta = 1 from U(n); stage 2 starts from U(n) + (dt/2) S(U(n+1/2)) =
+    (U(n) + U(n+1/2))/2 -- with no transport dt S(U(n+1/2)) = U(n+1/2) - U(n)
+    by stage 1 -- and makes the implicit update with theta = 1/2.  Returns the
+    final state with ``status`` the worse of the two stages."""
+    import dataclasses
+    if state.get("src") is not None:
+        raise ValueError("imex_step takes no source term")
+    s1 = source_update(state, dataclasses.replace(p, theta=1.0), g, n_threads=n_threads)
+    mid = dict(state)
+    for k in ("egas", "mom", "erad", "frad"):
+        mid[k] = 0.5 * (np.asarray(state[k], dtype=np.float64) + s1[k])
+    s2 = source_update(mid, dataclasses.replace(p, theta=0.5), g, n_threads=n_threads)
+    s2["status"] = np.maximum(s1["status"], s2["status"])
+    return s2

@@ -414,6 +414,105 @@ extern "C" int rhd_source_update_noalloc(rhd_state_t *state, const rhd_groups_t 
 }
 
 // ---------------------------------------------------------------------------
+// The two-stage IMEX step without transport
+// ---------------------------------------------------------------------------
+namespace rhd {
+namespace {
+
+void *g_imex_ws[kMaxDevices];
+size_t g_imex_bytes[kMaxDevices];
+
+// mode 0: U^(n) -> ws; 1: U = (U + ws)/2 and stage-1 status/iters -> ws;
+// 2: status = max(status, ws status), iters = min(255, iters + ws iters).
+__global__ void imex_kernel(const __grid_constant__ KParams P, double *ws, uint8_t *ws_st,
+                            int mode) {
+  const int64_t n = P.n;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    if (mode == 2) {
+      if (P.status) P.status[i] = P.status[i] > ws_st[i] ? P.status[i] : ws_st[i];
+      if (P.iters) {
+        const int it = (int)P.iters[i] + (int)ws_st[n + i];
+        P.iters[i] = (uint8_t)(it > 255 ? 255 : it);
+      }
+      continue;
+    }
+    double *w = ws;
+    double *u[4] = {P.egas, P.mom[0], P.mom[1], P.mom[2]};
+    for (int k = 0; k < 4; ++k) {
+      if (mode == 0) w[(int64_t)k * n + i] = u[k][i];
+      else u[k][i] = 0.5 * (u[k][i] + w[(int64_t)k * n + i]);
+    }
+    w += 4 * n;
+    for (int g = 0; g < P.G; ++g) {
+      const int64_t o = (int64_t)g * P.gs + i;
+      double *a[4] = {P.erad, P.frad[0], P.frad[1], P.frad[2]};
+      for (int k = 0; k < 4; ++k) {
+        const int64_t q = ((int64_t)k * P.G + g) * n + i;
+        if (mode == 0) w[q] = a[k][o];
+        else a[k][o] = 0.5 * (a[k][o] + w[q]);
+      }
+    }
+    if (mode == 1) {
+      ws_st[i] = P.status ? P.status[i] : 0;
+      ws_st[n + i] = P.iters ? P.iters[i] : 0;
+    }
+  }
+}
+
+int imex_workspace(int64_t n, int G, double **ws, uint8_t **st) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RHD_ECUDA;
+  const size_t words = (size_t)n * (4 + 4 * (size_t)G);
+  const size_t bytes = words * sizeof(double) + 2 * (size_t)n + 256;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (g_imex_bytes[dev] < bytes) {
+    if (g_imex_ws[dev]) cudaFree(g_imex_ws[dev]);
+    g_imex_ws[dev] = nullptr;
+    g_imex_bytes[dev] = 0;
+    if (cudaMalloc(&g_imex_ws[dev], bytes) != cudaSuccess) return RHD_ENOMEM;
+    g_imex_bytes[dev] = bytes;
+  }
+  *ws = (double *)g_imex_ws[dev];
+  *st = (uint8_t *)(*ws + words);
+  return RHD_OK;
+}
+
+}  // namespace
+}  // namespace rhd
+
+extern "C" int rhd_imex_step(rhd_state_t *state, const rhd_groups_t *groups,
+                             const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
+                             void *stream) {
+  if (!state) return RHD_EINVAL;
+  if (state->src) return RHD_EINVAL;
+  static thread_local rhd::KParams kp;
+  rhd_state_t s1 = *state;
+  s1.theta = 1.0;
+  int rc = rhd::pack(&s1, groups, opacity_law, dt, n_cells, &kp);
+  if (rc != RHD_OK) return rc;
+  if (n_cells == 0) return RHD_OK;
+  int sms = 0;
+  rc = rhd::ensure_device(&sms);
+  if (rc != RHD_OK) return rc;
+  double *ws = nullptr;
+  uint8_t *wst = nullptr;
+  rc = rhd::imex_workspace(kp.n, kp.G, &ws, &wst);
+  if (rc != RHD_OK) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int blocks = (int)((n_cells + 255) / 256 < 65535 ? (n_cells + 255) / 256 : 65535);
+  rhd::imex_kernel<<<blocks, 256, 0, st>>>(kp, ws, wst, 0);           // keep U^(n)
+  rc = rhd::launch(kp, state->precision, sms, st);                     // stage 1, theta = 1
+  if (rc != RHD_OK) return rc;
+  rhd::imex_kernel<<<blocks, 256, 0, st>>>(kp, ws, wst, 1);           // (U^(n) + U^(n+1/2))/2
+  kp.theta = 0.5;
+  rc = rhd::launch(kp, state->precision, sms, st);                     // stage 2, theta = 1/2
+  if (rc != RHD_OK) return rc;
+  rhd::imex_kernel<<<blocks, 256, 0, st>>>(kp, ws, wst, 2);           // status, iters
+  return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
+}
+
+// ---------------------------------------------------------------------------
 // Batched uneven grids
 // ---------------------------------------------------------------------------
 // Grids are split in two classes, each with its own work queue: one cell per

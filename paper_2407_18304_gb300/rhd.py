@@ -121,6 +121,9 @@ def lib() -> ctypes.CDLL:
             f = getattr(_lib, name)
             f.restype = ctypes.c_int
             f.argtypes = args
+        _lib.rhd_imex_step.restype = ctypes.c_int
+        _lib.rhd_imex_step.argtypes = [ctypes.POINTER(State), ctypes.POINTER(Groups),
+                                       ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _P]
         _lib.rhd_profile_start.restype = ctypes.c_int
         _lib.rhd_profile_start.argtypes = []
         _lib.rhd_profile_stop.restype = ctypes.c_int
@@ -236,6 +239,33 @@ def source_update(state: dict, edges, law, *, dt: float, c_v: float, consts: dic
     s = stream if stream is not None else torch.cuda.current_stream()
     rc = lib().rhd_source_update(ctypes.byref(st), ctypes.byref(gr), ctypes.byref(lw), float(dt),
                                  int(n), ctypes.c_void_p(s.cuda_stream))
+    del keep
+    if rc != 0:
+        raise RhdError(rc, lib().rhd_strerror(rc).decode())
+
+
+def imex_step(state: dict, edges, law, *, dt: float, c_v: float, consts: dict,
+              precision: int = FP64, closure: int = M1, tol: float = 0.0,
+              tol_outer: float = 0.0, max_newton: int = 0, max_outer: int = 0,
+              status: torch.Tensor | None = None, iters: torch.Tensor | None = None,
+              mode: int = PPL_FIXED, khat_g=None, alpha_g=None, temp_exponent: float = 0.0,
+              T_ref: float = 1.0, stream: torch.cuda.Stream | None = None, flags: int = 0) -> None:
+    """``rhd_imex_step``: one step of the two-stage IMEX integrator without
+    transport (stage 1 theta = 1, stage 2 theta = 1/2 from the average of the
+    start and stage 1); same arguments as ``source_update``; a ``src`` entry is
+    refused by the library (RhdError)."""
+    rho = state["rho"]
+    n = rho.shape[0]
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    G = len(e) - 1
+    st = _state(state, G, n, n, c_v=c_v, consts=consts, theta=1.0, precision=precision,
+                closure=closure, tol=tol, tol_outer=tol_outer, max_newton=max_newton,
+                max_outer=max_outer, status=status, iters=iters, flags=flags)
+    gr = Groups(G, _dp(e))
+    lw, keep = make_law(law, mode, khat_g, alpha_g, temp_exponent, T_ref)
+    s = stream if stream is not None else torch.cuda.current_stream()
+    rc = lib().rhd_imex_step(ctypes.byref(st), ctypes.byref(gr), ctypes.byref(lw), float(dt),
+                             int(n), ctypes.c_void_p(s.cuda_stream))
     del keep
     if rc != 0:
         raise RhdError(rc, lib().rhd_strerror(rc).decode())

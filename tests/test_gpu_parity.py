@@ -329,3 +329,39 @@ def test_ragged_group_counts_in_the_warp_mapping(G, precision):
     keys = [k for k in e if not k.endswith("_plain")] if precision == rhd.FP64 else ["T", "egas", "erad"]
     for k in keys:
         assert e[k] < bound, (k, e[k])
+
+
+@pytest.mark.parametrize("precision", [rhd.FP64, rhd.MIXED])
+def test_imex_step_matches_the_oracle_composition(precision):
+    """rhd_imex_step (two implicit stages, theta = 1 then 1/2 from the average)
+    against the oracle's composition of the same two stages."""
+    import dataclasses
+    w = synth.preset("mixed_128cube_ng16", n_cells=400, seed=61)
+    st = {k: (None if v is None else v.cuda().clone()) for k, v in w.state.items()}
+    n = st["rho"].shape[0]
+    status = torch.full((n,), 255, dtype=torch.uint8, device="cuda")
+    kw = TIGHT if precision == rhd.FP64 else {}
+    rhd.imex_step(st, w.edges, w.law, dt=w.dt, c_v=w.c_v, consts=w.consts, precision=precision,
+                  status=status, **kw)
+    torch.cuda.synchronize()
+    g = synth.to_numpy(st)
+    g["status"] = status.cpu().numpy().astype(np.int32)
+    from parity import oracle_groups
+    p = O.Params(c=w.consts["c"], c_hat=w.consts["c_hat"], a_rad=w.consts["a_rad"],
+                 h=w.consts["h"], k_B=w.consts["k_B"], c_v=w.c_v, dt=w.dt, max_iter=200)
+    o = O.imex_step(synth.to_numpy(w.state), p, oracle_groups(w))
+    st0 = synth.to_numpy(w.state)
+    ok = converged(g, o)
+    assert (~ok).mean() <= MAX_UNCONVERGED
+    floor = FLOOR if precision == rhd.FP64 else 10 * 1e-11 / 1e-6
+    e = errors(select(g, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, w.edges,
+               floor=floor)
+    _report(f"imex prec={precision}", e)
+    ce, cm = conservation(select(g, ok), select(st0, ok), w.consts["c"], w.consts["c_hat"])
+    assert ce < 64 * 2.0 ** -52 and cm < 64 * 2.0 ** -52
+    bound = FP64_TOL if precision == rhd.FP64 else 1e-6
+    for k in ("T", "egas", "erad"):
+        assert e[k] < bound, (k, e[k])
+    with pytest.raises(rhd.RhdError):
+        rhd.imex_step(dict(st, src=torch.zeros_like(st["erad"])), w.edges, w.law, dt=w.dt,
+                      c_v=w.c_v, consts=w.consts)

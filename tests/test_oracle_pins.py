@@ -517,3 +517,32 @@ def test_invalid_cells_are_untouched():
     for k in ("erad", "frad", "mom"):
         np.testing.assert_array_equal(out[k][..., 1:4], st[k][..., 1:4])
     assert np.all(out["status"][[0, 4, 5]] == 0)
+
+
+@pytest.mark.parametrize("tau", [1e-2, 1.0, 10.0])
+def test_imex_step_amplification_of_a_small_grey_disequilibrium(tau):
+    """The IMEX composition without transport acts on a small grey
+    disequilibrium D like y' = -lambda y does under it: stage 1 divides by
+    1 + z, stage 2 averages with the start and divides by 1 + z/2, so one
+    step multiplies D by ((1 + 1/(1 + z))/2)/(1 + z/2) = 1/(1 + z),
+    z = dt chi (c_hat + c kappa).  (z stays small enough that the O(delta z)
+    nonlinear part and the solve's tolerance stay below the 2e-6 asked.)"""
+    rho, T0, delta = 1.0, 1.0e7, 1e-7
+    c, a, cv = synth.C_LIGHT, synth.A_RAD, synth.C_V
+    chi = tau / (c * synth.DT)
+    E0 = a * T0 ** 4
+    st = {"rho": np.array([rho]), "mom": np.zeros((3, 1)), "egas": np.array([rho * cv * T0]),
+          "kappa0": np.array([chi / rho]), "erad": np.array([[E0 * (1 + delta)]]),
+          "frad": np.zeros((3, 1, 1)), "src": None}
+    p = O.Params(c=c, c_hat=c, a_rad=a, c_v=cv, dt=synth.DT)
+    edges = np.array([0.0, math.inf])
+    out = O.imex_step(st, p, O.Groups(edges, np.ones(1), np.zeros(1)))
+    kap = 4 * a * T0 ** 3 / (rho * cv)
+    T1 = gas_T(out | {"rho": st["rho"]}, cv)[0]
+    D0 = -delta * E0
+    D1 = kap * rho * cv * (T1 - T0) - (out["erad"][0, 0] - E0)
+    z = synth.DT * chi * (c + c * kap)
+    assert D1 / D0 == pytest.approx(1.0 / (1.0 + z), rel=2e-6)
+    # total energy kept
+    e0 = st["egas"][0] + st["erad"][0, 0]
+    assert abs(out["egas"][0] + out["erad"][0, 0] - e0) <= 4e-16 * e0
