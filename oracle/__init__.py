@@ -14,9 +14,13 @@ Parity status of each function (what pins it; the pins live in
 * ``ppl_mean_opacity`` -- quadrature of eq. chiQ for powerlaw opacity and
   spectrum; the PC reduction at alpha_chi = 0.
 * ``group_table`` -- hand-evaluated laws; PC/PPL limits.
+* ``ppl_free_slopes`` -- a hand-worked minmod example, the exact index of a
+  binned powerlaw spectrum, the edge groups and undefined slopes.
 * ``group_terms`` -- the analytic Planck mean of the pulse opacity (Sec. 4.2.3,
   the value printed there), chi_F = chi_0 in the PC case (after eq. chiDiff),
-  the diffusion-limit invariant of eq. Fdiff.
+  the diffusion-limit invariant of eq. Fdiff; with free slopes, chi_E and chi_B
+  of a binned powerlaw spectrum against quadrature of eq. chiQ, and chi_E =
+  chi_B for E_g = b_g.
 * ``closure`` -- the free-streaming and isotropic limits, trace = E.
 * ``arrowhead_solve`` -- dense LU on random arrowheads.
 * ``source_update`` -- conservation, v=0 equilibrium, grey reduction, linear
@@ -44,6 +48,7 @@ CLOSURE_M1 = 0
 CLOSURE_EDDINGTON = 1
 PPL_FIXED = 0
 PC = 1
+PPL_FREE = 2
 
 
 def build(force: bool = False) -> str:
@@ -73,7 +78,8 @@ class _Params(ctypes.Structure):
 class _Groups(ctypes.Structure):
     _fields_ = [("n_groups", ctypes.c_int32), ("edges", ctypes.POINTER(ctypes.c_double)),
                 ("khat_minus", ctypes.POINTER(ctypes.c_double)),
-                ("alpha", ctypes.POINTER(ctypes.c_double))]
+                ("alpha", ctypes.POINTER(ctypes.c_double)),
+                ("free_slopes", ctypes.c_int32)]
 
 
 _lib = None
@@ -96,7 +102,9 @@ def lib():
         _lib.orc_group_table.argtypes = [i32, dp, i32, i32, dp, dp, dp, d, dp, dp]
         _lib.orc_group_terms.restype = None
         _lib.orc_group_terms.argtypes = [ctypes.POINTER(_Params), ctypes.POINTER(_Groups), d, d,
-                                         dp, dp, dp, dp, dp]
+                                         dp, dp, dp, dp, dp, dp, dp]
+        _lib.orc_ppl_free_slopes.restype = None
+        _lib.orc_ppl_free_slopes.argtypes = [i32, dp, dp, dp]
         _lib.orc_closure.restype = None
         _lib.orc_closure.argtypes = [i32, d, d, dp, dp]
         _lib.orc_arrowhead_solve.restype = None
@@ -146,16 +154,18 @@ class Params:
 
 @dataclass
 class Groups:
-    """Group edges and per-group opacity table (khat at the lower edge, slope)."""
+    """Group edges and per-group opacity table (khat at the lower edge, slope).
+    free_slopes: spectral indices of B_nu and E_nu from Appendix A instead of -1."""
     edges: np.ndarray
     khat_minus: np.ndarray
     alpha: np.ndarray
+    free_slopes: bool = False
     _keep: list = field(default_factory=list, repr=False)
 
     def _c(self) -> _Groups:
         e, k, a = _f64(self.edges), _f64(self.khat_minus), _f64(self.alpha)
         self._keep = [e, k, a]
-        return _Groups(len(k), _dp(e), _dp(k), _dp(a))
+        return _Groups(len(k), _dp(e), _dp(k), _dp(a), int(bool(self.free_slopes)))
 
 
 def planck_P(x: float) -> float:
@@ -174,8 +184,19 @@ def ppl_mean_opacity(chi_minus, alpha_chi, alpha_Q, r) -> float:
     return lib().orc_ppl_mean_opacity(float(chi_minus), float(alpha_chi), float(alpha_Q), float(r))
 
 
+def ppl_free_slopes(edges, Q) -> np.ndarray:
+    """alpha_Q,g of Appendix A (eqs. sg, minmod) from group values Q_g."""
+    e, q = _f64(edges), _f64(Q)
+    out = np.zeros(len(q))
+    lib().orc_ppl_free_slopes(len(q), _dp(e), _dp(q), _dp(out))
+    return out
+
+
 def group_table(edges, mode, nu_break, seg_logk, seg_beta, nu_ref):
-    """(khat_minus, alpha) per group from a piecewise-powerlaw opacity law."""
+    """(khat_minus, alpha) per group from a piecewise-powerlaw opacity law
+    (PPL_FREE shares the PPL_FIXED table; the slopes are the Groups' flag)."""
+    if mode == PPL_FREE:
+        mode = PPL_FIXED
     e = _f64(edges)
     ng = len(e) - 1
     nb, lk, be = _f64(nu_break), _f64(seg_logk), _f64(seg_beta)
@@ -189,13 +210,18 @@ def group_table(edges, mode, nu_break, seg_logk, seg_beta, nu_ref):
     return km, al
 
 
-def group_terms(params: Params, groups: Groups, chi0_scale: float, T: float) -> dict:
+def group_terms(params: Params, groups: Groups, chi0_scale: float, T: float,
+                erad0=None) -> dict:
+    """b_g, Delta terms and the mean opacities at T; erad0 sets chi_E's slopes
+    when groups.free_slopes."""
     ng = len(groups.khat_minus)
-    out = {k: np.zeros(ng) for k in ("b", "dnb", "dnxb", "chiB", "chiF")}
+    out = {k: np.zeros(ng) for k in ("b", "dnb", "dnxb", "chiB", "chiE", "chiF")}
     pc, gc = params._c(), groups._c()
+    e0 = None if erad0 is None else _f64(erad0)
     lib().orc_group_terms(ctypes.byref(pc), ctypes.byref(gc), float(chi0_scale), float(T),
+                          None if e0 is None else _dp(e0),
                           _dp(out["b"]), _dp(out["dnb"]), _dp(out["dnxb"]), _dp(out["chiB"]),
-                          _dp(out["chiF"]))
+                          _dp(out["chiE"]), _dp(out["chiF"]))
     return out
 
 

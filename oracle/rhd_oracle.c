@@ -172,20 +172,69 @@ int orc_group_table(int32_t n_groups, const double *edges, int32_t mode, int32_t
 }
 
 /* ------------------------------------------------------------------------ */
+/* PPL slopes fitted to the group values (Appendix A)                        */
+/* ------------------------------------------------------------------------ */
+/* eq. sg: slope between groups g and g+1 of Qbar against nubar in log-log;
+ * NAN when either Qbar is not positive or the slope is not finite */
+static double orc_edge_slope(const double *edges, const double *Q, int g) {
+  double qa = Q[g] / (edges[g + 1] - edges[g]);
+  double qb = Q[g + 1] / (edges[g + 2] - edges[g + 1]);
+  if (!(qa > 0.0) || !(qb > 0.0)) return NAN;
+  double nua = sqrt(edges[g] * edges[g + 1]);
+  double nub = sqrt(edges[g + 1] * edges[g + 2]);
+  double s = log(qb / qa) / log(nub / nua);
+  return isfinite(s) ? s : NAN;
+}
+
+static double orc_minmod(double a, double b) {
+  if (a > 0.0 && b > 0.0) return a < b ? a : b;
+  if (a < 0.0 && b < 0.0) return a > b ? a : b;
+  return 0.0;
+}
+
+void orc_ppl_free_slopes(int32_t n_groups, const double *edges, const double *Q,
+                         double *alpha_out) {
+  for (int g = 0; g < n_groups; ++g) alpha_out[g] = -1.0; /* eq. minmod, first and last */
+  for (int g = 1; g + 1 < n_groups; ++g) {
+    double sl = orc_edge_slope(edges, Q, g - 1);
+    double sr = orc_edge_slope(edges, Q, g);
+    if (isnan(sl) || isnan(sr)) continue; /* reading: undefined slope -> -1 */
+    alpha_out[g] = orc_minmod(sl, sr);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
 /* Group terms at temperature T                                              */
 /* ------------------------------------------------------------------------ */
 void orc_group_terms(const orc_params *p, const orc_groups *gt, double chi0_scale, double T,
-                     double *b, double *dnb, double *dnxb, double *chiB, double *chiF) {
+                     const double *erad0, double *b, double *dnb, double *dnxb, double *chiB,
+                     double *chiE, double *chiF) {
   orc_init_series();
+  const int G = gt->n_groups;
   double fac = p->a_rad * T * T * T * T;
   double tfac = (p->temp_exponent != 0.0) ? pow(T / p->T_ref, p->temp_exponent) : 1.0;
-  for (int g = 0; g < gt->n_groups; ++g) {
+  double *bg = (double *)malloc(sizeof(double) * 3 * (size_t)G);
+  double *aB = bg + G, *aE = aB + G;
+  /* b_g = 4 pi B_g / c of every group first: the Appendix A slopes of B_nu
+   * need the neighbours */
+  for (int g = 0; g < G; ++g) {
+    double n0 = gt->edges[g], n1 = gt->edges[g + 1];
+    double x0 = p->h * n0 / (p->k_B * T);
+    double x1 = isinf(n1) ? INFINITY : p->h * n1 / (p->k_B * T);
+    bg[g] = fac * orc_planck_band(x0, x1);
+  }
+  /* spectral indices of B_nu and E_nu inside each group: -1 (fixed slope), or
+   * Appendix A from b_g(T) and from the starting radiation energy */
+  for (int g = 0; g < G; ++g) aB[g] = aE[g] = -1.0;
+  if (gt->free_slopes) {
+    orc_ppl_free_slopes(G, gt->edges, bg, aB);
+    if (erad0) orc_ppl_free_slopes(G, gt->edges, erad0, aE);
+  }
+  for (int g = 0; g < G; ++g) {
     double n0 = gt->edges[g], n1 = gt->edges[g + 1];
     double x0 = p->h * n0 / (p->k_B * T);
     double x1 = isinf(n1) ? INFINITY : p->h * n1 / (p->k_B * T);
     double alpha = gt->alpha[g];
-    /* b_g = 4 pi B_g / c */
-    double bg = fac * orc_planck_band(x0, x1);
     /* (4 pi/c) Delta_g(nu B_nu) */
     double d0 = orc_nu_B(x0), d1 = orc_nu_B(x1);
     double dnbg = fac * (d1 - d0);
@@ -193,29 +242,31 @@ void orc_group_terms(const orc_params *p, const orc_groups *gt, double chi0_scal
     double chim = chi0_scale * tfac * gt->khat_minus[g];
     double chip = (alpha == 0.0) ? chim : chim * pow(n1 / n0, alpha);
     double dnxbg = fac * (chip * d1 - chim * d0);
-    /* PPL fixed slope (alpha_Q = -1): chi_B = chi_E = chi_minus (r^a - 1)/(a ln r) */
-    double chiBg = (alpha == 0.0) ? chim : orc_ppl_mean_opacity(chim, alpha, -1.0, n1 / n0);
-    double chiEg = chiBg;
+    /* eq. chiQg for B_nu and E_nu (PC: chi_0 is flat, any spectrum gives chim) */
+    double chiBg = (alpha == 0.0) ? chim : orc_ppl_mean_opacity(chim, alpha, aB[g], n1 / n0);
+    double chiEg = (alpha == 0.0) ? chim : orc_ppl_mean_opacity(chim, alpha, aE[g], n1 / n0);
     /* eq. chiDiff.  The exact diffusion-limit flux mean is a positively
      * weighted mean of chi_0 over the group (weight B_nu - dB_nu/dln(nu)/3 > 0),
      * so it lies between the smallest and largest chi_0 inside the group; the
      * PPL estimate is held to that range (it can leave it, even turn negative,
      * for steep in-group slopes).  When b_g underflows the estimate is chi_E. */
-    double den = (4.0 / 3.0) * bg - dnbg / 3.0;
+    double den = (4.0 / 3.0) * bg[g] - dnbg / 3.0;
     double chiFg;
     if (den > 0.0)
-      chiFg = ((chiBg + chiEg / 3.0) * bg + (alpha * chiEg * bg - dnxbg) / 3.0) / den;
+      chiFg = ((chiBg + chiEg / 3.0) * bg[g] + (alpha * chiEg * bg[g] - dnxbg) / 3.0) / den;
     else
       chiFg = chiEg;
     double chlo = chim < chip ? chim : chip, chhi = chim < chip ? chip : chim;
     if (chiFg < chlo) chiFg = chlo;
     if (chiFg > chhi) chiFg = chhi;
-    if (b) b[g] = bg;
+    if (b) b[g] = bg[g];
     if (dnb) dnb[g] = dnbg;
     if (dnxb) dnxb[g] = dnxbg;
     if (chiB) chiB[g] = chiBg;
+    if (chiE) chiE[g] = chiEg;
     if (chiF) chiF[g] = chiFg;
   }
+  free(bg);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -323,7 +374,8 @@ typedef struct {
   int G;
   double rho, chi0s, m0[3], egas0, Etot, Eint0;
   const double *E0, *F0, *S; /* E0[g], F0[3g+d], S[g] (S may be NULL) */
-  double *b, *dnb, *dnxb, *chiB, *chiF;
+  const double *Es;           /* E0[g] + S[g]: the spectrum that sets alpha_E (free slopes) */
+  double *b, *dnb, *dnxb, *chiB, *chiE, *chiF;
 } orc_cell;
 
 static int orc_residual(const orc_cell *c, const double *y, double *r) {
@@ -335,7 +387,8 @@ static int orc_residual(const orc_cell *c, const double *y, double *r) {
   double m[3] = {y[1], y[2], y[3]};
   double v[3] = {m[0] / c->rho, m[1] / c->rho, m[2] / c->rho};
   double KE = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / c->rho;
-  orc_group_terms(p, c->gt, c->chi0s, T, c->b, c->dnb, c->dnxb, c->chiB, c->chiF);
+  orc_group_terms(p, c->gt, c->chi0s, T, c->Es, c->b, c->dnb, c->dnxb, c->chiB, c->chiE,
+                  c->chiF);
   double tdt = p->c_hat * p->theta * p->dt;
   double sumR = 0.0, dF[3] = {0.0, 0.0, 0.0};
   for (int g = 0; g < G; ++g) {
@@ -344,7 +397,7 @@ static int orc_residual(const orc_cell *c, const double *y, double *r) {
     const double *F = y + 4 + G + 3 * g;
     const double *F0 = c->F0 + 3 * g;
     double S = c->S ? c->S[g] : 0.0;
-    double chiE = c->chiB[g];
+    double chiE = c->chiE[g];
     double w = (v[0] * F[0] + v[1] * F[1] + v[2] * F[2]) / (p->c * p->c);
     double A = tdt * (c->chiB[g] * c->b[g] + (1.0 + alpha) * c->chiF[g] * w);
     r[4 + g] = E - (c->E0[g] + S + A) / (1.0 + tdt * chiE);
@@ -522,8 +575,8 @@ int orc_source_update(int64_t n_cells, const orc_params *p, const orc_groups *gt
     double *S = F0 + 3 * G; /* G */
     double *scratch = S + G; /* 5G needed, 2G + n left over is plenty */
     double *tb = scratch, *tdnb = tb + G, *tdnxb = tdnb + G;
-    double *tchiB = (double *)malloc(sizeof(double) * 2 * (size_t)G);
-    double *tchiF = tchiB + G;
+    double *tchiB = (double *)malloc(sizeof(double) * 4 * (size_t)G);
+    double *tchiE = tchiB + G, *tchiF = tchiE + G, *Es = tchiF + G;
 #ifdef _OPENMP
 #pragma omp for schedule(dynamic, 4)
 #endif
@@ -577,7 +630,10 @@ int orc_source_update(int64_t n_cells, const orc_params *p, const orc_groups *gt
       c.dnb = tdnb;
       c.dnxb = tdnxb;
       c.chiB = tchiB;
+      c.chiE = tchiE;
       c.chiF = tchiF;
+      for (int g = 0; g < G; ++g) Es[g] = E0[g] + S[g];
+      c.Es = Es;
       y[0] = Eint0;
       for (int d = 0; d < 3; ++d) y[1 + d] = m0[d];
       for (int g = 0; g < G; ++g) {

@@ -12,7 +12,8 @@
  * system of Sec. 3 -- eqs. egupdate, eupdate (energies), vupdate, fupdate
  * (momenta) -- with the four-force of eqs. G0_3 and G1_3 (Sec. 2.2.2), the
  * PPL fixed-slope mean opacities of eq. chiQg with alpha_Q = -1 (Sec. 2.2.2),
- * the diffusion-limit flux-mean opacity of eq. chiDiff, and a group-by-group
+ * (or the Appendix A slopes, free_slopes), the diffusion-limit flux-mean
+ * opacity of eq. chiDiff, and a group-by-group
  * closure for P_g (Sec. 2.1).  The root is found by a plain Newton iteration
  * on all 4+4*N_g unknowns with a finite-difference Jacobian and a dense
  * partial-pivot LU; the paper's conservative write-back (Sec. 3, after the
@@ -34,7 +35,7 @@ extern "C" {
 #endif
 
 enum { ORC_CLOSURE_M1 = 0, ORC_CLOSURE_EDDINGTON = 1 };
-enum { ORC_PPL_FIXED = 0, ORC_PC = 1 };
+enum { ORC_PPL_FIXED = 0, ORC_PC = 1, ORC_PPL_FREE = 2 };
 
 typedef struct {
   double c, c_hat, a_rad, h, k_B; /* constants (cgs or any consistent units) */
@@ -48,12 +49,18 @@ typedef struct {
 } orc_params;
 
 /* Per-group opacity table (Sec. 2.2.2): chi_0(nu) = rho*kappa0*khat_minus[g]*
- * (nu/nu_minus)^alpha[g] inside group g.  PC mode is alpha = 0 (Sec. 2.2.1). */
+ * (nu/nu_minus)^alpha[g] inside group g.  PC mode is alpha = 0 (Sec. 2.2.1).
+ * free_slopes = 0: the spectral indices alpha_Q of B_nu and E_nu inside every
+ * group are -1 (PPL fixed slope, Sec. 2.2.2).  free_slopes = 1: they come from
+ * the group values by the edge slopes and minmod of Appendix A -- alpha_B from
+ * b_g(T) at the temperature of every evaluation, alpha_E from the radiation
+ * energy the update starts from, E_g^t + S_g. */
 typedef struct {
   int32_t n_groups;
   const double *edges;      /* [n_groups+1] lab-frame group edges, increasing */
   const double *khat_minus; /* [n_groups] opacity shape at the lower edge */
   const double *alpha;      /* [n_groups] powerlaw index inside the group */
+  int32_t free_slopes;      /* 0: alpha_Q = -1; 1: Appendix A slopes */
 } orc_groups;
 
 /* Cumulative Planck fraction P(x) = (15/pi^4) int_0^x t^3/(e^t-1) dt and its
@@ -68,6 +75,18 @@ double orc_planck_band(double x0, double x1);
  * each bracket replaced by ln r when its exponent is zero. */
 double orc_ppl_mean_opacity(double chi_minus, double alpha_chi, double alpha_Q, double r);
 
+/* Spectral indices alpha_Q,g of a radiation quantity from its group values
+ * Q[g] (Appendix A, eqs. sg and minmod): the edge slopes s_(g+1/2) =
+ * ln(Qbar_(g+1)/Qbar_g) / ln(nubar_(g+1)/nubar_g) with Qbar_g = Q_g/(nu_g+ -
+ * nu_g-) and nubar_g = sqrt(nu_g+ nu_g-); alpha = -1 for the first and the
+ * last group and minmod(s_(g-1/2), s_(g+1/2)) between.  Reading: a slope
+ * whose Qbar is not positive on either side (or whose value is not finite) is
+ * undefined, and a group with an undefined edge slope takes -1 like the edge
+ * groups.  minmod(a, b) = the one of smaller magnitude when a and b have the
+ * same sign, else 0.  Edges must be finite and > 0. */
+void orc_ppl_free_slopes(int32_t n_groups, const double *edges, const double *Q,
+                         double *alpha_out);
+
 /* Group table from a piecewise-powerlaw opacity law (Sec. 2.2.2):
  * khat(nu) = exp(seg_logk[s] + seg_beta[s]*ln(nu/nu_ref)) in segment s, the
  * segments separated by n_seg-1 increasing breakpoints nu_break.  PPL_FIXED:
@@ -81,13 +100,16 @@ int orc_group_table(int32_t n_groups, const double *edges, int32_t mode, int32_t
                     double nu_ref, double *khat_minus_out, double *alpha_out);
 
 /* Group-integrated Planck terms and mean opacities at temperature T for one
- * cell (chi0_scale = rho*kappa0).  Outputs, each [n_groups]:
+ * cell (chi0_scale = rho*kappa0).  erad0: [n_groups] radiation energy whose
+ * spectral indices set chi_E when gt->free_slopes (may be NULL otherwise).
+ * Outputs, each [n_groups]:
  *   b     = 4 pi B_g / c
  *   dnb   = (4 pi / c) Delta_g(nu B_nu)
  *   dnxb  = (4 pi / c) Delta_g(nu chi_0 B_nu)
- *   chiB  = chiE (PPL fixed slope), chiF (eq. chiDiff).  Any pointer may be NULL. */
+ *   chiB, chiE (eq. chiQg), chiF (eq. chiDiff).  Any output pointer may be NULL. */
 void orc_group_terms(const orc_params *p, const orc_groups *gt, double chi0_scale, double T,
-                     double *b, double *dnb, double *dnxb, double *chiB, double *chiF);
+                     const double *erad0, double *b, double *dnb, double *dnxb, double *chiB,
+                     double *chiE, double *chiF);
 
 /* Closure P_g(E_g, F_g): M1 (Levermore 1984) or Eddington; P is 3x3 row-major. */
 void orc_closure(int32_t closure, double c, double E, const double F[3], double P[9]);
