@@ -60,6 +60,15 @@ extern "C" {
 /* rhd_opacity_law_t.mode */
 #define RHD_PPL_FIXED 0 /* piecewise powerlaw, alpha_Q = -1 (Sec. 2.2.2, favoured) */
 #define RHD_PC 1        /* piecewise constant (Sec. 2.2.1) */
+#define RHD_PPL_FREE 2  /* piecewise powerlaw opacity with the spectral indices alpha_Q of
+                           B_nu and E_nu fitted to the group values (Appendix A, eqs. sg and
+                           minmod; -1 in the first and last group and next to a group value
+                           that is not positive): alpha_B from b_g(T) at every Newton
+                           evaluation (with its T-derivative in the Jacobian), alpha_E from
+                           E_g^t + S_g of the cell.  Runs the FP64 passes with one cell per
+                           thread in either precision (the FP32 passes of RHD_MIXED are not
+                           built for it, so a warm start from them is skipped); not accepted
+                           by the batched interface (RHD_ELAW). */
 
 /* rhd_state_t.flags */
 #define RHD_GROUP_TEST 1 /* the outer iteration also stops only when, in every group,
@@ -127,10 +136,11 @@ typedef struct {
  * table given directly (the paper lets the user give the slopes, Sec. 2.2.2).
  * PPL_FIXED takes khat_gminus = khat just above nu_g- and alpha_g =
  * ln(khat(nu_g+)/khat(nu_g-))/ln(nu_g+/nu_g-) (Sec. 2.2.2, the tabulated-opacity
- * slope; a breakpoint on an edge belongs to the group above it).  PC takes khat
+ * slope; a breakpoint on an edge belongs to the group above it); PPL_FREE takes the
+ * same table.  PC takes khat
  * at the logarithmic group centre and alpha = 0.  All arrays are HOST memory. */
 typedef struct {
-  int32_t mode;            /* RHD_PPL_FIXED | RHD_PC */
+  int32_t mode;            /* RHD_PPL_FIXED | RHD_PC | RHD_PPL_FREE */
   int32_t n_seg;           /* 1 .. RHD_MAX_SEGMENTS (ignored when khat_gminus != NULL) */
   const double *nu_break;  /* [n_seg-1] */
   const double *seg_logk;  /* [n_seg] natural log of khat at nu_ref for the segment's powerlaw */

@@ -11,6 +11,7 @@
 
 #include "rhd_common.cuh"
 #include "rhd_fp64.cuh"
+#include "rhd_pplfree.cuh"
 #include "rhd_mixed.cuh"
 #include "rhd_batched.cuh"
 #include "rhd_warp.cuh"
@@ -168,13 +169,14 @@ int pack(const rhd_state_t *s, const rhd_groups_t *gr, const rhd_opacity_law_t *
   if (s->precision != RHD_FP64 && s->precision != RHD_MIXED) return RHD_EINVAL;
   if (s->closure != RHD_M1 && s->closure != RHD_EDDINGTON) return RHD_EINVAL;
   if (s->flags & ~(RHD_GROUP_TEST | RHD_FLUX_TEST | RHD_CELL_PER_THREAD)) return RHD_EINVAL;
-  if (law->mode != RHD_PPL_FIXED && law->mode != RHD_PC) return RHD_ELAW;
+  if (law->mode != RHD_PPL_FIXED && law->mode != RHD_PC && law->mode != RHD_PPL_FREE)
+    return RHD_ELAW;
   // edges: strictly increasing; PPL needs finite positive edges
   for (int e = 0; e <= G; ++e) {
     const double x = gr->edges[e];
     if (std::isnan(x) || x < 0.0) return RHD_EEDGES;
     if (e > 0 && !(x > gr->edges[e - 1])) return RHD_EEDGES;
-    if (law->mode == RHD_PPL_FIXED && !pos_finite(x)) return RHD_EEDGES;
+    if (law->mode != RHD_PC && !pos_finite(x)) return RHD_EEDGES;
     if (law->mode == RHD_PC && std::isinf(x) && e != G) return RHD_EEDGES;
   }
   std::memset(kp, 0, sizeof(KParams));
@@ -183,7 +185,7 @@ int pack(const rhd_state_t *s, const rhd_groups_t *gr, const rhd_opacity_law_t *
     for (int g = 0; g < G; ++g) {
       if (!pos_finite(law->khat_gminus[g])) return RHD_ELAW;
       kp->khat_g[g] = law->khat_gminus[g];
-      if (law->mode == RHD_PPL_FIXED) {
+      if (law->mode != RHD_PC) {
         if (!law->alpha_g || !std::isfinite(law->alpha_g[g])) return RHD_ELAW;
         kp->alpha_g[g] = law->alpha_g[g];
       }
@@ -267,6 +269,14 @@ void launch_warp(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st
 }
 
 template <int MAXG>
+void launch_free(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
+  const int threads = 128;
+  const size_t smem = free_table_bytes(kp.G);
+  const int b = persistent_blocks(solve_free_kernel<MAXG>, smem, sms, kp.n, threads);
+  solve_free_kernel<MAXG><<<b, threads, smem, st>>>(kp, W);
+}
+
+template <int MAXG>
 void launch_thread(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
   const int threads = 128;
   const size_t smem = table_bytes(kp.G);
@@ -297,6 +307,12 @@ void launch_fp64_passes(const KParams &kp, const WarmStart &W, int sms, cudaStre
 // (rhd_warp.cuh; the split measured on GB300), one cell per thread again past
 // 128 groups, where a lane's share of the groups no longer fits in registers.
 void launch_fp64_passes_impl(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
+  if (kp.mode == RHD_PPL_FREE) {  // free slopes: one cell per thread (rhd_pplfree.cuh)
+    if (kp.G <= 16) launch_free<16>(kp, W, sms, st);
+    else if (kp.G <= 64) launch_free<64>(kp, W, sms, st);
+    else launch_free<kMaxG>(kp, W, sms, st);
+    return;
+  }
   if (kp.flags & RHD_CELL_PER_THREAD) {
     if (kp.G <= 16) launch_thread<16>(kp, W, sms, st);
     else if (kp.G <= 64) launch_thread<64>(kp, W, sms, st);
@@ -331,6 +347,10 @@ template <int MAXG>
 int launch_mixed(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int sms,
                  cudaStream_t st) {
   const WarmStart none{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+  if (kp.mode == RHD_PPL_FREE) {  // no FP32 passes for free slopes: FP64 from the cold start
+    launch_fp64_passes(kp, none, sms, st);
+    return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
+  }
   launch_fp32_passes<MAXG>(kp, wo, none, sms, st);
   launch_fp64_passes(kp, wi, sms, st);
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
@@ -342,7 +362,8 @@ int launch_mixed(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int 
 template <int MAXG>
 int launch_warm_g(const KParams &kp, int precision, const WarmOut &wo, const WarmStart &wi,
                   int sms, cudaStream_t st) {
-  if (precision == RHD_MIXED) launch_fp32_passes<MAXG>(kp, wo, wi, sms, st);
+  if (precision == RHD_MIXED && kp.mode != RHD_PPL_FREE)
+    launch_fp32_passes<MAXG>(kp, wo, wi, sms, st);
   launch_fp64_passes(kp, wi, sms, st);
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
 }
@@ -599,6 +620,7 @@ int pack_batch(rhd_context *c, const rhd_grid_t *grids, int n_grids, int cpi, in
     const rhd_grid_t &g = grids[j];
     const int rc = pack(&g.state, &g.groups, &g.opacity_law, g.dt, g.n_cells, &c->h_grids[j]);
     if (rc != RHD_OK) return rc;
+    if (g.opacity_law.mode == RHD_PPL_FREE) return RHD_ELAW;  // per-cell solve only
     if (g.groups.n_groups > kMaxGB) return RHD_ESIZE;
     if (*prec < 0) *prec = g.state.precision;
     if (g.state.precision != *prec) return RHD_EINVAL;

@@ -116,7 +116,7 @@ __device__ inline GroupTable build_table(const KParams &P, double *smem) {
     xe[t] = P.h_over_k * P.edges[t];  // inf stays inf, 0 stays 0
     if (t == G) continue;
     const double n0 = P.edges[t], n1 = P.edges[t + 1];
-    if (P.mode == RHD_PPL_FIXED) {
+    if (P.mode != RHD_PC) {  // PPL, fixed or free slopes: same per-group law
       const double lr = log(n1 / n0);
       double lk0, a;
       if (P.has_table) {

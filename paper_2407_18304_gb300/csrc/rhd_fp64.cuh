@@ -141,14 +141,15 @@ __device__ __forceinline__ bool load_cell(const KParams &P, int64_t i, Cell &C, 
 }
 
 // 1/tau_E and -1/e_g = tau_E/(1 + tau_E) per group for opacity scale cs.
+// ikE: per-group 1/(chi_E / cs) of the cell (free slopes), else the table's.
 template <int MAXG>
 __device__ __forceinline__ void set_tau(const KParams &P, const GroupTable &tab, Cell &C,
-                                        Arr64<MAXG> &A, double cs) {
+                                        Arr64<MAXG> &A, double cs, const double *ikE = nullptr) {
   const double tdt = P.c_hat * P.theta * P.dt;
   C.cs = cs;
   C.its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
   for (int g = 0; g < P.G; ++g) {
-    const double it = C.its * tab.ikbar[g];  // 1/tau_E (0 marks an uncoupled group)
+    const double it = C.its * (ikE ? ikE[g] : tab.ikbar[g]);  // 1/tau_E (0: uncoupled)
     A.qe[g] = it > 0.0 ? 1.0 / (1.0 + it) : 0.0;
   }
 }
@@ -166,6 +167,41 @@ __device__ __forceinline__ void outer_begin(const KParams &P, Cell &C, Arr64<MAX
   C.it = 0;
 }
 
+// a8 and the Newton step of a7, after the residual of every group is in
+// A.FR/A.dg and its sums are taken: the convergence test (then each R_g from
+// its own row, return 1), the iteration cap (return 2), or the arrowhead
+// elimination of eq. matrix and the step (return 0).
+template <int MAXG>
+__device__ __forceinline__ int inner_tail(const KParams &P, Cell &C, Arr64<MAXG> &A, double sumR,
+                                          double sFRe, double sde, double sabs) {
+  const int G = P.G;
+  const double cr = P.c / P.c_hat;
+  const double FG = C.Eint + C.KE - C.eg0 + cr * sumR;
+  // a8: convergence test
+  if (fabs(FG) < P.tol * C.Etot && cr * sabs < P.tol * C.Etot) {
+    // each R_g from its own row of eq. FGFR at the converged T (the arrowhead
+    // rows with dE = 0): groups far below E_tot, which the aggregate test
+    // cannot see, end consistent with T to round-off
+    for (int g = 0; g < G; ++g)
+      if (A.qe[g] > 0.0) A.R[g] += A.FR[g] * A.qe[g];
+    return 1;
+  }
+  if (C.it >= P.max_newton) return 2;
+  // a7: arrowhead elimination of eq. matrix: dE from the reduced first row,
+  // then each dR_g from its own row
+  const double dE = (-FG + cr * sFRe) / (1.0 - cr * sde);
+  double lam = 1.0;
+  for (int k = 0; k < 40 && !(C.Eint + lam * dE > 0.0); ++k) lam *= 0.5;
+  C.Eint += lam * dE;
+  for (int g = 0; g < G; ++g) {
+    const double ie = A.qe[g] > 0.0 ? A.qe[g] : 1.0;
+    A.R[g] += lam * (A.FR[g] + A.dg[g] * dE) * ie;
+  }
+  ++C.nit;
+  ++C.it;
+  return 0;
+}
+
 // One inner Newton iteration (a4-a8): evaluate the residual at the current
 // iterate; if the convergence test passes, set each R_g from its own row and
 // return 1; at the iteration cap return 2; else take the Newton step, return 0.
@@ -174,7 +210,6 @@ __device__ __forceinline__ int inner_step(const KParams &P, const GroupTable &ta
                                           Arr64<MAXG> &A) {
   const int G = P.G;
   const int64_t i = C.i;
-  const double cr = P.c / P.c_hat;
   const double T = C.Eint * C.irc;
   if (P.temp_exp != 0.0) set_tau(P, tab, C, A, C.chi0s * pow(T / P.T_ref, P.temp_exp));
   const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
@@ -225,56 +260,34 @@ __device__ __forceinline__ int inner_step(const KParams &P, const GroupTable &ta
     eL = eU;
     lowL = lowU;
   }
-  const double FG = C.Eint + C.KE - C.eg0 + cr * sumR;
-  // a8: convergence test
-  if (fabs(FG) < P.tol * C.Etot && cr * sabs < P.tol * C.Etot) {
-    // each R_g from its own row of eq. FGFR at the converged T (the arrowhead
-    // rows with dE = 0): groups far below E_tot, which the aggregate test
-    // cannot see, end consistent with T to round-off
-    for (int g = 0; g < G; ++g)
-      if (A.qe[g] > 0.0) A.R[g] += A.FR[g] * A.qe[g];
-    return 1;
-  }
-  if (C.it >= P.max_newton) return 2;
-  // a7: arrowhead elimination of eq. matrix: dE from the reduced first row,
-  // then each dR_g from its own row
-  const double dE = (-FG + cr * sFRe) / (1.0 - cr * sde);
-  double lam = 1.0;
-  for (int k = 0; k < 40 && !(C.Eint + lam * dE > 0.0); ++k) lam *= 0.5;
-  C.Eint += lam * dE;
-  for (int g = 0; g < G; ++g) {
-    const double ie = A.qe[g] > 0.0 ? A.qe[g] : 1.0;
-    A.R[g] += lam * (A.FR[g] + A.dg[g] * dE) * ie;
-  }
-  ++C.nit;
-  ++C.it;
-  return 0;
+  return inner_tail(P, C, A, sumR, sFRe, sde, sabs);
 }
 
 // a9-a12 after an inner solve: write-back, flux and momentum update, outer
 // test.  Returns true when the cell is done (converged or at a cap); else the
 // next outer pass has been set up.
 // The Newton part of flux_update for the groups whose eq. numF1 step
-// contracts by less than 1/2 per outer pass.  Fk holds the eq. numF1 values
+// contracts by less than 1/2 per outer pass (kE[g] = chi_E / cs; bq = chi_B
+// b_g / chi_E).  Fk holds the eq. numF1 values
 // and is updated; returns the change of their sum and its l1 size.  Out of
 // line (few cells take it) with scalar and array arguments only, so that the
 // caller's cell state stays in registers.
 __device__ __noinline__ FluxDelta flux_newton_pass(
     int G, int64_t i, int64_t gs, const double *erad, const double *src, const double *ft0p,
-    const double *ft1p, const double *ft2p, const double *kbar, const double *alpha,
+    const double *ft1p, const double *ft2p, const double *kE, const double *alpha,
     const double *R, const double *bq, const double *dnx, const double *qF, double *Fk, double c,
     double tdt, double cs, double v0, double v1, double v2) {
   const double vmag = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
   FluxDelta d = {0.0, 0.0, 0.0, 0.0};
   for (int g = 0; g < G; ++g) {
     const int64_t o = (int64_t)g * gs + i;
-    const double chiB = cs * kbar[g];
-    const double inv = 1.0 / (1.0 + tdt * chiB * qF[g]);
-    const double kap = tdt * (1.0 + alpha[g]) * chiB * inv;
+    const double chiE = cs * kE[g];
+    const double inv = 1.0 / (1.0 + tdt * chiE * qF[g]);
+    const double kap = tdt * (1.0 + alpha[g]) * chiE * inv;
     if (!(10.0 * fabs(kap) * vmag > c)) continue;
     const double s = src ? src[o] : 0.0;
     const double Enew = erad[o] + R[g] + s;
-    const double srcg = chiB * (bq[g] - dnx[g] * (1.0 / 3.0));
+    const double srcg = chiE * (bq[g] - dnx[g] * (1.0 / 3.0));
     const Vec3<double> F = flux_newton<double>(
         c, Enew, kap, (ft0p[o] + tdt * v0 * srcg) * inv, (ft1p[o] + tdt * v1 * srcg) * inv,
         (ft2p[o] + tdt * v2 * srcg) * inv, v0, v1, v2, Fk[3 * g], Fk[3 * g + 1], Fk[3 * g + 2],
@@ -290,9 +303,11 @@ __device__ __noinline__ FluxDelta flux_newton_pass(
   return d;
 }
 
+// kE: per-group chi_E / cs of the cell (free slopes), else the table's kbar.
 template <int MAXG>
 __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &tab, Cell &C,
-                                          Arr64<MAXG> &A) {
+                                          Arr64<MAXG> &A, const double *kE = nullptr) {
+  const double *kq = kE ? kE : tab.kbar;
   const int G = P.G;
   const int64_t i = C.i;
   const double c = P.c, chat = P.c_hat, cr = c / chat;
@@ -319,13 +334,13 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
     const int64_t o = (int64_t)g * P.gs + i;
     const double s = P.src ? P.src[o] : 0.0;
     const double Enew = P.erad[o] + A.R[g] + s;
-    const double chiB = C.cs * tab.kbar[g], a = tab.alpha[g];
+    const double chiE = C.cs * kq[g], a = tab.alpha[g];  // A.bq holds chi_B b_g / chi_E
     double vp0, vp1, vp2;
     closure_vP<double>(P.closure, c, Enew, A.Fk[3 * g], A.Fk[3 * g + 1], A.Fk[3 * g + 2], v[0],
                        v[1], v[2], vp0, vp1, vp2);
-    const double srcg = chiB * (A.bq[g] - A.dnx[g] * (1.0 / 3.0));
-    const double inv = 1.0 / (1.0 + tdt * chiB * A.qF[g]);
-    const double kap = tdt * (1.0 + a) * chiB * inv;
+    const double srcg = chiE * (A.bq[g] - A.dnx[g] * (1.0 / 3.0));
+    const double inv = 1.0 / (1.0 + tdt * chiE * A.qF[g]);
+    const double kap = tdt * (1.0 + a) * chiE * inv;
     newton = newton || 10.0 * fabs(kap) * vmag > c;
     const double ft0 = P.frad[0][o], ft1 = P.frad[1][o], ft2 = P.frad[2][o];
     const double n0 = (ft0 + tdt * v[0] * srcg) * inv + kap * vp0;
@@ -341,7 +356,7 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
   }
   if (newton && C.slow && P.closure == RHD_M1) {
     const FluxDelta d =
-        flux_newton_pass(G, i, P.gs, P.erad, P.src, P.frad[0], P.frad[1], P.frad[2], tab.kbar,
+        flux_newton_pass(G, i, P.gs, P.erad, P.src, P.frad[0], P.frad[1], P.frad[2], kq,
                          tab.alpha, A.R, A.bq, A.dnx, A.qF, A.Fk, c, tdt, C.cs, v[0], v[1], v[2]);
     dF[0] += d.x;
     dF[1] += d.y;
@@ -361,7 +376,7 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
   for (int g = 0; g < G; ++g) {
     const double wn =
         (vn[0] * A.Fk[3 * g] + vn[1] * A.Fk[3 * g + 1] + vn[2] * A.Fk[3 * g + 2]) * inv_c2;
-    const double tauE = tdt * C.cs * tab.kbar[g];
+    const double tauE = tdt * C.cs * kq[g];
     const double cg = fabs(tauE * (1.0 + tab.alpha[g]) * A.qF[g] * (wn - A.w[g])) / (1.0 + tauE);
     chg += cg;
     if (gtest) {

@@ -16,7 +16,7 @@ from . import build as _build
 
 FP64, MIXED = 0, 1
 M1, EDDINGTON = 0, 1
-PPL_FIXED, PC = 0, 1
+PPL_FIXED, PC, PPL_FREE = 0, 1, 2
 STATUS_OK, STATUS_FALLBACK, STATUS_MAXITER, STATUS_INVALID = 0, 1, 2, 3
 GROUP_TEST = 1
 FLUX_TEST = 2

@@ -10,12 +10,13 @@ from paper_2407_18304_gb300 import rhd, synth
 
 
 def oracle_groups(w, mode=O.PPL_FIXED, khat_g=None, alpha_g=None):
+    free = mode == O.PPL_FREE
     if khat_g is not None:
         al = np.zeros(len(khat_g)) if alpha_g is None else np.asarray(alpha_g, float)
-        return O.Groups(w.edges, np.asarray(khat_g, float), al)
+        return O.Groups(w.edges, np.asarray(khat_g, float), al, free_slopes=free)
     km, al = O.group_table(w.edges, mode, w.law.nu_break, w.law.seg_logk, w.law.seg_beta,
                            w.law.nu_ref)
-    return O.Groups(w.edges, km, al)
+    return O.Groups(w.edges, km, al, free_slopes=free)
 
 
 def run_oracle(w, *, theta=1.0, closure=rhd.M1, c_hat=None, mode=O.PPL_FIXED, khat_g=None,

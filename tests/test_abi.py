@@ -36,7 +36,7 @@ def test_every_declared_symbol_is_exported(lib):
         assert hasattr(lib, n), n
 
 
-def _call(lib, edges, law=None, n_cells=0, **fields):
+def _call(lib, edges, law=None, n_cells=0, mode=rhd.PPL_FIXED, **fields):
     w = synth.preset("tiny", n_cells=1)
     st = rhd.State()
     st.c_v, st.theta = w.c_v, 1.0
@@ -45,7 +45,7 @@ def _call(lib, edges, law=None, n_cells=0, **fields):
         setattr(st, k, v)
     e = np.ascontiguousarray(edges, dtype=np.float64)
     gr = rhd.Groups(len(e) - 1, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
-    lw, keep = rhd.make_law(law if law is not None else w.law)
+    lw, keep = rhd.make_law(law if law is not None else w.law, mode)
     return lib.rhd_source_update(ctypes.byref(st), ctypes.byref(gr), ctypes.byref(lw), w.dt,
                                  n_cells, None)
 
@@ -57,6 +57,11 @@ def test_argument_checks_without_a_device(lib):
     bad[2] = bad[1]
     assert _call(lib, bad) == -2
     assert _call(lib, np.concatenate([[0.0], edges[1:]])) == -2  # PPL needs nu > 0
+    assert _call(lib, edges, mode=rhd.PPL_FREE) == 0
+    assert _call(lib, np.concatenate([[0.0], edges[1:]]), mode=rhd.PPL_FREE) == -2
+    assert _call(lib, np.concatenate([edges[:-1], [np.inf]]), mode=rhd.PPL_FREE) == -2
+    assert _call(lib, np.concatenate([[0.0], edges[1:]]), mode=rhd.PC) == 0
+    assert _call(lib, edges, mode=3) == -3
     assert _call(lib, synth.log_edges(300)) == -6
     assert _call(lib, edges, c_v=-1.0) == -1
     assert _call(lib, edges, precision=7) == -1
