@@ -78,6 +78,8 @@ struct Cell {
   double chg_prev; // outer-test change of the previous pass
   int nit, stat, it, outer;
   int slow;        // the outer iteration contracted slowly: Newton flux steps on
+  int fresh;       // the last inner step converged: FR_g ~ 0 at the current T, R_g
+  int cached;      // A.FR holds the residual at the current T, R_g (see inner_cached)
 };
 
 // Thread-local per-group arrays of the FP64 passes.
@@ -137,6 +139,8 @@ __device__ __forceinline__ bool load_cell(const KParams &P, int64_t i, Cell &C, 
   C.it = 0;
   C.chg_prev = HUGE_VAL;
   C.slow = 0;
+  C.fresh = 0;
+  C.cached = 0;
   return true;
 }
 
@@ -184,8 +188,10 @@ __device__ __forceinline__ int inner_tail(const KParams &P, Cell &C, Arr64<MAXG>
     // cannot see, end consistent with T to round-off
     for (int g = 0; g < G; ++g)
       if (A.qe[g] > 0.0) A.R[g] += A.FR[g] * A.qe[g];
+    C.fresh = 1;
     return 1;
   }
+  C.fresh = 0;
   if (C.it >= P.max_newton) return 2;
   // a7: arrowhead elimination of eq. matrix: dE from the reduced first row,
   // then each dR_g from its own row
@@ -202,12 +208,36 @@ __device__ __forceinline__ int inner_tail(const KParams &P, Cell &C, Arr64<MAXG>
   return 0;
 }
 
+// The first inner iteration of an outer pass after a converged one.  T and
+// R_g are still those of the last full evaluation, where each row of eq. FGFR
+// was solved to round-off (R_g += FR_g qe_g), and the outer step changed only
+// v (so E_kin) and F_g: the residual of row g is then exactly its v.F_g term,
+// (1 + alpha) (chi_F/chi_E) (w_new - w_old), which outer_end left in A.FR,
+// and b_g, chi_F, dF_R,g/dE_gas are unchanged.  The test and the Newton step
+// are those of a full evaluation; the next evaluation is a full one at the
+// stepped T.
+template <int MAXG>
+__device__ __forceinline__ int inner_cached(const KParams &P, Cell &C, Arr64<MAXG> &A) {
+  C.cached = 0;
+  double sumR = 0.0, sFRe = 0.0, sde = 0.0, sabs = 0.0;
+  for (int g = 0; g < P.G; ++g) {
+    const double fr = A.FR[g];
+    const double iee = A.qe[g] > 0.0 ? A.qe[g] : 1.0;
+    sumR += A.R[g];
+    sFRe -= fr * iee;
+    sde -= A.dg[g] * iee;
+    sabs += fabs(fr);
+  }
+  return inner_tail(P, C, A, sumR, sFRe, sde, sabs);
+}
+
 // One inner Newton iteration (a4-a8): evaluate the residual at the current
 // iterate; if the convergence test passes, set each R_g from its own row and
 // return 1; at the iteration cap return 2; else take the Newton step, return 0.
 template <int MAXG>
 __device__ __forceinline__ int inner_step(const KParams &P, const GroupTable &tab, Cell &C,
                                           Arr64<MAXG> &A) {
+  if (C.cached) return inner_cached(P, C, A);
   const int G = P.G;
   const int64_t i = C.i;
   const double T = C.Eint * C.irc;
@@ -377,8 +407,10 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
     const double wn =
         (vn[0] * A.Fk[3 * g] + vn[1] * A.Fk[3 * g + 1] + vn[2] * A.Fk[3 * g + 2]) * inv_c2;
     const double tauE = tdt * C.cs * kq[g];
-    const double cg = fabs(tauE * (1.0 + tab.alpha[g]) * A.qF[g] * (wn - A.w[g])) / (1.0 + tauE);
+    const double dvf = (1.0 + tab.alpha[g]) * A.qF[g] * (wn - A.w[g]);
+    const double cg = fabs(tauE * dvf) / (1.0 + tauE);
     chg += cg;
+    A.FR[g] = A.qe[g] > 0.0 ? dvf : -A.R[g];  // the residual at T, R_g for the new w (inner_cached)
     if (gtest) {
       const int64_t o = (int64_t)g * P.gs + i;
       const double s = P.src ? P.src[o] : 0.0;
@@ -398,7 +430,14 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
     C.stat = RHD_STATUS_MAXITER;
     return true;
   }
-  // warm start of the next inner solve from the written-back gas energy
+  if (C.fresh) {
+    // the next inner solve starts at this T and R_g, where its first
+    // residual is known without evaluating the groups (inner_cached)
+    outer_begin(P, C, A);
+    C.cached = 1;
+    return false;
+  }
+  // otherwise from the written-back gas energy
   C.Eint = C.egas_new - KEn;
   if (!(C.Eint > 0.0)) {
     C.stat = RHD_STATUS_MAXITER;

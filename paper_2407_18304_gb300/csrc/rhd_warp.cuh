@@ -23,6 +23,7 @@ struct WCell {
   double rho, m0[3], eg0, chi0s, Etot, rcv, irc;
   double m[3], v[3], KE, Eint, egas_new, cs, its, chg_prev;
   int nit, stat, it, outer, slow;
+  int fresh, cached;  // as Cell::fresh, Cell::cached
   double R[GPL], w[GPL], FR[GPL], dg[GPL], qe[GPL], bq[GPL], dnx[GPL], qF[GPL];
   double itau[GPL];   // 1/tau_E of the group (0 when uncoupled)
   double E0[GPL];     // E_g^t + S_g
@@ -97,6 +98,8 @@ __device__ __forceinline__ bool wload(const KParams &P, int64_t i, int l, unsign
   C.it = 0;
   C.chg_prev = HUGE_VAL;
   C.slow = 0;
+  C.fresh = 0;
+  C.cached = 0;
   return true;
 }
 
@@ -151,13 +154,67 @@ __device__ __forceinline__ void wouter_begin(const KParams &P, WCell<L, GPL> &C)
   C.it = 0;
 }
 
+// The sums over the cell's groups, the convergence test and the Newton step
+// of an inner iteration (as inner_tail; the per-lane partial sums in).
+template <int L, int GPL>
+__device__ __forceinline__ int wtail(const KParams &P, unsigned mask, WCell<L, GPL> &C,
+                                     double sumR, double sFRe, double sde, double sabs) {
+  const double cr = P.c / P.c_hat;
+  sumR = seg_sum<L>(sumR, mask);
+  sFRe = seg_sum<L>(sFRe, mask);
+  sde = seg_sum<L>(sde, mask);
+  sabs = seg_sum<L>(sabs, mask);
+  const double FG = C.Eint + C.KE - C.eg0 + cr * sumR;
+  if (fabs(FG) < P.tol * C.Etot && cr * sabs < P.tol * C.Etot) {
+#pragma unroll
+    for (int j = 0; j < GPL; ++j)
+      if (C.qe[j] > 0.0) C.R[j] += C.FR[j] * C.qe[j];
+    C.fresh = 1;
+    return 1;
+  }
+  C.fresh = 0;
+  if (C.it >= P.max_newton) return 2;
+  const double dE = (-FG + cr * sFRe) / (1.0 - cr * sde);
+  double lam = 1.0;
+  for (int k = 0; k < 40 && !(C.Eint + lam * dE > 0.0); ++k) lam *= 0.5;
+  C.Eint += lam * dE;
+#pragma unroll
+  for (int j = 0; j < GPL; ++j) {
+    const double ie = C.qe[j] > 0.0 ? C.qe[j] : 1.0;
+    C.R[j] += lam * (C.FR[j] + C.dg[j] * dE) * ie;
+  }
+  ++C.nit;
+  ++C.it;
+  return 0;
+}
+
+// The first inner iteration of an outer pass after a converged one (as
+// inner_cached): C.FR holds the v.F-term change that wouter_end left there.
+template <int L, int GPL>
+__device__ __forceinline__ int winner_cached(const KParams &P, int l, unsigned mask,
+                                             WCell<L, GPL> &C) {
+  C.cached = 0;
+  double sumR = 0.0, sFRe = 0.0, sde = 0.0, sabs = 0.0;
+#pragma unroll
+  for (int j = 0; j < GPL; ++j) {
+    if (l + L * j >= P.G) continue;
+    const double fr = C.FR[j];
+    const double iee = C.qe[j] > 0.0 ? C.qe[j] : 1.0;
+    sumR += C.R[j];
+    sFRe -= fr * iee;
+    sde -= C.dg[j] * iee;
+    sabs += fabs(fr);
+  }
+  return wtail(P, mask, C, sumR, sFRe, sde, sabs);
+}
+
 // One inner Newton iteration (a4-a8), as inner_step.
 template <int L, int GPL>
 __device__ __forceinline__ int winner_step(const KParams &P, const GroupTable &tab, int l,
                                            int lane0, unsigned mask, WCell<L, GPL> &C) {
+  if (C.cached) return winner_cached(P, l, mask, C);
   constexpr int NE = GPL + 1;
   const int G = P.G;
-  const double cr = P.c / P.c_hat;
   const double T = C.Eint * C.irc;
   if (P.temp_exp != 0.0) wset_tau(P, tab, l, C, C.chi0s * pow(T / P.T_ref, P.temp_exp));
   const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
@@ -237,30 +294,7 @@ __device__ __forceinline__ int winner_step(const KParams &P, const GroupTable &t
     sde -= d * iee;
     sabs += fabs(fr);
   }
-  sumR = seg_sum<L>(sumR, mask);
-  sFRe = seg_sum<L>(sFRe, mask);
-  sde = seg_sum<L>(sde, mask);
-  sabs = seg_sum<L>(sabs, mask);
-  const double FG = C.Eint + C.KE - C.eg0 + cr * sumR;
-  if (fabs(FG) < P.tol * C.Etot && cr * sabs < P.tol * C.Etot) {
-#pragma unroll
-    for (int j = 0; j < GPL; ++j)
-      if (C.qe[j] > 0.0) C.R[j] += C.FR[j] * C.qe[j];
-    return 1;
-  }
-  if (C.it >= P.max_newton) return 2;
-  const double dE = (-FG + cr * sFRe) / (1.0 - cr * sde);
-  double lam = 1.0;
-  for (int k = 0; k < 40 && !(C.Eint + lam * dE > 0.0); ++k) lam *= 0.5;
-  C.Eint += lam * dE;
-#pragma unroll
-  for (int j = 0; j < GPL; ++j) {
-    const double ie = C.qe[j] > 0.0 ? C.qe[j] : 1.0;
-    C.R[j] += lam * (C.FR[j] + C.dg[j] * dE) * ie;
-  }
-  ++C.nit;
-  ++C.it;
-  return 0;
+  return wtail(P, mask, C, sumR, sFRe, sde, sabs);
 }
 
 // a9-a12, as outer_end.
@@ -352,7 +386,9 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
     if (g >= G) continue;
     const double wn = (vn[0] * C.Fk[j][0] + vn[1] * C.Fk[j][1] + vn[2] * C.Fk[j][2]) * inv_c2;
     // tau_E / (1 + tau_E) = qe (0 for an uncoupled group, whose term is 0)
-    const double cg = fabs((1.0 + tab.alpha[g]) * C.qF[j] * (wn - C.w[j])) * C.qe[j];
+    const double dvf = (1.0 + tab.alpha[g]) * C.qF[j] * (wn - C.w[j]);
+    const double cg = fabs(dvf) * C.qe[j];
+    C.FR[j] = C.qe[j] > 0.0 ? dvf : -C.R[j];  // the residual at T, R_g for the new w
     cg_sum += cg;
     if (gtest) {
       const double e0 = C.E0[j];  // E^t + S (the group's own energy scale)
@@ -373,6 +409,11 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
   if (C.outer >= P.max_outer) {
     C.stat = RHD_STATUS_MAXITER;
     return true;
+  }
+  if (C.fresh) {  // next pass starts at this T, R_g with a known residual
+    wouter_begin(P, C);
+    C.cached = 1;
+    return false;
   }
   C.Eint = C.egas_new - KEn;
   if (!(C.Eint > 0.0)) {
