@@ -169,7 +169,7 @@ __device__ inline GroupTable build_table(const KParams &P, double *smem) {
 
 // FP64 edge values: pq = P(x) when low (x < 2), else Q(x) = 1 - P(x);
 // d = D(x) = (15/pi^4) x^4/(e^x-1) and ed = x dD/dx = D (4 - x e^x/(e^x-1)).
-// One expm1 gives x/(e^x - 1) and e^-x = 1/(expm1(x) + 1); P and Q come from the
+// One expm1 and one division give x/(e^x - 1) and e^-x = 1/(expm1(x) + 1); P and Q come from the
 // piecewise polynomials of planck_table.h (P = 15/pi^4 x^3 g(x) below x = 2,
 // Q = 15/pi^4 x^3 e^-x h(x) above), the segment read off the exponent and two
 // leading mantissa bits of x: every x takes the same instructions, so the
@@ -193,8 +193,16 @@ __device__ __forceinline__ void edge_tab(const double *pc, double x, double &pq,
     return;
   }
   const double em = expm1(x);
-  const double xr = x / em;          // x/(e^x - 1)
-  const double emx = 1.0 / (em + 1.0);  // e^-x
+  double xr, emx;  // x/(e^x - 1), e^-x
+  if (x < 300.0) {  // one reciprocal of (e^x - 1) e^x serves both (no overflow below 354)
+    const double ep = em + 1.0;
+    const double r = 1.0 / (em * ep);
+    xr = x * ep * r;
+    emx = em * r;
+  } else {
+    xr = x / em;
+    emx = 1.0 / (em + 1.0);
+  }
   const double x3 = x * x * x;
   d = kPlanckNorm * x3 * xr;
   ed = d * (4.0 - xr - x);  // x e^x/(e^x-1) = x/(e^x-1) + x
@@ -218,30 +226,43 @@ __device__ __forceinline__ double band_fp64(double pqL, bool lowL, double pqU, b
   return (1.0 - pqU) - pqL;               // edges straddle the split
 }
 
-// v . P_g for the closure P(E, F) applied to one group (Sec. 2.1).
+// v . P_g for the closure P(E, F) applied to one group (Sec. 2.1).  M1:
+// P = E [iso I + dir n n^T], n = F/|F|, iso = (1 - chi)/2, dir = (3 chi - 1)/2
+// with Levermore's chi(f) = (3 + 4 f^2)/(5 + 2 sqrt(4 - 3 f^2)), f = |F|/(cE).
+// Multiplying numerator and denominator by 5 - 2 sqrt(4 - 3 f^2) turns the
+// denominator into 3 (3 + 4 f^2), so chi = (5 - 2 s)/3 with s = sqrt(4 - 3 f^2):
+// iso = (s - 1)/3 and dir = 2 - s = 3 f^2 / (2 + s).  With S = cE s =
+// sqrt(4 (cE)^2 - 3 |F|^2) that is
+//   v . P = [(S - cE)/3 v + 3 (v . F) F / (2 cE + S)] / c,
+// one square root and one division.  f >= 1 is held at 1 (chi = 1):
+// v . P = E (v . F) F / |F|^2.
 template <typename R>
 __device__ __forceinline__ void closure_vP(int closure, R c, R E, R F0, R F1, R F2, R v0, R v1,
                                            R v2, R &o0, R &o1, R &o2) {
   const R fn2 = F0 * F0 + F1 * F1 + F2 * F2;
-  R iso = R(1) / R(3), dir = R(0);
-  R n0 = R(0), n1 = R(0), n2 = R(0);
   if (closure == RHD_M1 && E > R(0) && fn2 > R(0)) {
-    const R inv = rsqrt(fn2);  // 1/|F|
-    const R fn = fn2 * inv;
-    R f = fn / (c * E);
-    if (f > R(1)) f = R(1);
-    const R f2 = f * f;
-    const R chi = (R(3) + R(4) * f2) / (R(5) + R(2) * sqrt(R(4) - R(3) * f2));
-    iso = R(0.5) * (R(1) - chi);
-    dir = R(0.5) * (R(3) * chi - R(1));
-    n0 = F0 * inv;
-    n1 = F1 * inv;
-    n2 = F2 * inv;
+    const R cE = c * E, cE2 = cE * cE;
+    const R vF = v0 * F0 + v1 * F1 + v2 * F2;
+    if (fn2 < cE2) {
+      const R S = sqrt(R(4) * cE2 - R(3) * fn2);
+      const R ic = R(1) / c;
+      const R a = (S - cE) * (R(1) / R(3)) * ic;
+      const R k = R(3) * vF * ic / (R(2) * cE + S);
+      o0 = a * v0 + k * F0;
+      o1 = a * v1 + k * F1;
+      o2 = a * v2 + k * F2;
+    } else {
+      const R k = E * vF / fn2;
+      o0 = k * F0;
+      o1 = k * F1;
+      o2 = k * F2;
+    }
+    return;
   }
-  const R vn = (v0 * n0 + v1 * n1 + v2 * n2) * dir;
-  o0 = E * (iso * v0 + vn * n0);
-  o1 = E * (iso * v1 + vn * n1);
-  o2 = E * (iso * v2 + vn * n2);
+  const R e3 = E * (R(1) / R(3));
+  o0 = e3 * v0;
+  o1 = e3 * v1;
+  o2 = e3 * v2;
 }
 
 // v . P_g and M = d(v . P_g)/dF_g at fixed E_g for the M1 closure of
