@@ -67,7 +67,7 @@ __device__ __forceinline__ R chiF_q(R b, R aT4, R dD, R a, R rm, R rp, R dL, R d
 // Per-cell constants and the FP64 iterate of one cell.
 struct Cell {
   int64_t i;
-  double rho, m0[3], eg0, chi0s, Etot, rcv, irc;
+  double rho, irho, m0[3], eg0, chi0s, Etot, rcv, irc;  // irho = 1/rho
   double m[3];     // momentum of the current outer iterate
   double v[3];     // its velocity (frozen during the inner solve)
   double KE;       // its kinetic energy (frozen during the inner solve)
@@ -124,6 +124,7 @@ __device__ __forceinline__ bool load_cell(const KParams &P, int64_t i, Cell &C, 
     return false;
   }
   C.chi0s = C.rho * k0;
+  C.irho = 1.0 / C.rho;
   C.Etot = C.eg0 + (P.c / P.c_hat) * (sumE0 + sumS);  // energy at the start (reading: c/c_hat)
   C.rcv = C.rho * P.c_v;
   C.irc = 1.0 / C.rcv;
@@ -161,11 +162,11 @@ __device__ __forceinline__ void set_tau(const KParams &P, const GroupTable &tab,
 // a3: the terms frozen for one outer pass.
 template <int MAXG>
 __device__ __forceinline__ void outer_begin(const KParams &P, Cell &C, Arr64<MAXG> &A) {
-  const double rho = C.rho, inv_c2 = 1.0 / (P.c * P.c);
-  C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) / rho;
-  C.v[0] = C.m[0] / rho;
-  C.v[1] = C.m[1] / rho;
-  C.v[2] = C.m[2] / rho;
+  const double ir = C.irho, inv_c2 = 1.0 / (P.c * P.c);
+  C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) * ir;
+  C.v[0] = C.m[0] * ir;
+  C.v[1] = C.m[1] * ir;
+  C.v[2] = C.m[2] * ir;
   for (int g = 0; g < P.G; ++g)
     A.w[g] = (C.v[0] * A.Fk[3 * g] + C.v[1] * A.Fk[3 * g + 1] + C.v[2] * A.Fk[3 * g + 2]) * inv_c2;
   C.it = 0;
@@ -344,7 +345,6 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
   const double tdt = chat * P.theta * P.dt;
   const double inv_c2 = 1.0 / (c * c);
   const double icc = 1.0 / (c * chat);
-  const double rho = C.rho;
   const bool gtest = (P.flags & RHD_GROUP_TEST) != 0;
 
   // ---- a9: conservative energy write-back
@@ -356,7 +356,8 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
   // every group, then flux_newton_pass where the closure's dependence on F
   // needs it (see flux_update)
   const double *v = C.v;
-  const double vmag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const double v2c = 100.0 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);  // (10 |v|)^2
+  const double c2 = c * c;
   double dF[3] = {0.0, 0.0, 0.0};
   double fchg = 0.0;  // sum_g |F_g,new - F_g,old|_1 (RHD_FLUX_TEST)
   bool newton = false;
@@ -371,7 +372,7 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
     const double srcg = chiE * (A.bq[g] - A.dnx[g] * (1.0 / 3.0));
     const double inv = 1.0 / (1.0 + tdt * chiE * A.qF[g]);
     const double kap = tdt * (1.0 + a) * chiE * inv;
-    newton = newton || 10.0 * fabs(kap) * vmag > c;
+    newton = newton || kap * kap * v2c > c2;  // 10 |kap| |v| > c
     const double ft0 = P.frad[0][o], ft1 = P.frad[1][o], ft2 = P.frad[2][o];
     const double n0 = (ft0 + tdt * v[0] * srcg) * inv + kap * vp0;
     const double n1 = (ft1 + tdt * v[1] * srcg) * inv + kap * vp1;
@@ -399,8 +400,9 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
   // effect on R_g after the implicit energy solve (divided by
   // 1 + c_hat theta dt chi_E), plus the change of the kinetic energy, which
   // moves T = (E_gas - E_kin)/(rho c_v) and with it every term of R_g
-  const double vn[3] = {mn[0] / rho, mn[1] / rho, mn[2] / rho};
-  const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho;
+  const double ir = C.irho;
+  const double vn[3] = {mn[0] * ir, mn[1] * ir, mn[2] * ir};
+  const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) * ir;
   double chg = fabs(KEn - C.KE) + ((P.flags & RHD_FLUX_TEST) ? fchg / c : 0.0);
   bool gok = true;
   for (int g = 0; g < G; ++g) {

@@ -20,7 +20,7 @@ namespace rhd {
 template <int L, int GPL>
 struct WCell {
   int64_t i;
-  double rho, m0[3], eg0, chi0s, Etot, rcv, irc;
+  double rho, irho, m0[3], eg0, chi0s, Etot, rcv, irc;
   double m[3], v[3], KE, Eint, egas_new, cs, its, chg_prev;
   int nit, stat, it, outer, slow;
   int fresh, cached;  // as Cell::fresh, Cell::cached
@@ -83,6 +83,7 @@ __device__ __forceinline__ bool wload(const KParams &P, int64_t i, int l, unsign
   }
   sumE0 = seg_sum<L>(sumE0, mask);
   C.chi0s = C.rho * k0;
+  C.irho = 1.0 / C.rho;
   C.Etot = C.eg0 + (P.c / P.c_hat) * sumE0;
   C.rcv = C.rho * P.c_v;
   C.irc = 1.0 / C.rcv;
@@ -143,11 +144,11 @@ __device__ __forceinline__ void wapply_warm(const KParams &P, const WarmStart &W
 
 template <int L, int GPL>
 __device__ __forceinline__ void wouter_begin(const KParams &P, WCell<L, GPL> &C) {
-  const double rho = C.rho, inv_c2 = 1.0 / (P.c * P.c);
-  C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) / rho;
-  C.v[0] = C.m[0] / rho;
-  C.v[1] = C.m[1] / rho;
-  C.v[2] = C.m[2] / rho;
+  const double ir = C.irho, inv_c2 = 1.0 / (P.c * P.c);
+  C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) * ir;
+  C.v[0] = C.m[0] * ir;
+  C.v[1] = C.m[1] * ir;
+  C.v[2] = C.m[2] * ir;
 #pragma unroll
   for (int j = 0; j < GPL; ++j)
     C.w[j] = (C.v[0] * C.Fk[j][0] + C.v[1] * C.Fk[j][1] + C.v[2] * C.Fk[j][2]) * inv_c2;
@@ -306,7 +307,6 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
   const double tdt = chat * P.theta * P.dt;
   const double inv_c2 = 1.0 / (c * c);
   const double icc = 1.0 / (c * chat);
-  const double rho = C.rho;
   const bool gtest = (P.flags & RHD_GROUP_TEST) != 0;
 
   double sumR = 0.0;
@@ -317,7 +317,8 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
   C.egas_new = C.eg0 - cr * sumR;
 
   const double *v = C.v;
-  const double vmag = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+  const double v2c = 100.0 * (v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);  // (10 |v|)^2
+  const double c2 = c * c;
   double dF[3] = {0.0, 0.0, 0.0};
   double fchg = 0.0;
   bool newton = false;
@@ -335,7 +336,7 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
     const double srcg = chiB * (C.bq[j] - C.dnx[j] * (1.0 / 3.0));
     const double inv = 1.0 / (1.0 + tdt * chiB * C.qF[j]);
     const double kap = tdt * (1.0 + a) * chiB * inv;
-    newton = newton || 10.0 * fabs(kap) * vmag > c;
+    newton = newton || kap * kap * v2c > c2;  // 10 |kap| |v| > c
     const double n0 = (ft[0] + tdt * v[0] * srcg) * inv + kap * vp0;
     const double n1 = (ft[1] + tdt * v[1] * srcg) * inv + kap * vp1;
     const double n2 = (ft[2] + tdt * v[2] * srcg) * inv + kap * vp2;
@@ -356,7 +357,7 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
       const double chiB = C.cs * tab.kbar[g];
       const double inv = 1.0 / (1.0 + tdt * chiB * C.qF[j]);
       const double kap = tdt * (1.0 + tab.alpha[g]) * chiB * inv;
-      if (!(10.0 * fabs(kap) * vmag > c)) continue;
+      if (!(kap * kap * v2c > c2)) continue;
       const double srcg = chiB * (C.bq[j] - C.dnx[j] * (1.0 / 3.0));
       const int64_t o = (int64_t)g * P.gs + C.i;
       const Vec3<double> F = flux_newton<double>(
@@ -376,8 +377,9 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
   dF[1] = seg_sum<L>(dF[1], mask);
   dF[2] = seg_sum<L>(dF[2], mask);
   const double mn[3] = {C.m0[0] - dF[0] * icc, C.m0[1] - dF[1] * icc, C.m0[2] - dF[2] * icc};
-  const double vn[3] = {mn[0] / rho, mn[1] / rho, mn[2] / rho};
-  const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho;
+  const double ir = C.irho;
+  const double vn[3] = {mn[0] * ir, mn[1] * ir, mn[2] * ir};
+  const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) * ir;
   double cg_sum = 0.0;
   bool gok = true;
 #pragma unroll
