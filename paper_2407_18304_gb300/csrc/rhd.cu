@@ -234,6 +234,9 @@ int pack(const rhd_state_t *s, const rhd_groups_t *gr, const rhd_opacity_law_t *
   kp->dt = dt;
   kp->c = s->c;
   kp->c_hat = s->c_hat;
+  kp->cr = s->c / s->c_hat;
+  kp->inv_c2 = 1.0 / (s->c * s->c);
+  kp->icc = 1.0 / (s->c * s->c_hat);
   kp->a_rad = s->a_rad;
   kp->h_over_k = s->h / s->k_B;
   kp->tol = s->tol > 0.0 ? s->tol : 1e-11;

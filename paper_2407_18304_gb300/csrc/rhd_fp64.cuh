@@ -162,7 +162,7 @@ __device__ __forceinline__ void set_tau(const KParams &P, const GroupTable &tab,
 // a3: the terms frozen for one outer pass.
 template <int MAXG>
 __device__ __forceinline__ void outer_begin(const KParams &P, Cell &C, Arr64<MAXG> &A) {
-  const double ir = C.irho, inv_c2 = 1.0 / (P.c * P.c);
+  const double ir = C.irho, inv_c2 = P.inv_c2;
   C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) * ir;
   C.v[0] = C.m[0] * ir;
   C.v[1] = C.m[1] * ir;
@@ -180,7 +180,7 @@ template <int MAXG>
 __device__ __forceinline__ int inner_tail(const KParams &P, Cell &C, Arr64<MAXG> &A, double sumR,
                                           double sFRe, double sde, double sabs) {
   const int G = P.G;
-  const double cr = P.c / P.c_hat;
+  const double cr = P.cr;
   const double FG = C.Eint + C.KE - C.eg0 + cr * sumR;
   // a8: convergence test
   if (fabs(FG) < P.tol * C.Etot && cr * sabs < P.tol * C.Etot) {
@@ -341,10 +341,10 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
   const double *kq = kE ? kE : tab.kbar;
   const int G = P.G;
   const int64_t i = C.i;
-  const double c = P.c, chat = P.c_hat, cr = c / chat;
+  const double c = P.c, chat = P.c_hat, cr = P.cr;
   const double tdt = chat * P.theta * P.dt;
-  const double inv_c2 = 1.0 / (c * c);
-  const double icc = 1.0 / (c * chat);
+  const double inv_c2 = P.inv_c2;
+  const double icc = P.icc;
   const bool gtest = (P.flags & RHD_GROUP_TEST) != 0;
 
   // ---- a9: conservative energy write-back

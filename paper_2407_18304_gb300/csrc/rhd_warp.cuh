@@ -144,7 +144,7 @@ __device__ __forceinline__ void wapply_warm(const KParams &P, const WarmStart &W
 
 template <int L, int GPL>
 __device__ __forceinline__ void wouter_begin(const KParams &P, WCell<L, GPL> &C) {
-  const double ir = C.irho, inv_c2 = 1.0 / (P.c * P.c);
+  const double ir = C.irho, inv_c2 = P.inv_c2;
   C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) * ir;
   C.v[0] = C.m[0] * ir;
   C.v[1] = C.m[1] * ir;
@@ -160,7 +160,7 @@ __device__ __forceinline__ void wouter_begin(const KParams &P, WCell<L, GPL> &C)
 template <int L, int GPL>
 __device__ __forceinline__ int wtail(const KParams &P, unsigned mask, WCell<L, GPL> &C,
                                      double sumR, double sFRe, double sde, double sabs) {
-  const double cr = P.c / P.c_hat;
+  const double cr = P.cr;
   sumR = seg_sum<L>(sumR, mask);
   sFRe = seg_sum<L>(sFRe, mask);
   sde = seg_sum<L>(sde, mask);
@@ -303,10 +303,10 @@ template <int L, int GPL>
 __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &tab, int l,
                                            unsigned mask, WCell<L, GPL> &C) {
   const int G = P.G;
-  const double c = P.c, chat = P.c_hat, cr = c / chat;
+  const double c = P.c, chat = P.c_hat, cr = P.cr;
   const double tdt = chat * P.theta * P.dt;
-  const double inv_c2 = 1.0 / (c * c);
-  const double icc = 1.0 / (c * chat);
+  const double inv_c2 = P.inv_c2;
+  const double icc = P.icc;
   const bool gtest = (P.flags & RHD_GROUP_TEST) != 0;
 
   double sumR = 0.0;

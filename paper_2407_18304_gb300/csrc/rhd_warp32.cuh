@@ -23,7 +23,7 @@ constexpr int kPlanckF = (kDeg32 + 3) * planck_table::kSeg;  // coef [8][kSeg], 
 template <int L, int GPL>
 struct WCell32 {
   int64_t i;
-  double rho, m0[3], eg0, chi0s, Etot, irc, sE;
+  double rho, irho, irhoc, m0[3], eg0, chi0s, Etot, irc, sE;  // irho = 1/rho, irhoc = 1/(rho c)
   double m[3], KE, Eint;  // Eint: the FP64 base of the current pass
   double chg_prev;
   int nit, it, outer, slow;
@@ -137,8 +137,10 @@ __device__ __forceinline__ bool w32_load(const KParams &P, const GroupTable &tab
   if (!__all_sync(mask, valid)) return false;
   sumE0 = seg_sum<L>(sumE0, mask);
   C.chi0s = C.rho * k0;
-  C.Etot = C.eg0 + (P.c / P.c_hat) * sumE0;
-  C.irc = 1.0 / (C.rho * P.c_v);
+  C.Etot = C.eg0 + P.cr * sumE0;
+  C.irho = 1.0 / C.rho;
+  C.irhoc = C.irho / P.c;
+  C.irc = C.irho / P.c_v;
   C.sE = 1.0 / C.Etot;
   C.m[0] = C.m0[0];
   C.m[1] = C.m0[1];
@@ -169,9 +171,8 @@ __device__ __forceinline__ bool w32_load(const KParams &P, const GroupTable &tab
 // a3 for a pass, and the FP64 base of the internal energy.
 template <int L, int GPL>
 __device__ __forceinline__ void w32_outer_begin(const KParams &P, WCell32<L, GPL> &C) {
-  const double rho = C.rho, c = P.c;
-  C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) / rho;
-  for (int d = 0; d < 3; ++d) C.be[d] = (float)(C.m[d] / (rho * c));
+  C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) * C.irho;
+  for (int d = 0; d < 3; ++d) C.be[d] = (float)(C.m[d] * C.irhoc);
 #pragma unroll
   for (int j = 0; j < GPL; ++j)
     C.w[j] = C.be[0] * C.f[j][0] + C.be[1] * C.f[j][1] + C.be[2] * C.f[j][2];
@@ -191,7 +192,7 @@ __device__ __forceinline__ int w32_inner_step(const KParams &P, const GroupTable
                                               WCell32<L, GPL> &C) {
   constexpr int NE = GPL + 1;
   const int G = P.G;
-  const float cr = (float)(P.c / P.c_hat);
+  const float cr = (float)P.cr;
   const float tol32 = 2e-6f;
   const int max_it = P.max_newton < 32 ? P.max_newton : 32;
   const float eint = C.eb + C.dlt;          // E_int / E_tot
@@ -282,8 +283,8 @@ template <int L, int GPL>
 __device__ __forceinline__ bool w32_outer_end(const KParams &P, const GroupTable &tab, int l,
                                               unsigned mask, WCell32<L, GPL> &C) {
   const int G = P.G;
-  const double c = P.c, chat = P.c_hat, rho = C.rho, Etot = C.Etot;
-  const float cr = (float)(c / chat);
+  const double Etot = C.Etot;
+  const float cr = (float)P.cr;
   float sR = 0.0f;
 #pragma unroll
   for (int j = 0; j < GPL; ++j)
@@ -312,11 +313,11 @@ __device__ __forceinline__ bool w32_outer_end(const KParams &P, const GroupTable
     }
   }
   for (int d = 0; d < 3; ++d) df[d] = seg_sumf<L>(df[d], mask);
-  const double mf = Etot / chat;
+  const double mf = Etot * P.icc * P.c;  // E_tot / c_hat
   const double mn[3] = {C.m0[0] - mf * df[0], C.m0[1] - mf * df[1], C.m0[2] - mf * df[2]};
-  const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho;
-  const float bn[3] = {(float)(mn[0] / (rho * c)), (float)(mn[1] / (rho * c)),
-                       (float)(mn[2] / (rho * c))};
+  const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) * C.irho;
+  const float bn[3] = {(float)(mn[0] * C.irhoc), (float)(mn[1] * C.irhoc),
+                       (float)(mn[2] * C.irhoc)};
   float cg = 0.0f;
 #pragma unroll
   for (int j = 0; j < GPL; ++j) {
