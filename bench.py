@@ -159,27 +159,33 @@ def fp_peaks() -> dict:
         return {"error": str(e)}
 
 
-# Algorithmic FP64 flops (DFMA counted twice) per cell-group, from the SASS
-# instruction counts ncu reports on a 65536-cell sample of the same workload
-# with one cell per thread (RHD_CELL_PER_THREAD: every instruction is one
-# cell's own work; the default warp-per-cell mapping executes about 50 % more
-# FP64 instructions, replicated per-cell work); profiles/solve_full_256cube_ng64.md.
-# The FP64-pass kernel (the one that dominates a call, timed live below):
-FP64_PASS_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1635.9,
-                          ("full_256cube_ng64", "mixed"): 1641.3,
-                          ("full_256cube_ng64", "fp64"): 2926.0,
-                          ("full_256cube_ng64", "fp64+surrogate"): 2740.3}
-# ... and the whole call (inference, FP32 passes, FP64 passes)
-CALL_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1669.2,
-                     ("full_256cube_ng64", "mixed"): 1659.8,
-                     ("full_256cube_ng64", "fp64"): 2926.0,
-                     ("full_256cube_ng64", "fp64+surrogate"): 2755.9}
+# Algorithmic FP64 work per cell-group, from the SASS instruction counts ncu
+# reports on a 65536-cell sample of the same workload with one cell per thread
+# (RHD_CELL_PER_THREAD: every instruction is one cell's own work; the default
+# warp-per-cell mapping executes about 30 % more, the per-cell scalar work that
+# every lane of the cell repeats).
+# FP64 arithmetic instructions (DFMA, DADD, DMUL: one issue each) of the
+# FP64-pass kernel (the one that dominates a call, timed live below):
+FP64_PASS_INST_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 729.4,
+                         ("full_256cube_ng64", "mixed"): 732.3,
+                         ("full_256cube_ng64", "fp64"): 1314.0,
+                         ("full_256cube_ng64", "fp64+surrogate"): 1206.4}
+# ... the same as flops (DFMA counted twice)
+FP64_PASS_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1104.2,
+                          ("full_256cube_ng64", "mixed"): 1108.8,
+                          ("full_256cube_ng64", "fp64"): 2009.3,
+                          ("full_256cube_ng64", "fp64+surrogate"): 1836.9}
+# ... and the flops of the whole call (inference, FP32 passes, FP64 passes)
+CALL_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1133.7,
+                     ("full_256cube_ng64", "mixed"): 1123.2,
+                     ("full_256cube_ng64", "fp64"): 2009.3,
+                     ("full_256cube_ng64", "fp64+surrogate"): 1852.5}
 # DRAM bytes (read + write) per cell-group of one launch of the FP64-pass
 # kernel in the default mapping, from the same capture
-FP64_PASS_TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 69.1,
-                            ("full_256cube_ng64", "mixed"): 69.4,
-                            ("full_256cube_ng64", "fp64"): 52.0,
-                            ("full_256cube_ng64", "fp64+surrogate"): 69.2}
+FP64_PASS_TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 69.4,
+                            ("full_256cube_ng64", "mixed"): 69.3,
+                            ("full_256cube_ng64", "fp64"): 52.1,
+                            ("full_256cube_ng64", "fp64+surrogate"): 69.0}
 
 
 def train_surrogate(args, w, dev, rank):
@@ -297,7 +303,7 @@ def run_ours(args, ws, rank):
            "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if prec == rhd.FP64 else ("f32+f64+bf16" if use_sur else "f32+f64"),
-           "data": "synthetic (seeded; recipe in DESIGN.md)",
+           "data": "synthetic (seeded generators of paper_2407_18304_gb300.synth)",
            "config": {"workload": name, "cells": n, "n_groups": G, "form": form,
                       "mapping": "cell per thread" if args.cell_per_thread else "warp per cell",
                       "precision": args.precision, "tol": 1e-11, "tol_outer": 1e-13,
@@ -316,31 +322,42 @@ def run_ours(args, ws, rank):
             res["mixed_form"] = side(rhd.MIXED, False, args.fp64_steps)
             res["fp64_surrogate_form"] = side(rhd.FP64, True, args.fp64_steps)
 
-    # roofline of the dominant kernel (the FP64 passes; FP64-issue bound, see
-    # the design doc section 7), its duration measured live with CUDA events
+    # roofline of the dominant kernel (the FP64 passes), its duration measured
+    # live with CUDA events.  The kernel is bound by the issue rate of the FP64
+    # pipe: GB300 issues two FP64 lanes per SM per clock,
+    # and a DADD or DMUL takes an issue slot as a DFMA does, so the roofline is
+    # algorithmic FP64 instructions per second against the measured DFMA
+    # instruction rate; the flop form (DFMA = 2 flops, against the DFMA flop
+    # peak) is reported beside it.
     peaks = fp_peaks()
     res["fp_peaks_measured"] = peaks
     mean_call_s = t_dev / args.steps
-    bytes_alg = n * (G * 64 + 82)  # in+out FP64 SoA per call
+    bytes_alg = n * (G * 64 + 82)  # in+out FP64 SoA per call: E_g, F_g and the per-cell fields
     hbm_frac = bytes_alg / mean_call_s / 1e9 / _measured_hbm()
     key = (name, form)
-    per_cg = FP64_PASS_FLOPS_PER_CG.get(key)
-    if per_cg is not None and kernel_ms[1] > 0:
-        peak = peaks.get("fp64_fma_tflops") or 1.25
+    per_inst = FP64_PASS_INST_PER_CG.get(key)
+    if per_inst is not None and kernel_ms[1] > 0:
+        peak_tf = peaks.get("fp64_fma_tflops") or 1.25
         k_s = kernel_ms[0] / 1e3
-        ach = per_cg * n * G / k_s / 1e12
+        ach_i = per_inst * n * G / k_s / 1e9
+        peak_i = peak_tf * 1e3 / 2.0
+        ach_f = FP64_PASS_FLOPS_PER_CG[key] * n * G / k_s / 1e12
         tr = FP64_PASS_TRAFFIC_PER_CG.get(key)
         res["roofline"] = {
-            "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s", "frac": ach / peak,
+            "bound": "alu", "achieved": ach_i, "peak": peak_i, "unit": "G FP64 inst/s",
+            "frac": ach_i / peak_i,
             "traffic": tr * n * G if tr is not None else None,
             "kernel": "FP64 passes (solve_warp_kernel<32,2>)",
             "kernel_ms": kernel_ms[0], "kernel_launches_timed": kernel_ms[1],
-            "what": "algorithmic FP64 flops (DFMA = 2) of the kernel per launch / its CUDA-event "
-                    "duration, vs the DFMA peak",
-            "peak_source": ("measured fp_peak DFMA loop (nominal 152 SMs x 4 flop/clk x 2.07 GHz "
-                            "= 1.26 TFLOP/s)" if "fp64_fma_tflops" in peaks
-                            else "nominal 1.25 TFLOP/s"),
-            "fp64_flops_per_cell_group": per_cg,
+            "what": "algorithmic FP64 arithmetic instructions (DFMA, DADD, DMUL) of the kernel "
+                    "per launch / its CUDA-event duration, vs the measured DFMA instruction rate",
+            "peak_source": ("measured fp_peak DFMA loop / 2 flops per DFMA (nominal 152 SMs x "
+                            "2 FP64 lanes/clk x 2.07 GHz = 629 G inst/s)" if "fp64_fma_tflops" in peaks
+                            else "nominal 1.25 TFLOP/s / 2"),
+            "fp64_inst_per_cell_group": per_inst,
+            "flops": {"achieved": ach_f, "peak": peak_tf, "unit": "TFLOP/s",
+                      "frac": ach_f / peak_tf,
+                      "fp64_flops_per_cell_group": FP64_PASS_FLOPS_PER_CG[key]},
             "call_fp64_tflops": CALL_FLOPS_PER_CG.get(key, 0.0) * n * G / mean_call_s / 1e12,
             "hbm_frac_of_call": hbm_frac}
     else:
@@ -423,7 +440,7 @@ def run_batched(args, ws, rank):
            "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
            "dtype": "f64" if prec == rhd.FP64 else "f32+f64",
-           "data": "synthetic (seeded; recipe in DESIGN.md)",
+           "data": "synthetic (seeded generators of paper_2407_18304_gb300.synth)",
            "config": {"workload": BATCHED, "grids": len(grids),
                       "cells": int(sum(g.n_cells for g in grids)), "cell_groups": int(units1),
                       "precision": args.precision, "tol": 1e-11, "tol_outer": 1e-13,

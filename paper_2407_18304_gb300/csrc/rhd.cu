@@ -235,6 +235,7 @@ int pack(const rhd_state_t *s, const rhd_groups_t *gr, const rhd_opacity_law_t *
   kp->c = s->c;
   kp->c_hat = s->c_hat;
   kp->cr = s->c / s->c_hat;
+  kp->ic = 1.0 / s->c;
   kp->inv_c2 = 1.0 / (s->c * s->c);
   kp->icc = 1.0 / (s->c * s->c_hat);
   kp->a_rad = s->a_rad;

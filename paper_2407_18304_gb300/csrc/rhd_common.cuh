@@ -39,7 +39,7 @@ struct KParams {
   int64_t n;   // cells
   int64_t gs;  // group stride
   double c_v, theta, dt, c, c_hat, a_rad, h_over_k;
-  double cr, inv_c2, icc;  // c / c_hat, 1 / c^2, 1 / (c c_hat) (set with c and c_hat)
+  double cr, ic, inv_c2, icc;  // c / c_hat, 1 / c, 1 / c^2, 1 / (c c_hat) (set with c, c_hat)
   double tol, tol_outer;
   int max_newton, max_outer, closure, flags;
   int G, mode, n_seg, has_table;

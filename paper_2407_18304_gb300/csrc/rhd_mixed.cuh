@@ -136,7 +136,8 @@ __device__ __forceinline__ bool load_cell32(const KParams &P, const GroupTable &
   }
   if (!valid) return false;  // the FP64 launch writes the status
   C.chi0s = C.rho * k0;
-  C.Etot = C.eg0 + (P.c / P.c_hat) * sumE0;
+  C.irho = 1.0 / C.rho;
+  C.Etot = C.eg0 + P.cr * sumE0;
   C.rcv = C.rho * P.c_v;
   C.irc = 1.0 / C.rcv;
   C.m[0] = C.m0[0];
@@ -166,9 +167,9 @@ __device__ __forceinline__ bool load_cell32(const KParams &P, const GroupTable &
 template <int MAXG>
 __device__ __forceinline__ void outer_begin32(const KParams &P, Cell &C, Cell32 &D,
                                               Arr32<MAXG> &B) {
-  const double rho = C.rho, c = P.c;
-  C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) / rho;
-  for (int d = 0; d < 3; ++d) D.be[d] = (float)(C.m[d] / (rho * c));
+  const double irc_ = C.irho * P.ic;  // 1/(rho c)
+  C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) * C.irho;
+  for (int d = 0; d < 3; ++d) D.be[d] = (float)(C.m[d] * irc_);
   for (int g = 0; g < P.G; ++g)
     B.w[g] = D.be[0] * B.f[3 * g] + D.be[1] * B.f[3 * g + 1] + D.be[2] * B.f[3 * g + 2];
   C.it = 0;
@@ -180,7 +181,7 @@ template <int MAXG>
 __device__ __forceinline__ int inner_step32(const KParams &P, const GroupTable &tab, Cell &C,
                                             Cell32 &D, Arr32<MAXG> &B) {
   const int G = P.G;
-  const float cr = (float)(P.c / P.c_hat);
+  const float cr = (float)P.cr;
   const double Etot = C.Etot, sE = D.sE;
   const float tol32 = 2e-6f;
   const int max_it = P.max_newton < 32 ? P.max_newton : 32;
@@ -254,8 +255,8 @@ template <int MAXG>
 __device__ __forceinline__ bool outer_end32(const KParams &P, const GroupTable &tab, Cell &C,
                                             Cell32 &D, Arr32<MAXG> &B) {
   const int G = P.G;
-  const double c = P.c, chat = P.c_hat, rho = C.rho, Etot = C.Etot;
-  const float cr = (float)(c / chat);
+  const double Etot = C.Etot, irc_ = C.irho * P.ic;
+  const float cr = (float)P.cr;
   float sR = 0.0f;
   for (int g = 0; g < G; ++g) sR += B.R[g];
   const double egas_new = C.eg0 - (double)cr * (double)sR * Etot;
@@ -279,11 +280,10 @@ __device__ __forceinline__ bool outer_end32(const KParams &P, const GroupTable &
     B.f[3 * g + 1] = F[1];
     B.f[3 * g + 2] = F[2];
   }
-  const double mf = Etot / chat;  // (c E_tot)/(c c_hat)
+  const double mf = Etot * P.icc * P.c;  // E_tot / c_hat = (c E_tot)/(c c_hat)
   const double mn[3] = {C.m0[0] - mf * df[0], C.m0[1] - mf * df[1], C.m0[2] - mf * df[2]};
-  const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / rho;
-  const float bn[3] = {(float)(mn[0] / (rho * c)), (float)(mn[1] / (rho * c)),
-                       (float)(mn[2] / (rho * c))};
+  const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) * C.irho;
+  const float bn[3] = {(float)(mn[0] * irc_), (float)(mn[1] * irc_), (float)(mn[2] * irc_)};
   float chg = (float)(fabs(KEn - C.KE) * D.sE);
   for (int g = 0; g < G; ++g) {
     const float wn = bn[0] * B.f[3 * g] + bn[1] * B.f[3 * g + 1] + bn[2] * B.f[3 * g + 2];
