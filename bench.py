@@ -294,8 +294,7 @@ def run_ours(args, ws, rank):
     t_max = allmax(t_dev, ws)
     units = float(n) * G * args.steps
     total_units = allsum(units, ws)
-    chunks = -(-n // rhd.SURROGATE_CHUNK)
-    launches = (1 if prec == rhd.FP64 else 2) + (6 * chunks if use_sur else 0)
+    launches = (1 if prec == rhd.FP64 else 2) + (1 if use_sur else 0)
     form = ("mixed" if prec == rhd.MIXED else "fp64") + ("+surrogate" if use_sur else "")
 
     res = {"metric": METRIC, "value": total_units / t_max, "unit": UNIT, "n_gpus": ws,

@@ -287,10 +287,19 @@ int rhd_surrogate_error(rhd_surrogate_t *s, int32_t *flag);
 /* rhd_source_update (FP64 or mixed form, from state->precision) started from the
  * surrogate's guess; groups->n_groups must equal the surrogate's.  Same results to
  * the caller's tolerance; status RHD_STATUS_FALLBACK marks cells that needed the
- * cold start.  Uses the library's per-device workspace like the mixed form. */
+ * cold start.  Uses the library's per-device workspace like the mixed form.  The
+ * guess comes from one persistent tensor-core kernel (features, the four layers
+ * with the activations kept on chip, the Newton start) over all n_cells. */
 int rhd_source_update_warm(rhd_surrogate_t *s, rhd_state_t *state, const rhd_groups_t *groups,
                            const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
                            void *stream);
+/* The Newton start rhd_source_update_warm takes, without solving: eint [n_cells]
+ * (DEVICE, FP64) gets the guess of the internal energy (-1 where the cell is
+ * invalid or the guess is not finite: cold start), r [n_groups][n_cells]
+ * (DEVICE, FP32, cell fastest) the guess of R_g / E_tot.  The state is read only. */
+int rhd_surrogate_warm_start(rhd_surrogate_t *s, const rhd_state_t *state,
+                             const rhd_groups_t *groups, const rhd_opacity_law_t *opacity_law,
+                             double dt, int64_t n_cells, double *eint, float *r, void *stream);
 
 /* ---- Benchmark support -------------------------------------------------------
  * Time the FP64-pass kernel of every rhd_source_update / rhd_source_update_warm

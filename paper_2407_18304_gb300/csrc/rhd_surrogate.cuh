@@ -39,17 +39,69 @@ __device__ __forceinline__ bool cell_T(const KParams &P, int64_t i, double &T) {
   return rho > 0.0 && isfinite(T) && T > 0.0;
 }
 
-// 2^-e as a double (|e| < 1000; exact).
-__device__ __forceinline__ double pow2_neg(int e) {
-  return __hiloint2double((1023 - e) << 20, 0);
+// Decomposition of a positive normal double without FP64 instructions (on
+// GB300 an FP64 instruction, conversions included, costs 64 FP32 ones): from
+// the bit pattern, x = m 2^ex with m in [0.5, 1) (as frexp), m cut to FP32.
+__device__ __forceinline__ float frexp_f(double x, int &ex) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  ex = ((hi >> 20) & 0x7FF) - 1022;
+  const unsigned frac = ((unsigned)(hi & 0xFFFFF) << 3) | ((unsigned)lo >> 29);
+  return __int_as_float((int)((126u << 23) | frac));
 }
 
-// Natural log of a positive finite double to FP32 accuracy without FP64
-// transcendentals: ln(m 2^e) = e ln 2 + ln m, with m in [0.5, 1).
+// x 2^-sh as FP32 from the bit pattern (mantissa cut, not rounded; 0 below
+// FP32's normal range, +-inf above it).
+__device__ __forceinline__ float scaled_f(double x, int sh) {
+  const int hi = __double2hiint(x), lo = __double2loint(x);
+  const int E = (hi >> 20) & 0x7FF;
+  const unsigned sign = (unsigned)hi & 0x80000000u;
+  if (E == 0) return __int_as_float((int)sign);
+  const int fe = E - 1023 - sh + 127;
+  if (fe <= 0) return __int_as_float((int)sign);
+  if (fe >= 255) return __int_as_float((int)(sign | 0x7F800000u));
+  const unsigned frac = ((unsigned)(hi & 0xFFFFF) << 3) | ((unsigned)lo >> 29);
+  return __int_as_float((int)(sign | ((unsigned)fe << 23) | frac));
+}
+
+// A group energy that carries a feature: positive, finite, not below about
+// 1.3e-290 (exponent field >= 60), tested on the bits.
+__device__ __forceinline__ bool usable_energy(double x) {
+  const int hi = __double2hiint(x);
+  return hi >= 0 && ((hi >> 20) & 0x7FF) >= 60 && ((hi >> 20) & 0x7FF) < 0x7FF;
+}
+
+// Natural log of a positive normal double to FP32 accuracy without FP64
+// instructions: ln(m 2^e) = e ln 2 + ln m, with m in [0.5, 1).
 __device__ __forceinline__ float ln_f(double x) {
   int e;
-  const double m = frexp(x, &e);
-  return (float)e * 0.69314718055994531f + __logf((float)m);
+  const float m = frexp_f(x, e);
+  return (float)e * 0.69314718055994531f + __logf(m);
+}
+
+// The per-group features of a usable group energy e with flux (fx, fy, fz):
+// ln(E_g / a_R T^4) held to [-700, 50] and |F_g| / (c E_g) held to 2, in FP32
+// after the exact power-of-two scaling of E_g's exponent.
+__device__ __forceinline__ void group_features(double e, double fx, double fy, double fz,
+                                               float lnaT4, float c, float &fe, float &ff) {
+  int ex;
+  const float m = frexp_f(e, ex);
+  const float ax = scaled_f(fx, ex), ay = scaled_f(fy, ex), az = scaled_f(fz, ex);
+  fe = fminf(fmaxf((float)ex * 0.69314718055994531f + __logf(m) - lnaT4, -700.0f), 50.0f);
+  ff = fminf(sqrtf(ax * ax + ay * ay + az * az) / (c * m), 2.0f);
+}
+
+// |v| / c and ln(c rho kappa0 dt) of a cell, in FP32 (rho v scaled by rho's exponent).
+__device__ __forceinline__ void cell_scalar_features(const KParams &P, int64_t i, float &fv,
+                                                     float &ft) {
+  const double rho = P.rho[i];
+  int er;
+  const float mr = frexp_f(rho, er);
+  const float a = scaled_f(P.mom[0][i], er), b = scaled_f(P.mom[1][i], er),
+              c = scaled_f(P.mom[2][i], er);
+  fv = sqrtf(a * a + b * b + c * c) / (mr * (float)P.c);
+  const double k0 = P.kappa0 ? P.kappa0[i] : 1.0;
+  const double tau = P.c * rho * k0 * P.dt;
+  ft = usable_energy(tau) ? ln_f(tau) : -690.8f;  // ln 1e-300
 }
 
 // Raw features of one cell into f[0 .. 2G+4); false for an invalid cell.
@@ -70,24 +122,15 @@ __device__ __forceinline__ bool cell_features(const KParams &P, int64_t i, float
   for (int g = 0; g < G; ++g) {
     const int64_t o = (int64_t)g * P.gs + i;
     const double e = P.erad[o];
-    if (!(e > 1e-290) || isinf(e)) {  // empty (or denormal) group
+    if (!usable_energy(e)) {  // empty (or denormal) group
       f[2 + g] = -700.0f;
       f[2 + G + g] = 0.0f;
       continue;
     }
-    int ex;
-    frexp(e, &ex);
-    const double sc = pow2_neg(ex);  // e * sc in [0.5, 1)
-    const float es = (float)(e * sc);
-    const float fx = (float)(P.frad[0][o] * sc), fy = (float)(P.frad[1][o] * sc),
-                fz = (float)(P.frad[2][o] * sc);
-    f[2 + g] = fminf(fmaxf(ln_f(e) - lnaT4, -700.0f), 50.0f);
-    f[2 + G + g] = fminf(sqrtf(fx * fx + fy * fy + fz * fz) / ((float)P.c * es), 2.0f);
+    group_features(e, P.frad[0][o], P.frad[1][o], P.frad[2][o], lnaT4, (float)P.c, f[2 + g],
+                   f[2 + G + g]);
   }
-  const double m0 = P.mom[0][i], m1 = P.mom[1][i], m2 = P.mom[2][i];
-  f[2 + 2 * G] = (float)(sqrt(m0 * m0 + m1 * m1 + m2 * m2) / (rho * P.c));
-  const double k0 = P.kappa0 ? P.kappa0[i] : 1.0;
-  f[3 + 2 * G] = (float)log(fmax(P.c * rho * k0 * P.dt, 1e-300));
+  cell_scalar_features(P, i, f[2 + 2 * G], f[3 + 2 * G]);
   return true;
 }
 
@@ -276,20 +319,6 @@ __global__ void init_kernel(float *p, int64_t count, float scale, uint64_t seed,
 
 // ---- inference -----------------------------------------------------------------
 
-// Standardised BF16 features of cells [c0, c0 + m) into xb [m][ldx].
-__global__ void infer_features_kernel(const __grid_constant__ KParams P, int64_t c0, int64_t m,
-                                      const float *xm, const float *xs, __nv_bfloat16 *xb,
-                                      int64_t ldx) {
-  float f[2 * kMaxGS + 4];
-  const int kin = 2 * P.G + 4;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    cell_features(P, c0 + j, f);
-    for (int k = 0; k < ldx; ++k)
-      xb[j * ldx + k] = __float2bfloat16(k < kin ? (f[k] - xm[k]) / xs[k] : 0.0f);
-  }
-}
-
 // Standardised BF16 rows [m][ldx] from raw FP32 features x [m][kin].
 __global__ void standardize_kernel(const float *__restrict__ x, int64_t m, int kin,
                                    const float *xm, const float *xs, __nv_bfloat16 *xb,
@@ -310,50 +339,10 @@ __global__ void destandardize_kernel(float *y, int64_t m, int nout, const float 
   }
 }
 
-// The warm start of cells [c0, c0 + m) from the network output y [m][nout]
-// (standardised): E_int,0 and R_g,0 / E_tot into the solver's warm-start
-// arrays (full grid, index c0 + j); F and rho v start from the state.
-__global__ void warm_from_net_kernel(const __grid_constant__ KParams P, int64_t c0, int64_t m,
-                                     const float *__restrict__ y, int nout, const float *ym,
-                                     const float *ys, WarmOut W) {
-  const int64_t n = P.n;
-  for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < m;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = c0 + j;
-    double T;
-    const bool ok = cell_T(P, i, T);
-    double sumE = 0.0;
-    for (int g = 0; g < P.G; ++g) {
-      const int64_t o = (int64_t)g * P.gs + i;
-      sumE += P.erad[o] + (P.src ? P.src[o] : 0.0);
-    }
-    const double etot = P.egas[i] + (P.c / P.c_hat) * sumE;
-    const double yT = (double)(y[j * nout] * ys[0] + ym[0]);
-    const double eint = ok ? P.rho[i] * P.c_v * T * exp(fmin(fmax(yT, -5.0), 5.0)) : -1.0;
-    W.eint[i] = isfinite(eint) ? eint : -1.0;
-    W.mom[i] = P.mom[0][i];
-    W.mom[n + i] = P.mom[1][i];
-    W.mom[2 * n + i] = P.mom[2][i];
-    W.nit[i] = 0;
-    // the guess only seeds the Newton iteration: FP32 arithmetic on the
-    // energy-scaled group quantities (R_g / E_tot is stored in FP32 anyway)
-    const double ie = ok && etot > 0.0 ? 1.0 / etot : 0.0;
-    const double fs = ie / P.c;
-    for (int g = 0; g < P.G; ++g) {
-      const int64_t o = (int64_t)g * P.gs + i, q = (int64_t)g * n + i;
-      const double e = P.erad[o], s = P.src ? P.src[o] : 0.0;
-      const float yg = fminf(fmaxf(y[j * nout + 1 + g] * ys[1 + g] + ym[1 + g], -30.0f), 30.0f);
-      const float r = (e > 0.0 ? (float)(e * ie) * expm1f(yg) : 0.0f) - (float)(s * ie);
-      W.r[q] = isfinite(r) ? r : 0.0f;
-      W.f[q] = (float)(P.frad[0][o] * fs);
-      W.f[(int64_t)P.G * n + q] = (float)(P.frad[1][o] * fs);
-      W.f[(int64_t)2 * P.G * n + q] = (float)(P.frad[2][o] * fs);
-    }
-  }
-}
-
 }  // namespace mlp
 }  // namespace rhd
+
+#include "rhd_mlp_fused.cuh"
 
 // ---------------------------------------------------------------------------
 // Host side
@@ -579,6 +568,40 @@ int infer_rows(rhd_surrogate *s, const InferBufs &b, int64_t m, float *y, cudaSt
                            s->params + s->off_b[3], nullptr, 0, s->err),
                  st);
   return e == cudaSuccess ? RHD_OK : RHD_ECUDA;
+}
+
+// The fused inference (rhd_mlp_fused.cuh) over all cells of kp into W.
+int launch_fused(rhd_surrogate *s, const KParams &kp, const WarmOut &W, bool full, int sms,
+                 cudaStream_t st) {
+  mlp::FusedNet N;
+  for (int l = 0; l < 4; ++l) {
+    N.w[l] = s->w[l];
+    N.b[l] = s->params + s->off_b[l];
+  }
+  N.xm = xm(s);
+  N.xs = xsd(s);
+  N.ym = ym(s);
+  N.ys = ysd(s);
+  N.kin = s->kin;
+  N.nout = s->nout;
+  N.k1 = mlp::round16(s->kin);
+  N.n4 = mlp::round16(s->nout);
+  N.full = full ? 1 : 0;
+  N.err = s->err;
+  const size_t smem = mlp::fused_bytes(N.k1, N.n4);
+  static size_t attr = 0;  // per process; the attribute is per function
+  if (smem > attr) {
+    if (cudaFuncSetAttribute(mlp::infer_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return RHD_ECUDA;
+    attr = smem;
+  }
+  const int64_t tiles = (kp.n + tc::kTileM - 1) / tc::kTileM;
+  const int64_t pairs = (tiles + mlp::kFusedGroups - 1) / mlp::kFusedGroups;
+  const int blocks = (int)(pairs < sms ? pairs : sms);
+  if (blocks > 0)
+    mlp::infer_fused_kernel<<<blocks, 128 * mlp::kFusedGroups, smem, st>>>(kp, N, W);
+  return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
 }
 
 int check_surrogate(const rhd_surrogate *s) {
@@ -862,22 +885,34 @@ extern "C" int rhd_source_update_warm(rhd_surrogate_t *s, rhd_state_t *state,
   int sms = 0;
   rc = rhd::ensure_device(&sms);
   if (rc != RHD_OK) return rc;
-  rc = rhd::ensure_infer(s);
-  if (rc != RHD_OK) return rc;
   rhd::WarmOut wo;
   rhd::WarmStart wi;
   rc = rhd::workspace(kp.n, kp.G, &wo, &wi);
   if (rc != RHD_OK) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  const rhd::InferBufs b = rhd::infer_views(s);
-  for (int64_t c0 = 0; c0 < n_cells; c0 += rhd::mlp::kChunk) {
-    const int64_t m = n_cells - c0 < rhd::mlp::kChunk ? n_cells - c0 : rhd::mlp::kChunk;
-    rhd::mlp::infer_features_kernel<<<rhd::blocks_for(m, 128), 128, 0, st>>>(
-        kp, c0, m, rhd::xm(s), rhd::xsd(s), b.xb, s->kpad);
-    rc = rhd::infer_rows(s, b, m, b.y, st);
-    if (rc != RHD_OK) return rc;
-    rhd::mlp::warm_from_net_kernel<<<rhd::blocks_for(m, 128), 128, 0, st>>>(
-        kp, c0, m, b.y, s->nout, rhd::ym(s), rhd::ysd(s), wo);
-  }
+  // the FP32 passes read only E_int,0 and R_g,0; the FP64 passes started
+  // directly (FP64 form, free slopes) also take rho v, F_g and the iterations
+  const bool full = state->precision == RHD_FP64 || kp.mode == RHD_PPL_FREE;
+  rc = rhd::launch_fused(s, kp, wo, full, sms, st);
+  if (rc != RHD_OK) return rc;
   return rhd::launch_warm(kp, state->precision, wo, wi, sms, st);
+}
+
+extern "C" int rhd_surrogate_warm_start(rhd_surrogate_t *s, const rhd_state_t *state,
+                                        const rhd_groups_t *groups,
+                                        const rhd_opacity_law_t *opacity_law, double dt,
+                                        int64_t n_cells, double *eint, float *r, void *stream) {
+  int rc = rhd::check_surrogate(s);
+  if (rc != RHD_OK) return rc;
+  static thread_local rhd::KParams kp;
+  rc = rhd::pack(state, groups, opacity_law, dt, n_cells, &kp);
+  if (rc != RHD_OK) return rc;
+  if (groups->n_groups != s->G) return RHD_EINVAL;
+  if (n_cells == 0) return RHD_OK;
+  if (!eint || !r) return RHD_EINVAL;
+  int sms = 0;
+  rc = rhd::ensure_device(&sms);
+  if (rc != RHD_OK) return rc;
+  rhd::WarmOut wo{eint, nullptr, r, nullptr, nullptr};
+  return rhd::launch_fused(s, kp, wo, false, sms, (cudaStream_t)stream);
 }

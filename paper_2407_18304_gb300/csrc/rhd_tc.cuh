@@ -180,10 +180,15 @@ struct GemmArgs {
   unsigned *err;           // set to 1 on a wait timeout
 };
 
+// tanh form of GELU, 0.5 z (1 + tanh(u)) with u = k0 (z + k1 z^3), written as
+// z / (1 + e^-2u) (0.5 (1 + tanh u) is the logistic function of 2u): one fast
+// exponential and one division, relative error ~1e-6 -- far below the BF16
+// rounding the activation gets next.  e^-2u overflows to inf for z << 0, where
+// the quotient is the correct 0.
 __device__ __forceinline__ float gelu(float z) {
-  // tanh form of GELU
   const float k0 = 0.7978845608028654f, k1 = 0.044715f;
-  return 0.5f * z * (1.0f + tanhf(k0 * (z + k1 * z * z * z)));
+  const float u = k0 * (z + k1 * z * z * z);
+  return __fdividef(z, 1.0f + __expf(-2.0f * u));
 }
 
 // NT = padded N (multiple of 16, <= 256); TCOLS = TMEM columns (power of 2 >= NT, >= 32).

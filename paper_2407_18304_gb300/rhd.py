@@ -116,6 +116,9 @@ def lib() -> ctypes.CDLL:
             "rhd_surrogate_error": [_P, ctypes.POINTER(ctypes.c_int32)],
             "rhd_source_update_warm": [_P, ctypes.POINTER(State), ctypes.POINTER(Groups),
                                        ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _P],
+            "rhd_surrogate_warm_start": [_P, ctypes.POINTER(State), ctypes.POINTER(Groups),
+                                         ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _F, _F,
+                                         _P],
         }
         for name, args in sig.items():
             f = getattr(_lib, name)
@@ -454,6 +457,19 @@ class Surrogate:
                                             ctypes.byref(lw), float(dt), n, _ptr(x), self._s(stream)))
         del keep
         return x
+
+    def warm_start(self, state, edges, law, *, dt, c_v, consts, stream=None):
+        """``rhd_surrogate_warm_start``: the Newton start the warm-started
+        update takes -- (E_int,0 [n] float64, R_g,0 / E_tot [G, n] float32)."""
+        st, gr, lw, keep, n = self._grid(state, edges, law, dt, c_v, consts)
+        dev = state["rho"].device
+        eint = torch.empty(n, dtype=torch.float64, device=dev)
+        r = torch.empty((len(edges) - 1, n), dtype=torch.float32, device=dev)
+        _raise(lib().rhd_surrogate_warm_start(self._h, ctypes.byref(st), ctypes.byref(gr),
+                                              ctypes.byref(lw), float(dt), n, _ptr(eint), _ptr(r),
+                                              self._s(stream)))
+        del keep
+        return eint, r
 
     def targets(self, before, after, edges, law, *, dt, c_v, consts, stream=None) -> torch.Tensor:
         sa, gr, lw, keep, n = self._grid(before, edges, law, dt, c_v, consts)

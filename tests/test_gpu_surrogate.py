@@ -47,6 +47,38 @@ def test_forward_matches_the_reference_network(G, n):
     assert sur.error_flag() == 0
 
 
+@pytest.mark.parametrize("G,n", [(4, 1000 + 37), (16, 300), (33, 129), (64, 777)])
+def test_fused_warm_start_matches_the_network(G, n):
+    """The fused inference kernel (features, four layers on chip, Newton
+    start) against the same network through rhd_surrogate_features +
+    rhd_surrogate_predict and the warm-start formulas written out here:
+    E_int,0 = rho c_v T exp(y_T), R_g,0 / E_tot = (E_g / E_tot) expm1(y_g) - S_g / E_tot,
+    both outputs held to [-5, 5] and [-30, 30].  Ragged last tile (n not a
+    multiple of 128), a source term, and group counts whose feature and
+    output widths are not multiples of 16."""
+    sur, p, norm = _random_net(G, 70 + G)
+    w = synth.preset("mixed_128cube_ng16", n_cells=n, seed=90 + G, n_groups=G, device="cuda")
+    w.state["src"] = 0.1 * w.state["erad"].flip(0).contiguous()
+    kw = dict(dt=w.dt, c_v=w.c_v, consts=w.consts)
+    eint, r = sur.warm_start(w.state, w.edges, w.law, **kw)
+    x = sur.features(w.state, w.edges, w.law, **kw)
+    y = sur.predict(x).cpu().numpy().astype(np.float64)
+    st = synth.to_numpy(w.state)
+    ke = 0.5 * (st["mom"] ** 2).sum(0) / st["rho"]
+    T = (st["egas"] - ke) / (st["rho"] * w.c_v)
+    etot = st["egas"] + (st["erad"] + st["src"]).sum(0) * w.consts["c"] / w.consts["c_hat"]
+    eint_ref = st["rho"] * w.c_v * T * np.exp(np.clip(y[:, 0], -5, 5))
+    yg = np.clip(y[:, 1:].T, -30, 30)
+    r_ref = st["erad"] / etot * np.expm1(yg) - st["src"] / etot
+    e1 = np.max(np.abs(eint.cpu().numpy() / eint_ref - 1))
+    # R_g is formed in FP32 from two terms: measure against their size
+    scale = st["erad"] / etot * (1 + np.abs(np.expm1(yg))) + st["src"] / etot
+    e2 = np.max(np.abs(r.cpu().numpy() - r_ref) / scale)
+    print(f"G={G} fused warm start vs network: E_int {e1:.2e}, R_g {e2:.2e}")
+    assert e1 < 1e-5 and e2 < 1e-5
+    assert sur.error_flag() == 0
+
+
 @pytest.mark.parametrize("G,n", [(4, 256), (32, 1024)])
 def test_gradients_match_the_reference_network(G, n):
     sur, p, norm = _random_net(G, 5 + G)
