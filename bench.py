@@ -475,50 +475,51 @@ def _measured_hbm() -> float:
 
 def run_e2e(args, w, prec, dev, ws, sur=None):
     """The same metric through the C ABI with the state in pinned host memory:
-    H2D of the inputs, the call, D2H of the results, all inside the timing."""
+    rhd_source_update_host streams the grid through the GPU in chunks (copy
+    in, solve, copy out, the copies overlapped with the solve), so every
+    step's host->device inputs and device->host results are inside the timing.
+    The host state is restored from a pristine pinned copy between steps,
+    outside the timing."""
     from paper_2407_18304_gb300 import rhd
     n, G = w.n_cells, w.n_groups
     keys_in = ["rho", "mom", "egas", "kappa0", "erad", "frad"]
     keys_out = ["mom", "egas", "erad", "frad"]
-    host_in = {k: torch.empty(tuple(w.state[k].shape), dtype=torch.float64, pin_memory=True)
-               for k in keys_in}
+    host = {k: torch.empty(tuple(w.state[k].shape), dtype=torch.float64, pin_memory=True)
+            for k in keys_in}
     for k in keys_in:
-        host_in[k].copy_(w.state[k])
-    host_out = {k: torch.empty(tuple(host_in[k].shape), dtype=torch.float64, pin_memory=True)
-                for k in keys_out}
+        host[k].copy_(w.state[k])
+    host["src"] = None
+    pristine = {k: host[k].clone() for k in keys_out}
     host_status = torch.empty(n, dtype=torch.uint8).pin_memory()
-    dst = {k: torch.empty_like(w.state[k]) for k in keys_in}
-    dst["src"] = None
-    status = torch.empty(n, dtype=torch.uint8, device=dev)
-    stream = torch.cuda.current_stream()
-    h2d = sum(host_in[k].numel() * 8 for k in keys_in)
-    d2h = sum(host_out[k].numel() * 8 for k in keys_out) + n
+    h2d = sum(host[k].numel() * 8 for k in keys_in)
+    d2h = sum(host[k].numel() * 8 for k in keys_out) + n
 
     def step():
-        for k in keys_in:
-            dst[k].copy_(host_in[k], non_blocking=True)
-        f = sur.source_update if sur is not None else rhd.source_update
-        f(dst, w.edges, w.law, dt=w.dt, c_v=w.c_v, consts=w.consts, precision=prec,
-          status=status, stream=stream)
-        for k in keys_out:
-            host_out[k].copy_(dst[k], non_blocking=True)
-        host_status.copy_(status, non_blocking=True)
+        rhd.source_update_host(host, w.edges, w.law, dt=w.dt, c_v=w.c_v, consts=w.consts,
+                               precision=prec, status=host_status, surrogate=sur)
 
-    step()
-    torch.cuda.synchronize()
-    barrier(ws)
-    t0 = time.perf_counter()
+    def restore():
+        for k in keys_out:
+            host[k].copy_(pristine[k])
+
+    step()  # warm-up: staging buffers, workspace
+    total = 0.0
     for _ in range(args.e2e_steps):
+        restore()
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
         step()
-    torch.cuda.synchronize()
-    dt = allmax(time.perf_counter() - t0, ws)
+        torch.cuda.synchronize()
+        total += time.perf_counter() - t0
+    dt = allmax(total, ws)
     units = allsum(float(n) * G * args.e2e_steps, ws)
-    del dst
+    del host, pristine
     return {"value": units / dt, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": args.e2e_steps,
-            "path": ("pinned host -> device copies, "
-                     + ("rhd_source_update_warm" if sur is not None else "rhd_source_update")
-                     + ", device -> pinned host")}
+            "path": ("rhd_source_update_host" + (" with the learned warm start" if sur is not None
+                                                 else "")
+                     + ": pinned host state, 2^20-cell chunks, copies overlapped with the solve")}
 
 
 def cpu_baseline(args, w):

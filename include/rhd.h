@@ -301,6 +301,24 @@ int rhd_surrogate_warm_start(rhd_surrogate_t *s, const rhd_state_t *state,
                              const rhd_groups_t *groups, const rhd_opacity_law_t *opacity_law,
                              double dt, int64_t n_cells, double *eint, float *r, void *stream);
 
+/* ---- Host-resident state --------------------------------------------------------
+ * rhd_source_update (surrogate == NULL) or rhd_source_update_warm (surrogate !=
+ * NULL) for a grid whose state lives in HOST memory: every pointer of *state is a
+ * host pointer (page-locked memory lets the copies overlap the solve; pageable
+ * memory works, serialised), with the layout of rhd_state_t (group_stride of the
+ * host arrays; 0 = n_cells).  The cells go through the GPU in chunks of
+ * chunk_cells (0 = 2^20): chunk k+1 is copied in and chunk k-1 copied out on two
+ * copy streams while chunk k is solved, through three device staging sets of the
+ * library (grown on demand, per device, never freed: 3 x chunk x (8 (6 + 5 N_g) + 2)
+ * bytes).  Each chunk is one rhd_source_update / rhd_source_update_warm call, so
+ * the results are those of the device entry, cell for cell.  Synchronous: returns
+ * when the host arrays (E_gas, rho v, E_g, F_g, status, iters) hold the result,
+ * or with the first error (every transfer started has then ended).  Calls on the
+ * same device must not overlap. */
+int rhd_source_update_host(rhd_state_t *state, const rhd_groups_t *groups,
+                           const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
+                           rhd_surrogate_t *surrogate, int64_t chunk_cells);
+
 /* ---- Benchmark support -------------------------------------------------------
  * Time the FP64-pass kernel of every rhd_source_update / rhd_source_update_warm
  * call this thread makes between rhd_profile_start and rhd_profile_stop, with

@@ -885,6 +885,7 @@ extern "C" int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids,
 }
 
 #include "rhd_surrogate.cuh"
+#include "rhd_host.cuh"
 
 extern "C" int rhd_profile_start(void) {
   for (auto &e : rhd::t_events) {

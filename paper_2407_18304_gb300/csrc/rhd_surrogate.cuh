@@ -39,37 +39,6 @@ __device__ __forceinline__ bool cell_T(const KParams &P, int64_t i, double &T) {
   return rho > 0.0 && isfinite(T) && T > 0.0;
 }
 
-// Decomposition of a positive normal double without FP64 instructions (on
-// GB300 an FP64 instruction, conversions included, costs 64 FP32 ones): from
-// the bit pattern, x = m 2^ex with m in [0.5, 1) (as frexp), m cut to FP32.
-__device__ __forceinline__ float frexp_f(double x, int &ex) {
-  const int hi = __double2hiint(x), lo = __double2loint(x);
-  ex = ((hi >> 20) & 0x7FF) - 1022;
-  const unsigned frac = ((unsigned)(hi & 0xFFFFF) << 3) | ((unsigned)lo >> 29);
-  return __int_as_float((int)((126u << 23) | frac));
-}
-
-// x 2^-sh as FP32 from the bit pattern (mantissa cut, not rounded; 0 below
-// FP32's normal range, +-inf above it).
-__device__ __forceinline__ float scaled_f(double x, int sh) {
-  const int hi = __double2hiint(x), lo = __double2loint(x);
-  const int E = (hi >> 20) & 0x7FF;
-  const unsigned sign = (unsigned)hi & 0x80000000u;
-  if (E == 0) return __int_as_float((int)sign);
-  const int fe = E - 1023 - sh + 127;
-  if (fe <= 0) return __int_as_float((int)sign);
-  if (fe >= 255) return __int_as_float((int)(sign | 0x7F800000u));
-  const unsigned frac = ((unsigned)(hi & 0xFFFFF) << 3) | ((unsigned)lo >> 29);
-  return __int_as_float((int)(sign | ((unsigned)fe << 23) | frac));
-}
-
-// A group energy that carries a feature: positive, finite, not below about
-// 1.3e-290 (exponent field >= 60), tested on the bits.
-__device__ __forceinline__ bool usable_energy(double x) {
-  const int hi = __double2hiint(x);
-  return hi >= 0 && ((hi >> 20) & 0x7FF) >= 60 && ((hi >> 20) & 0x7FF) < 0x7FF;
-}
-
 // Natural log of a positive normal double to FP32 accuracy without FP64
 // instructions: ln(m 2^e) = e ln 2 + ln m, with m in [0.5, 1).
 __device__ __forceinline__ float ln_f(double x) {

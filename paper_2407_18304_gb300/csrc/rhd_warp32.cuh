@@ -23,7 +23,9 @@ constexpr int kPlanckF = (kDeg32 + 3) * planck_table::kSeg;  // coef [8][kSeg], 
 template <int L, int GPL>
 struct WCell32 {
   int64_t i;
-  double rho, irho, irhoc, m0[3], eg0, chi0s, Etot, irc, sE;  // irho = 1/rho, irhoc = 1/(rho c)
+  double rho, irho, m0[3], eg0, chi0s, Etot, irc;  // irho = 1/rho
+  int shE, shV;  // E_tot = mE 2^shE, rho c = mV 2^shV (mE, mV in [0.5, 1))
+  float imE, imV;  // 1 / mE, 1 / mV
   double m[3], KE, Eint;  // Eint: the FP64 base of the current pass
   double chg_prev;
   int nit, it, outer, slow;
@@ -94,11 +96,15 @@ __device__ __forceinline__ float seg_sumf(float v, unsigned mask) {
 template <int L, int GPL>
 __device__ __forceinline__ void w32_set_tau(const KParams &P, const GroupTable &tab, int l,
                                             WCell32<L, GPL> &C, double cs) {
-  const double tdt = P.c_hat * P.theta * P.dt;
+  // tau_g = c_hat theta dt cs kbar_g in FP32 from the bit patterns: with
+  // c_hat theta dt cs = mt 2^et, tau_g = mt (kbar_g 2^et)
+  const double tcs = P.c_hat * P.theta * P.dt * cs;
+  int et = 0;
+  const float mt = tcs > 0.0 ? frexp_f(tcs, et) : 0.0f;
 #pragma unroll
   for (int j = 0; j < GPL; ++j) {
     const int g = l + L * j;
-    const float t = g < P.G ? (float)(tdt * cs * tab.kbar[g]) : 0.0f;
+    const float t = g < P.G ? mt * scaled_f(tab.kbar[g], -et) : 0.0f;
     C.tau[j] = t;
     C.itau[j] = t > 0.0f ? 1.0f / t : 0.0f;
     C.qe[j] = t > 0.0f ? t / (1.0f + t) : 0.0f;
@@ -139,9 +145,12 @@ __device__ __forceinline__ bool w32_load(const KParams &P, const GroupTable &tab
   C.chi0s = C.rho * k0;
   C.Etot = C.eg0 + P.cr * sumE0;
   C.irho = 1.0 / C.rho;
-  C.irhoc = C.irho / P.c;
   C.irc = C.irho / P.c_v;
-  C.sE = 1.0 / C.Etot;
+  // the energy-scaled group values are formed in FP32 from the bit patterns
+  // (exact power-of-two scaling by E_tot's exponent, then one FP32 multiply):
+  // no FP64 instruction per group
+  C.imE = 1.0f / frexp_f(C.Etot, C.shE);
+  C.imV = 1.0f / frexp_f(C.rho * P.c, C.shV);
   C.m[0] = C.m0[0];
   C.m[1] = C.m0[1];
   C.m[2] = C.m0[2];
@@ -150,15 +159,15 @@ __device__ __forceinline__ bool w32_load(const KParams &P, const GroupTable &tab
   C.outer = 0;
   C.chg_prev = HUGE_VAL;
   C.slow = 0;
-  const double fs = C.sE / P.c;
+  const float fsf = C.imE / (float)P.c;
 #pragma unroll
   for (int j = 0; j < GPL; ++j) {
     const int g = l + L * j;
     C.R[j] = 0.0f;
     if (g < G) {
       const int64_t o = (int64_t)g * P.gs + i;
-      C.e0[j] = (float)(e[j] * C.sE);
-      for (int d = 0; d < 3; ++d) C.ft[j][d] = C.f[j][d] = (float)(P.frad[d][o] * fs);
+      C.e0[j] = scaled_f(e[j], C.shE) * C.imE;
+      for (int d = 0; d < 3; ++d) C.ft[j][d] = C.f[j][d] = scaled_f(P.frad[d][o], C.shE) * fsf;
     } else {
       C.e0[j] = 0.0f;
       for (int d = 0; d < 3; ++d) C.ft[j][d] = C.f[j][d] = 0.0f;
@@ -172,16 +181,16 @@ __device__ __forceinline__ bool w32_load(const KParams &P, const GroupTable &tab
 template <int L, int GPL>
 __device__ __forceinline__ void w32_outer_begin(const KParams &P, WCell32<L, GPL> &C) {
   C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) * C.irho;
-  for (int d = 0; d < 3; ++d) C.be[d] = (float)(C.m[d] * C.irhoc);
+  for (int d = 0; d < 3; ++d) C.be[d] = scaled_f(C.m[d], C.shV) * C.imV;  // v / c
 #pragma unroll
   for (int j = 0; j < GPL; ++j)
     C.w[j] = C.be[0] * C.f[j][0] + C.be[1] * C.f[j][1] + C.be[2] * C.f[j][2];
   const double T0 = C.Eint * C.irc;
-  C.eb = (float)(C.Eint * C.sE);
+  C.eb = scaled_f(C.Eint, C.shE) * C.imE;
   C.dlt = 0.0f;
-  C.FG0 = (float)((C.Eint + C.KE - C.eg0) * C.sE);
-  C.k4 = (float)(P.a_rad * T0 * T0 * T0 * T0 * C.sE);
-  C.iT0 = (float)(1.0 / T0);
+  C.FG0 = scaled_f(C.Eint + C.KE - C.eg0, C.shE) * C.imE;
+  C.k4 = scaled_f(P.a_rad * T0 * T0 * T0 * T0, C.shE) * C.imE;
+  C.iT0 = 1.0f / (float)T0;
   C.it = 0;
 }
 
@@ -316,8 +325,8 @@ __device__ __forceinline__ bool w32_outer_end(const KParams &P, const GroupTable
   const double mf = Etot * P.icc * P.c;  // E_tot / c_hat
   const double mn[3] = {C.m0[0] - mf * df[0], C.m0[1] - mf * df[1], C.m0[2] - mf * df[2]};
   const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) * C.irho;
-  const float bn[3] = {(float)(mn[0] * C.irhoc), (float)(mn[1] * C.irhoc),
-                       (float)(mn[2] * C.irhoc)};
+  const float bn[3] = {scaled_f(mn[0], C.shV) * C.imV, scaled_f(mn[1], C.shV) * C.imV,
+                       scaled_f(mn[2], C.shV) * C.imV};
   float cg = 0.0f;
 #pragma unroll
   for (int j = 0; j < GPL; ++j) {
@@ -326,7 +335,7 @@ __device__ __forceinline__ bool w32_outer_end(const KParams &P, const GroupTable
     const float wn = bn[0] * C.f[j][0] + bn[1] * C.f[j][1] + bn[2] * C.f[j][2];
     cg += fabsf((1.0f + tab.alphaf[g]) * C.q[j] * (wn - C.w[j])) * C.qe[j];
   }
-  const float chg = (float)(fabs(KEn - C.KE) * C.sE) + seg_sumf<L>(cg, mask);
+  const float chg = scaled_f(fabs(KEn - C.KE), C.shE) * C.imE + seg_sumf<L>(cg, mask);
   C.m[0] = mn[0];
   C.m[1] = mn[1];
   C.m[2] = mn[2];

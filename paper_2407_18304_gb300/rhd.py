@@ -124,6 +124,10 @@ def lib() -> ctypes.CDLL:
             f = getattr(_lib, name)
             f.restype = ctypes.c_int
             f.argtypes = args
+        _lib.rhd_source_update_host.restype = ctypes.c_int
+        _lib.rhd_source_update_host.argtypes = [ctypes.POINTER(State), ctypes.POINTER(Groups),
+                                                ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64,
+                                                _P, ctypes.c_int64]
         _lib.rhd_imex_step.restype = ctypes.c_int
         _lib.rhd_imex_step.argtypes = [ctypes.POINTER(State), ctypes.POINTER(Groups),
                                        ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _P]
@@ -147,9 +151,9 @@ def _dp(a: np.ndarray):
     return a.ctypes.data_as(ctypes.POINTER(_D))
 
 
-def _check(t: torch.Tensor, name: str, shape, dtype=torch.float64):
-    if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
-        raise ValueError(f"{name} must be a CUDA tensor")
+def _check(t: torch.Tensor, name: str, shape, dtype=torch.float64, device: str = "cuda"):
+    if not isinstance(t, torch.Tensor) or t.device.type != device:
+        raise ValueError(f"{name} must be a {device.upper()} tensor")
     if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
         raise ValueError(f"{name}: expected contiguous {dtype} {tuple(shape)}, got "
                          f"{t.dtype} {tuple(t.shape)}")
@@ -178,22 +182,23 @@ def make_law(law, mode: int = PPL_FIXED, khat_g=None, alpha_g=None, temp_exponen
 
 def _state(state: dict, G: int, n: int, gs: int, *, c_v: float, consts: dict, theta: float,
            precision: int, closure: int, tol: float, tol_outer: float, max_newton: int,
-           max_outer: int, status, iters, flags: int) -> State:
+           max_outer: int, status, iters, flags: int, device: str = "cuda") -> State:
     """Check the tensors of one grid and fill the C state struct."""
     rho = state["rho"]
-    _check(rho, "rho", (rho.shape[0],))
-    _check(state["mom"], "mom", (3, rho.shape[0]))
-    _check(state["egas"], "egas", (rho.shape[0],))
-    _check(state["erad"], "erad", (G, gs))
-    _check(state["frad"], "frad", (3, G, gs))
+    d = device
+    _check(rho, "rho", (rho.shape[0],), device=d)
+    _check(state["mom"], "mom", (3, rho.shape[0]), device=d)
+    _check(state["egas"], "egas", (rho.shape[0],), device=d)
+    _check(state["erad"], "erad", (G, gs), device=d)
+    _check(state["frad"], "frad", (3, G, gs), device=d)
     if state.get("kappa0") is not None:
-        _check(state["kappa0"], "kappa0", (rho.shape[0],))
+        _check(state["kappa0"], "kappa0", (rho.shape[0],), device=d)
     if state.get("src") is not None:
-        _check(state["src"], "src", (G, gs))
+        _check(state["src"], "src", (G, gs), device=d)
     if status is not None:
-        _check(status, "status", (rho.shape[0],), torch.uint8)
+        _check(status, "status", (rho.shape[0],), torch.uint8, device=d)
     if iters is not None:
-        _check(iters, "iters", (rho.shape[0],), torch.uint8)
+        _check(iters, "iters", (rho.shape[0],), torch.uint8, device=d)
     mom, frad = state["mom"], state["frad"]
     st = State()
     st.rho = _ptr(rho)
@@ -269,6 +274,35 @@ def imex_step(state: dict, edges, law, *, dt: float, c_v: float, consts: dict,
     s = stream if stream is not None else torch.cuda.current_stream()
     rc = lib().rhd_imex_step(ctypes.byref(st), ctypes.byref(gr), ctypes.byref(lw), float(dt),
                              int(n), ctypes.c_void_p(s.cuda_stream))
+    del keep
+    if rc != 0:
+        raise RhdError(rc, lib().rhd_strerror(rc).decode())
+
+
+def source_update_host(state: dict, edges, law, *, dt: float, c_v: float, consts: dict,
+                       theta: float = 1.0, precision: int = FP64, closure: int = M1,
+                       tol: float = 0.0, tol_outer: float = 0.0, max_newton: int = 0,
+                       max_outer: int = 0, status: torch.Tensor | None = None,
+                       iters: torch.Tensor | None = None, mode: int = PPL_FIXED, khat_g=None,
+                       alpha_g=None, temp_exponent: float = 0.0, T_ref: float = 1.0,
+                       flags: int = 0, surrogate: "Surrogate | None" = None,
+                       chunk_cells: int = 0) -> None:
+    """``rhd_source_update_host``: the update of a grid whose tensors live in
+    host memory (CPU float64 tensors, pinned for overlapped copies; same layout
+    as ``source_update``), in chunks streamed through the GPU; with a
+    ``surrogate`` each chunk starts from its guess.  Synchronous."""
+    rho = state["rho"]
+    n = rho.shape[0]
+    e = np.ascontiguousarray(edges, dtype=np.float64)
+    G = len(e) - 1
+    st = _state(state, G, n, n, c_v=c_v, consts=consts, theta=theta, precision=precision,
+                closure=closure, tol=tol, tol_outer=tol_outer, max_newton=max_newton,
+                max_outer=max_outer, status=status, iters=iters, flags=flags, device="cpu")
+    gr = Groups(G, _dp(e))
+    lw, keep = make_law(law, mode, khat_g, alpha_g, temp_exponent, T_ref)
+    h = surrogate._h if surrogate is not None else None
+    rc = lib().rhd_source_update_host(ctypes.byref(st), ctypes.byref(gr), ctypes.byref(lw),
+                                      float(dt), int(n), h, int(chunk_cells))
     del keep
     if rc != 0:
         raise RhdError(rc, lib().rhd_strerror(rc).decode())

@@ -74,6 +74,28 @@ def test_argument_checks_without_a_device(lib):
     assert lib.rhd_version() >= 100
 
 
+def test_host_entry_checks_without_a_device(lib):
+    """rhd_source_update_host validates like the device entry before touching a
+    device: zero cells return at once, a negative chunk or bad edges are refused."""
+    w = synth.preset("tiny", n_cells=1)
+    st = rhd.State()
+    st.c_v, st.theta = w.c_v, 1.0
+    st.c, st.c_hat, st.a_rad, st.h, st.k_B = (w.consts[k] for k in ("c", "c_hat", "a_rad", "h", "k_B"))
+    e = np.ascontiguousarray(synth.log_edges(4), dtype=np.float64)
+    gr = rhd.Groups(len(e) - 1, e.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    lw, keep = rhd.make_law(w.law)
+    f = lib.rhd_source_update_host
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double,
+                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64]
+    assert f(ctypes.byref(st), ctypes.byref(gr), ctypes.byref(lw), w.dt, 0, None, 0) == 0
+    assert f(ctypes.byref(st), ctypes.byref(gr), ctypes.byref(lw), w.dt, 0, None, -5) == -1
+    assert f(None, ctypes.byref(gr), ctypes.byref(lw), w.dt, 0, None, 0) == -1
+    bad = e[::-1].copy()
+    gb = rhd.Groups(len(bad) - 1, bad.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert f(ctypes.byref(st), ctypes.byref(gb), ctypes.byref(lw), w.dt, 0, None, 0) == -2
+
+
 def test_batched_entry_points_reject_null_arguments_without_a_device(lib):
     grids = (rhd.Grid * 1)()
     assert lib.rhd_source_update_batched(None, grids, 1, None) == -1
