@@ -79,7 +79,9 @@ extern "C" {
                                  spreads a cell's 33..128 groups over a warp's lanes; same
                                  equations and results to rounding, slower at those sizes;
                                  for comparison and for counting the algorithm's operations
-                                 without the lane-replicated per-cell work) */
+                                 without the lane-replicated per-cell work: under this flag
+                                 the thread mapping also takes the warp mapping's cached first
+                                 iteration of each outer pass, which it otherwise skips) */
 #define RHD_FLUX_TEST 2  /* the outer iteration also stops only when the change of the
                             group fluxes, sum_g |F_g,new - F_g,old|_1 / c, is below
                             tol_outer E_tot (the paper's test sees F_g only through the

@@ -280,12 +280,12 @@ void launch_free(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st
   solve_free_kernel<MAXG><<<b, threads, smem, st>>>(kp, W);
 }
 
-template <int MAXG>
+template <int MAXG, bool CACHE = false>
 void launch_thread(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
   const int threads = 128;
   const size_t smem = table_bytes(kp.G);
-  const int b = persistent_blocks(solve_fp64_kernel<MAXG>, smem, sms, kp.n, threads);
-  solve_fp64_kernel<MAXG><<<b, threads, smem, st>>>(kp, W);
+  const int b = persistent_blocks(solve_fp64_kernel<MAXG, CACHE>, smem, sms, kp.n, threads);
+  solve_fp64_kernel<MAXG, CACHE><<<b, threads, smem, st>>>(kp, W);
 }
 
 // rhd_profile_start/stop: event pairs around the FP64-pass launches of this thread.
@@ -317,10 +317,10 @@ void launch_fp64_passes_impl(const KParams &kp, const WarmStart &W, int sms, cud
     else launch_free<kMaxG>(kp, W, sms, st);
     return;
   }
-  if (kp.flags & RHD_CELL_PER_THREAD) {
-    if (kp.G <= 16) launch_thread<16>(kp, W, sms, st);
-    else if (kp.G <= 64) launch_thread<64>(kp, W, sms, st);
-    else launch_thread<kMaxG>(kp, W, sms, st);
+  if (kp.flags & RHD_CELL_PER_THREAD) {  // with the warp mapping's cached iterations
+    if (kp.G <= 16) launch_thread<16, true>(kp, W, sms, st);
+    else if (kp.G <= 64) launch_thread<64, true>(kp, W, sms, st);
+    else launch_thread<kMaxG, true>(kp, W, sms, st);
     return;
   }
   if (kp.G <= 16) launch_thread<16>(kp, W, sms, st);

@@ -80,6 +80,7 @@ struct Cell {
   int slow;        // the outer iteration contracted slowly: Newton flux steps on
   int fresh;       // the last inner step converged: FR_g ~ 0 at the current T, R_g
   int cached;      // A.FR holds the residual at the current T, R_g (see inner_cached)
+  int use_cache;   // take the cached first iteration of a pass (see outer_end)
 };
 
 // Thread-local per-group arrays of the FP64 passes.
@@ -142,6 +143,7 @@ __device__ __forceinline__ bool load_cell(const KParams &P, int64_t i, Cell &C, 
   C.slow = 0;
   C.fresh = 0;
   C.cached = 0;
+  C.use_cache = 0;  // set by the kernels that take the cached iteration
   return true;
 }
 
@@ -235,10 +237,10 @@ __device__ __forceinline__ int inner_cached(const KParams &P, Cell &C, Arr64<MAX
 // One inner Newton iteration (a4-a8): evaluate the residual at the current
 // iterate; if the convergence test passes, set each R_g from its own row and
 // return 1; at the iteration cap return 2; else take the Newton step, return 0.
-template <int MAXG>
+template <int MAXG, bool CACHE = false>
 __device__ __forceinline__ int inner_step(const KParams &P, const GroupTable &tab, Cell &C,
                                           Arr64<MAXG> &A) {
-  if (C.cached) return inner_cached(P, C, A);
+  if (CACHE && C.cached) return inner_cached(P, C, A);
   const int G = P.G;
   const int64_t i = C.i;
   const double T = C.Eint * C.irc;
@@ -412,7 +414,7 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
     const double dvf = (1.0 + tab.alpha[g]) * A.qF[g] * (wn - A.w[g]);
     const double cg = fabs(tauE * dvf) / (1.0 + tauE);
     chg += cg;
-    A.FR[g] = A.qe[g] > 0.0 ? dvf : -A.R[g];  // the residual at T, R_g for the new w (inner_cached)
+    if (C.use_cache) A.FR[g] = A.qe[g] > 0.0 ? dvf : -A.R[g];  // residual at T, R_g, new w
     if (gtest) {
       const int64_t o = (int64_t)g * P.gs + i;
       const double s = P.src ? P.src[o] : 0.0;
@@ -432,7 +434,7 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
     C.stat = RHD_STATUS_MAXITER;
     return true;
   }
-  if (C.fresh) {
+  if (C.fresh && C.use_cache) {
     // the next inner solve starts at this T and R_g, where its first
     // residual is known without evaluating the groups (inner_cached)
     outer_begin(P, C, A);
@@ -504,8 +506,13 @@ __device__ __forceinline__ void apply_warm(const KParams &P, const WarmStart &W,
 // ..., finishing each before the next.  With a warm start (W.r) the first
 // attempt starts from it; if that attempt does not converge and W.fallback is
 // set, the cell is solved again from the cold start (status FALLBACK if that
-// converges).
-template <int MAXG>
+// converges).  CACHE: take the cached first iteration of each outer pass.  The
+// lanes of a warp hold different cells here, so a cached iteration on some
+// lanes runs beside full evaluations on others and saves nothing (measured:
+// +50 % time at 16 and 32 groups, and the extra path costs registers); it is
+// instantiated for RHD_CELL_PER_THREAD, which runs the warp mapping's
+// algorithm to count its operations.
+template <int MAXG, bool CACHE = false>
 __global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__ KParams P,
                                                          const WarmStart W) {
   extern __shared__ double sm[];
@@ -516,18 +523,20 @@ __global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__
   const bool warm = W.r != nullptr;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
     if (!load_cell(P, i, C, A)) continue;
+    C.use_cache = CACHE;
     for (int attempt = 0; attempt < 2; ++attempt) {
       int nit0 = 0;
       if (attempt == 1) {
         if (!(warm && W.fallback && C.stat != RHD_STATUS_OK)) break;
         nit0 = C.nit;
         load_cell(P, i, C, A);
+        C.use_cache = CACHE;
       }
       set_tau(P, tab, C, A, C.chi0s);
       if (warm && attempt == 0) apply_warm(P, W, C, A);
       outer_begin(P, C, A);
       for (;;) {
-        const int r = inner_step(P, tab, C, A);
+        const int r = inner_step<MAXG, CACHE>(P, tab, C, A);
         if (r == 0) continue;
         if (r == 2) C.stat = RHD_STATUS_MAXITER;
         if (outer_end(P, tab, C, A)) break;

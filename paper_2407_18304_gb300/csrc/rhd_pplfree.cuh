@@ -161,7 +161,6 @@ template <int MAXG>
 __device__ __forceinline__ int inner_step_free(const KParams &P, const GroupTable &tab,
                                                const FreeGeom &fg, Cell &C, Arr64<MAXG> &A,
                                                FreeArr<MAXG> &F) {
-  if (C.cached) return inner_cached(P, C, A);
   const int G = P.G;
   const int64_t i = C.i;
   const double T = C.Eint * C.irc;
