@@ -166,26 +166,26 @@ def fp_peaks() -> dict:
 # every lane of the cell repeats).
 # FP64 arithmetic instructions (DFMA, DADD, DMUL: one issue each) of the
 # FP64-pass kernel (the one that dominates a call, timed live below):
-FP64_PASS_INST_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 729.4,
-                         ("full_256cube_ng64", "mixed"): 732.3,
-                         ("full_256cube_ng64", "fp64"): 1314.0,
-                         ("full_256cube_ng64", "fp64+surrogate"): 1206.4}
+FP64_PASS_INST_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 715.8,
+                         ("full_256cube_ng64", "mixed"): 718.8,
+                         ("full_256cube_ng64", "fp64"): 1294.4,
+                         ("full_256cube_ng64", "fp64+surrogate"): 1186.9}
 # ... the same as flops (DFMA counted twice)
-FP64_PASS_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1104.2,
-                          ("full_256cube_ng64", "mixed"): 1108.8,
-                          ("full_256cube_ng64", "fp64"): 2009.3,
-                          ("full_256cube_ng64", "fp64+surrogate"): 1836.9}
+FP64_PASS_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1066.6,
+                          ("full_256cube_ng64", "mixed"): 1071.3,
+                          ("full_256cube_ng64", "fp64"): 1955.0,
+                          ("full_256cube_ng64", "fp64+surrogate"): 1782.7}
 # ... and the flops of the whole call (inference, FP32 passes, FP64 passes)
-CALL_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1133.7,
-                     ("full_256cube_ng64", "mixed"): 1123.2,
-                     ("full_256cube_ng64", "fp64"): 2009.3,
-                     ("full_256cube_ng64", "fp64+surrogate"): 1852.5}
+CALL_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1081.3,
+                     ("full_256cube_ng64", "mixed"): 1085.7,
+                     ("full_256cube_ng64", "fp64"): 1955.0,
+                     ("full_256cube_ng64", "fp64+surrogate"): 1783.5}
 # DRAM bytes (read + write) per cell-group of one launch of the FP64-pass
 # kernel in the default mapping, from the same capture
-FP64_PASS_TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 69.4,
-                            ("full_256cube_ng64", "mixed"): 69.3,
-                            ("full_256cube_ng64", "fp64"): 52.1,
-                            ("full_256cube_ng64", "fp64+surrogate"): 69.0}
+FP64_PASS_TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 69.3,
+                            ("full_256cube_ng64", "mixed"): 69.1,
+                            ("full_256cube_ng64", "fp64"): 52.0,
+                            ("full_256cube_ng64", "fp64+surrogate"): 68.9}
 
 
 def train_surrogate(args, w, dev, rank):

@@ -297,6 +297,33 @@ __device__ __forceinline__ void closure_vP(int closure, R c, R E, R F0, R F1, R 
   o2 = e3 * v2;
 }
 
+// closure_vP in parts for a caller that divides by another positive quantity
+// as well (the flux update): v . P = a v + (kn / kd) F with kd > 0, so that
+// one reciprocal serves both divisions.  ic = 1 / c.
+template <typename R>
+__device__ __forceinline__ void closure_vP_parts(int closure, R c, R ic, R E, R F0, R F1, R F2,
+                                                 R v0, R v1, R v2, R &a, R &kn, R &kd) {
+  const R fn2 = F0 * F0 + F1 * F1 + F2 * F2;
+  if (closure == RHD_M1 && E > R(0) && fn2 > R(0)) {
+    const R cE = c * E, cE2 = cE * cE;
+    const R vF = v0 * F0 + v1 * F1 + v2 * F2;
+    if (fn2 < cE2) {
+      const R S = sqrt(R(4) * cE2 - R(3) * fn2);
+      a = (S - cE) * (R(1) / R(3)) * ic;
+      kn = R(3) * vF * ic;
+      kd = R(2) * cE + S;
+    } else {
+      a = R(0);
+      kn = E * vF;
+      kd = fn2;
+    }
+    return;
+  }
+  a = E * (R(1) / R(3));
+  kn = R(0);
+  kd = R(1);
+}
+
 // v . P_g and M = d(v . P_g)/dF_g at fixed E_g for the M1 closure of
 // closure_vP (Levermore's Eddington factor chi(f), f = |F|/(cE) held at 1):
 // with n = F/|F|, vn = v . n,

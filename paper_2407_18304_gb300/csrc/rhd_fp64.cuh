@@ -368,11 +368,25 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
     const double s = P.src ? P.src[o] : 0.0;
     const double Enew = P.erad[o] + A.R[g] + s;
     const double chiE = C.cs * kq[g], a = tab.alpha[g];  // A.bq holds chi_B b_g / chi_E
-    double vp0, vp1, vp2;
-    closure_vP<double>(P.closure, c, Enew, A.Fk[3 * g], A.Fk[3 * g + 1], A.Fk[3 * g + 2], v[0],
-                       v[1], v[2], vp0, vp1, vp2);
+    // v.P_g = ca v + (kn / kd) F_g; one reciprocal of (1 + c_hat theta dt chi_F) kd
+    // gives both divisions
+    double ca, kn, kd;
+    closure_vP_parts<double>(P.closure, c, P.ic, Enew, A.Fk[3 * g], A.Fk[3 * g + 1],
+                             A.Fk[3 * g + 2], v[0], v[1], v[2], ca, kn, kd);
     const double srcg = chiE * (A.bq[g] - A.dnx[g] * (1.0 / 3.0));
-    const double inv = 1.0 / (1.0 + tdt * chiE * A.qF[g]);
+    const double den = 1.0 + tdt * chiE * A.qF[g];
+    const double dk = den * kd;
+    double inv, kf;
+    if (dk > 1e-290) {  // one reciprocal (kd is tiny only for a nearly empty group)
+      const double rr = 1.0 / dk;
+      inv = kd * rr;
+      kf = kn * den * rr;
+    } else {
+      inv = 1.0 / den;
+      kf = kn / kd;
+    }
+    const double vp0 = ca * v[0] + kf * A.Fk[3 * g], vp1 = ca * v[1] + kf * A.Fk[3 * g + 1],
+                 vp2 = ca * v[2] + kf * A.Fk[3 * g + 2];
     const double kap = tdt * (1.0 + a) * chiE * inv;
     newton = newton || kap * kap * v2c > c2;  // 10 |kap| |v| > c
     const double ft0 = P.frad[0][o], ft1 = P.frad[1][o], ft2 = P.frad[2][o];

@@ -330,11 +330,25 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
     const double chiB = C.cs * tab.kbar[g], a = tab.alpha[g];
     const int64_t o = (int64_t)g * P.gs + C.i;
     const double ft[3] = {P.frad[0][o], P.frad[1][o], P.frad[2][o]};
-    double vp0, vp1, vp2;
-    closure_vP<double>(P.closure, c, Enew, C.Fk[j][0], C.Fk[j][1], C.Fk[j][2], v[0], v[1], v[2],
-                       vp0, vp1, vp2);
+    // v.P_g = ca v + (kn / kd) F_g; one reciprocal of (1 + c_hat theta dt chi_F) kd
+    // gives both divisions
+    double ca, kn, kd;
+    closure_vP_parts<double>(P.closure, c, P.ic, Enew, C.Fk[j][0], C.Fk[j][1], C.Fk[j][2], v[0],
+                             v[1], v[2], ca, kn, kd);
     const double srcg = chiB * (C.bq[j] - C.dnx[j] * (1.0 / 3.0));
-    const double inv = 1.0 / (1.0 + tdt * chiB * C.qF[j]);
+    const double den = 1.0 + tdt * chiB * C.qF[j];
+    const double dk = den * kd;
+    double inv, kf;
+    if (dk > 1e-290) {  // one reciprocal (kd is tiny only for a nearly empty group)
+      const double rr = 1.0 / dk;
+      inv = kd * rr;
+      kf = kn * den * rr;
+    } else {
+      inv = 1.0 / den;
+      kf = kn / kd;
+    }
+    const double vp0 = ca * v[0] + kf * C.Fk[j][0], vp1 = ca * v[1] + kf * C.Fk[j][1],
+                 vp2 = ca * v[2] + kf * C.Fk[j][2];
     const double kap = tdt * (1.0 + a) * chiB * inv;
     newton = newton || kap * kap * v2c > c2;  // 10 |kap| |v| > c
     const double n0 = (ft[0] + tdt * v[0] * srcg) * inv + kap * vp0;

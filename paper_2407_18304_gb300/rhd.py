@@ -364,7 +364,7 @@ def source_update_noalloc(state: dict, edges, law, *, dt: float, c_v: float, con
 
 
 MAX_GROUPS_BATCHED = 64
-SURROGATE_CHUNK = 1 << 20  # cells per inference chunk of rhd_source_update_warm
+HOST_CHUNK = 1 << 20  # default cells per chunk of rhd_source_update_host
 MAX_GRIDS = 4096
 
 
