@@ -161,9 +161,9 @@ template <int L, int GPL>
 __device__ __forceinline__ int wtail(const KParams &P, unsigned mask, WCell<L, GPL> &C,
                                      double sumR, double sFRe, double sde, double sabs) {
   const double cr = P.cr;
+  // the test's two sums first: the step's two are only needed when it fails
+  // (most full evaluations of a warm-started pass end converged)
   sumR = seg_sum<L>(sumR, mask);
-  sFRe = seg_sum<L>(sFRe, mask);
-  sde = seg_sum<L>(sde, mask);
   sabs = seg_sum<L>(sabs, mask);
   const double FG = C.Eint + C.KE - C.eg0 + cr * sumR;
   if (fabs(FG) < P.tol * C.Etot && cr * sabs < P.tol * C.Etot) {
@@ -175,6 +175,8 @@ __device__ __forceinline__ int wtail(const KParams &P, unsigned mask, WCell<L, G
   }
   C.fresh = 0;
   if (C.it >= P.max_newton) return 2;
+  sFRe = seg_sum<L>(sFRe, mask);
+  sde = seg_sum<L>(sde, mask);
   const double dE = (-FG + cr * sFRe) / (1.0 - cr * sde);
   double lam = 1.0;
   for (int k = 0; k < 40 && !(C.Eint + lam * dE > 0.0); ++k) lam *= 0.5;
