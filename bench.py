@@ -181,11 +181,11 @@ CALL_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1081.3,
                      ("full_256cube_ng64", "fp64"): 1955.0,
                      ("full_256cube_ng64", "fp64+surrogate"): 1783.5}
 # DRAM bytes (read + write) per cell-group of one launch of the FP64-pass
-# kernel in the default mapping, from the same capture
-FP64_PASS_TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 69.3,
-                            ("full_256cube_ng64", "mixed"): 69.1,
-                            ("full_256cube_ng64", "fp64"): 52.0,
-                            ("full_256cube_ng64", "fp64+surrogate"): 68.9}
+# kernel in the default mapping (ncu on the same sample, the current kernel)
+FP64_PASS_TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 69.1,
+                            ("full_256cube_ng64", "mixed"): 68.2,
+                            ("full_256cube_ng64", "fp64"): 51.6,
+                            ("full_256cube_ng64", "fp64+surrogate"): 68.4}
 
 
 def train_surrogate(args, w, dev, rank):
