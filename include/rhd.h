@@ -44,6 +44,7 @@ extern "C" {
 #define RHD_ECUDA (-4)    /* a CUDA call failed (launch, copy, device query) */
 #define RHD_ENOMEM (-5)   /* workspace allocation failed */
 #define RHD_ESIZE (-6)    /* a size exceeds a compiled limit (groups, segments, grids) */
+#define RHD_EIO (-7)      /* a file could not be opened, read or written, or is not a saved surrogate */
 
 /* compiled limits */
 #define RHD_MAX_GROUPS 256
@@ -286,6 +287,16 @@ int rhd_surrogate_train_step(rhd_surrogate_t *s, const float *x, const float *y,
 int rhd_surrogate_predict(rhd_surrogate_t *s, const float *x, int64_t n, float *y, void *stream);
 /* 1 if a tensor-core wait of this surrogate ever timed out (results then invalid). */
 int rhd_surrogate_error(rhd_surrogate_t *s, int32_t *flag);
+/* Save the network (parameters and standardisation, not the Adam moments) to a
+ * file: the 8 bytes "RHDMLP1\0", int32 n_groups, n_features, n_outputs, int64
+ * n_params, then n_params FP32 parameters and 2 (n_features + n_outputs) FP32
+ * standardisation values, all little-endian.  Synchronises the device.
+ * RHD_EIO when the file cannot be written. */
+int rhd_surrogate_save(rhd_surrogate_t *s, const char *path);
+/* Create a surrogate on the current device from a file rhd_surrogate_save wrote
+ * (Adam moments zero, so training resumes with a fresh optimiser state).
+ * RHD_EIO when the file cannot be read or its header or length does not match. */
+int rhd_surrogate_load(const char *path, rhd_surrogate_t **out);
 /* rhd_source_update (FP64 or mixed form, from state->precision) started from the
  * surrogate's guess; groups->n_groups must equal the surrogate's.  Same results to
  * the caller's tolerance; status RHD_STATUS_FALLBACK marks cells that needed the

@@ -4,6 +4,7 @@
 // rhd_batched.cuh (many grids, one persistent launch); this is the only
 // translation unit.
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -926,6 +927,7 @@ extern "C" const char *rhd_strerror(int code) {
     case RHD_ECUDA: return "CUDA error";
     case RHD_ENOMEM: return "out of workspace memory";
     case RHD_ESIZE: return "size exceeds a compiled limit";
+    case RHD_EIO: return "file error";
     default: return "unknown error";
   }
 }

@@ -885,3 +885,86 @@ extern "C" int rhd_surrogate_warm_start(rhd_surrogate_t *s, const rhd_state_t *s
   rhd::WarmOut wo{eint, nullptr, r, nullptr, nullptr};
   return rhd::launch_fused(s, kp, wo, false, sms, (cudaStream_t)stream);
 }
+
+// ---- saving and loading a network ------------------------------------------
+namespace rhd {
+namespace {
+constexpr char kMlpMagic[8] = {'R', 'H', 'D', 'M', 'L', 'P', '1', '\0'};
+
+struct MlpHeader {
+  char magic[8];
+  int32_t n_groups, n_features, n_outputs;
+  int32_t pad;
+  int64_t n_params;
+};
+static_assert(sizeof(MlpHeader) == 32, "file header");
+}  // namespace
+}  // namespace rhd
+
+extern "C" int rhd_surrogate_save(rhd_surrogate_t *s, const char *path) {
+  int rc = rhd::check_surrogate(s);
+  if (rc != RHD_OK) return rc;
+  if (!path) return RHD_EINVAL;
+  const size_t np = (size_t)s->nparam, nn = 2 * (size_t)(s->kin + s->nout);
+  std::vector<float> buf(np + nn);
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(buf.data(), s->params, sizeof(float) * np, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(buf.data() + np, s->norm, sizeof(float) * nn, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return RHD_ECUDA;
+  rhd::MlpHeader h{};
+  std::memcpy(h.magic, rhd::kMlpMagic, 8);
+  h.n_groups = s->G;
+  h.n_features = s->kin;
+  h.n_outputs = s->nout;
+  h.n_params = s->nparam;
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return RHD_EIO;
+  const bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+                  std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size();
+  return (std::fclose(f) == 0 && ok) ? RHD_OK : RHD_EIO;
+}
+
+extern "C" int rhd_surrogate_load(const char *path, rhd_surrogate_t **out) {
+  if (!path || !out) return RHD_EINVAL;
+  *out = nullptr;
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return RHD_EIO;
+  rhd::MlpHeader h{};
+  const bool head_ok = std::fread(&h, sizeof(h), 1, f) == 1 &&
+                       std::memcmp(h.magic, rhd::kMlpMagic, 8) == 0 && h.n_groups >= 1 &&
+                       h.n_groups <= rhd::mlp::kMaxGS && h.n_params > 0 &&
+                       h.n_features == 2 * h.n_groups + 4 && h.n_outputs == h.n_groups + 1;
+  if (!head_ok) {
+    std::fclose(f);
+    return RHD_EIO;
+  }
+  const size_t np = (size_t)h.n_params, nn = 2 * (size_t)(h.n_features + h.n_outputs);
+  std::vector<float> buf(np + nn);
+  const bool body_ok = std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size() &&
+                       std::fgetc(f) == EOF;
+  std::fclose(f);
+  if (!body_ok) return RHD_EIO;
+  rhd_surrogate_t *s = nullptr;
+  int rc = rhd_surrogate_create(h.n_groups, 0, &s);
+  if (rc != RHD_OK) return rc;
+  if (s->nparam != h.n_params || s->kin != h.n_features || s->nout != h.n_outputs) {
+    rhd_surrogate_destroy(s);
+    return RHD_EIO;
+  }
+  if (cudaMemcpy(s->params, buf.data(), sizeof(float) * np, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(s->norm, buf.data() + np, sizeof(float) * nn, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(s->am, 0, sizeof(float) * np) != cudaSuccess ||
+      cudaMemset(s->av, 0, sizeof(float) * np) != cudaSuccess) {
+    rhd_surrogate_destroy(s);
+    return RHD_ECUDA;
+  }
+  s->step = 0;
+  rc = rhd::publish(s, nullptr);
+  if (rc == RHD_OK && cudaDeviceSynchronize() != cudaSuccess) rc = RHD_ECUDA;
+  if (rc != RHD_OK) {
+    rhd_surrogate_destroy(s);
+    return rc;
+  }
+  *out = s;
+  return RHD_OK;
+}

@@ -116,6 +116,8 @@ def lib() -> ctypes.CDLL:
             "rhd_surrogate_error": [_P, ctypes.POINTER(ctypes.c_int32)],
             "rhd_source_update_warm": [_P, ctypes.POINTER(State), ctypes.POINTER(Groups),
                                        ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _P],
+            "rhd_surrogate_save": [_P, ctypes.c_char_p],
+            "rhd_surrogate_load": [ctypes.c_char_p, ctypes.POINTER(_P)],
             "rhd_surrogate_warm_start": [_P, ctypes.POINTER(State), ctypes.POINTER(Groups),
                                          ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _F, _F,
                                          _P],
@@ -450,14 +452,29 @@ class Surrogate:
     cores mapping a cell's state to a guess of its updated temperature and
     group energies.  All arrays are CUDA float32 tensors, row-major."""
 
-    def __init__(self, n_groups: int, seed: int = 0):
-        h = _P()
-        _raise(lib().rhd_surrogate_create(int(n_groups), int(seed), ctypes.byref(h)))
+    def __init__(self, n_groups: int, seed: int = 0, _handle=None):
+        h = _handle
+        if h is None:
+            h = _P()
+            _raise(lib().rhd_surrogate_create(int(n_groups), int(seed), ctypes.byref(h)))
         self._h = h
         self.n_groups = int(n_groups)
         nf, no, npar = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
         _raise(lib().rhd_surrogate_dims(h, ctypes.byref(nf), ctypes.byref(no), ctypes.byref(npar)))
         self.n_features, self.n_outputs, self.n_params = nf.value, no.value, npar.value
+
+    def save(self, path: str) -> None:
+        """``rhd_surrogate_save``: parameters and standardisation to a file."""
+        _raise(lib().rhd_surrogate_save(self._h, os.fsencode(path)))
+
+    @classmethod
+    def load(cls, path: str) -> "Surrogate":
+        """``rhd_surrogate_load``: a surrogate on the current device from a saved file."""
+        h = _P()
+        _raise(lib().rhd_surrogate_load(os.fsencode(path), ctypes.byref(h)))
+        nf, no, npar = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        _raise(lib().rhd_surrogate_dims(h, ctypes.byref(nf), ctypes.byref(no), ctypes.byref(npar)))
+        return cls(no.value - 1, _handle=h)
 
     def close(self) -> None:
         if getattr(self, "_h", None) is not None and self._h.value:

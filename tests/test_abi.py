@@ -96,6 +96,29 @@ def test_host_entry_checks_without_a_device(lib):
     assert f(ctypes.byref(st), ctypes.byref(gb), ctypes.byref(lw), w.dt, 0, None, 0) == -2
 
 
+def test_surrogate_file_checks_without_a_device(lib, tmp_path):
+    """rhd_surrogate_load reads and checks the file before it touches a device:
+    a missing file, a foreign header or a short body are RHD_EIO; null
+    arguments RHD_EINVAL; saving a null surrogate RHD_EINVAL."""
+    load, save = lib.rhd_surrogate_load, lib.rhd_surrogate_save
+    load.restype = save.restype = ctypes.c_int
+    load.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+    save.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+    out = ctypes.c_void_p()
+    assert load(str(tmp_path / "missing.bin").encode(), ctypes.byref(out)) == -7
+    bad = tmp_path / "bad.bin"
+    bad.write_bytes(b"NOTMLP!!" + bytes(24))
+    assert load(str(bad).encode(), ctypes.byref(out)) == -7
+    short = tmp_path / "short.bin"
+    import struct
+    short.write_bytes(b"RHDMLP1\0" + struct.pack("<iiiiq", 4, 12, 5, 0, 1000) + bytes(64))
+    assert load(str(short).encode(), ctypes.byref(out)) == -7
+    assert load(None, ctypes.byref(out)) == -1
+    assert load(str(bad).encode(), None) == -1
+    assert save(None, str(bad).encode()) == -1
+    assert rhd.strerror(-7) == "file error"
+
+
 def test_batched_entry_points_reject_null_arguments_without_a_device(lib):
     grids = (rhd.Grid * 1)()
     assert lib.rhd_source_update_batched(None, grids, 1, None) == -1

@@ -79,6 +79,28 @@ def test_fused_warm_start_matches_the_network(G, n):
     assert sur.error_flag() == 0
 
 
+def test_save_and_load_give_the_same_network(tmp_path):
+    """rhd_surrogate_save / rhd_surrogate_load: parameters, standardisation,
+    predictions and the warm start of the reloaded network are those of the
+    saved one, bit for bit."""
+    sur, p, norm = _random_net(16, 99)
+    path = str(tmp_path / "net.bin")
+    sur.save(path)
+    back = rhd.Surrogate.load(path)
+    assert (back.n_groups, back.n_features, back.n_outputs, back.n_params) == (
+        sur.n_groups, sur.n_features, sur.n_outputs, sur.n_params)
+    p1, n1 = sur.get_params()
+    p2, n2 = back.get_params()
+    assert torch.equal(p1, p2) and torch.equal(n1, n2)
+    x = torch.randn(300, sur.n_features, device="cuda")
+    assert torch.equal(sur.predict(x), back.predict(x))
+    w = synth.preset("mixed_128cube_ng16", n_cells=333, seed=4, device="cuda")
+    kw = dict(dt=w.dt, c_v=w.c_v, consts=w.consts)
+    e1, r1 = sur.warm_start(w.state, w.edges, w.law, **kw)
+    e2, r2 = back.warm_start(w.state, w.edges, w.law, **kw)
+    assert torch.equal(e1, e2) and torch.equal(r1, r2)
+
+
 @pytest.mark.parametrize("G,n", [(4, 256), (32, 1024)])
 def test_gradients_match_the_reference_network(G, n):
     sur, p, norm = _random_net(G, 5 + G)
