@@ -17,15 +17,20 @@ Parity status of each function (what pins it; the pins live in
 * ``ppl_free_slopes`` -- a hand-worked minmod example, the exact index of a
   binned powerlaw spectrum, the edge groups and undefined slopes.
 * ``group_terms`` -- the analytic Planck mean of the pulse opacity (Sec. 4.2.3,
-  the value printed there), chi_F = chi_0 in the PC case (after eq. chiDiff),
+  the value printed there, and its printed T^-3.5 law at 2e7 K), chi_F = chi_0 in the PC case (after eq. chiDiff),
   the diffusion-limit invariant of eq. Fdiff; with free slopes, chi_E and chi_B
   of a binned powerlaw spectrum against quadrature of eq. chiQ, and chi_E =
   chi_B for E_g = b_g.
 * ``closure`` -- the free-streaming and isotropic limits, trace = E.
 * ``arrowhead_solve`` -- dense LU on random arrowheads.
 * ``source_update`` -- conservation, v=0 equilibrium, grey reduction, linear
-  relaxation closed form, the Doppler-test equilibrium temperature printed in
-  Sec. 4.2.1, and the group flux spectrum against the angle integral eq. bbF.
+  relaxation closed form (also with a source term), the source entering only
+  as E_g^(t) + S_g (eq. FGFR), the Doppler-test equilibrium temperature
+  printed in Sec. 4.2.1, the moving equilibrium at c_hat = c and c/10, and the
+  group flux spectrum against the angle integral eq. bbF.
+
+``tests/test_oracle_mutants.py`` plants plausible mistakes in copies of this
+package and checks that each one fails a pin.
 * ``imex_step`` -- two ``source_update`` calls composed as eqs. imex1/imex2
   prescribe with no transport; pinned by the closed-form amplification
   1/(1 + lambda dt) of a small grey disequilibrium and by conservation.
