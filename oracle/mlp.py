@@ -21,9 +21,11 @@ the output error dY and each dZ before they multiply a matrix (the bias
 gradients use the unrounded values).  Everything else is FP64.
 
 Parity status: pinned by central finite differences of the FP64 loss
-(gradient), by the zero-weight special case (output = b4 exactly), by the
-exact-GELU comparison (the tanh form is within 5e-4 of z Phi(z)), and by
-hand-checked bfloat16 roundings (``tests/test_oracle_mlp.py``).
+(gradient), by the zero-weight special case (output = b4 exactly), by a
+single-path network evaluated by hand (layout, standardisation and its
+inverse), by the loss of a zero output, by the exact-GELU comparison (the tanh
+form is within 5e-4 of z Phi(z)), and by hand-checked bfloat16 roundings
+(``tests/test_oracle_mlp.py``).
 """
 from __future__ import annotations
 

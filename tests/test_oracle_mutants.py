@@ -2,12 +2,13 @@
 
 Each mutant below is one mistake of the kind a restatement of the paper can
 make: a dropped term, a wrong sign, a wrong index, a transposed operand, a
-wrong constant.  The test copies the oracle (C and Python) and the pin tests
-into a scratch tree, plants the mistake in the copy, rebuilds the copy's
-library there and runs the pins (``test_oracle_pins.py``,
-``test_oracle_ppl_free.py``) against it.  The unmodified copy must pass; every
-mutant must make at least one pin fail.  Nothing is written to the repository:
-the mistakes exist only in the scratch copies, on the CPU.
+wrong constant.  The test copies the oracle (C and Python, the update and the
+warm start's network) and the pin tests into a scratch tree, plants the
+mistake in the copy, rebuilds the copy's library there and runs the pins
+(``test_oracle_mlp.py``, ``test_oracle_ppl_free.py``, ``test_oracle_pins.py``)
+against it.  The unmodified copy must pass; every mutant must make at least
+one pin fail.  Nothing is written to the repository: the mistakes exist only
+in the scratch copies, on the CPU.
 """
 from __future__ import annotations
 
@@ -25,6 +26,7 @@ pytest.importorskip("mpmath")  # the pins that quadrature fixes need it
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 C = "oracle/rhd_oracle.c"
 PY = "oracle/__init__.py"
+MLP = "oracle/mlp.py"
 
 # (name, what the mistake breaks, [(file, exact text, replacement), ...])
 MUTANTS = [
@@ -134,6 +136,31 @@ MUTANTS = [
      [(PY, "dataclasses.replace(p, theta=0.5)", "dataclasses.replace(p, theta=1.0)")]),
     ("imex_average", "IMEX stage 2 started from U(n+1/2) instead of (U(n) + U(n+1/2))/2",
      [(PY, "mid[k] = 0.5 * (np.asarray(state[k], dtype=np.float64) + s1[k])", "mid[k] = s1[k]")]),
+    # the learned warm start's reference network
+    ("mlp_x_standardise", "network: features multiplied by their sd instead of divided",
+     [(MLP, "xn = (np.asarray(x, dtype=np.float64) - xm) / xs", "xn = (np.asarray(x, dtype=np.float64) - xm) * xs")]),
+    ("mlp_y_standardise", "network: targets multiplied by their sd instead of divided",
+     [(MLP, "(np.asarray(y, dtype=np.float64) - ym) / ys", "(np.asarray(y, dtype=np.float64) - ym) * ys")]),
+    ("mlp_destandardise", "network: raw output divided by the target sd",
+     [(MLP, "return out * ys + ym", "return out / ys + ym")]),
+    ("mlp_layout", "network: weight matrices read [in][out] instead of [out][in]",
+     [(MLP, "dtype=np.float64).reshape(o, i))", "dtype=np.float64).reshape(i, o).T)")]),
+    ("mlp_loss_sum", "network: loss summed instead of averaged (forward and backward alike)",
+     [(MLP, "return float(np.mean((out - yn) ** 2))", "return float(np.sum((out - yn) ** 2))"),
+      (MLP, "L = float(np.mean((out - yn) ** 2))", "L = float(np.sum((out - yn) ** 2))"),
+      (MLP, "dy = 2.0 * (out - yn) / (B * n_out)", "dy = 2.0 * (out - yn)")]),
+    ("mlp_gelu_constant", "network: cubic coefficient of the tanh GELU off by ten",
+     [(MLP, "np.tanh(k0 * (z + 0.044715 * z ** 3))", "np.tanh(k0 * (z + 0.0044715 * z ** 3))")]),
+    ("mlp_gelu_grad_term", "network: GELU derivative without the factor 3 of the cubic",
+     [(MLP, "(1.0 + 3.0 * 0.044715 * z * z)", "(1.0 + 0.044715 * z * z)")]),
+    ("mlp_gelu_grad_dropped", "network: backprop through the GELU without its derivative",
+     [(MLP, "dz = dh * gelu_grad(zs[l])", "dz = dh")]),
+    ("mlp_hidden_bias", "network: hidden-layer bias dropped in the forward pass",
+     [(MLP, "z = a @ r(Ws[l]).T + bs[l]", "z = a @ r(Ws[l]).T")]),
+    ("mlp_output_bias_grad", "network: output-bias gradient averaged instead of summed",
+     [(MLP, "gb[3] = dy.sum(0)", "gb[3] = dy.mean(0)")]),
+    ("mlp_bf16_ties", "network: bfloat16 ties rounded up instead of to even",
+     [(MLP, "r = ((u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000)", "r = ((u + 0x8000) & 0xFFFF0000)")]),
 ]
 
 _COPY = ["oracle/__init__.py", "oracle/mlp.py", "oracle/rhd_oracle.c", "oracle/rhd_oracle.h",
@@ -141,7 +168,7 @@ _COPY = ["oracle/__init__.py", "oracle/mlp.py", "oracle/rhd_oracle.c", "oracle/r
          "paper_2407_18304_gb300/build.py", "paper_2407_18304_gb300/rhd.py",
          "paper_2407_18304_gb300/synth.py"]
 # fast pins first: -x stops a caught mutant at its first failure
-_PINS = ["tests/test_oracle_ppl_free.py", "tests/test_oracle_pins.py"]
+_PINS = ["tests/test_oracle_mlp.py", "tests/test_oracle_ppl_free.py", "tests/test_oracle_pins.py"]
 
 
 def _sandbox(base: str, edits) -> str:
