@@ -64,8 +64,9 @@ def parse():
                     help="time the solver from the cold start (no learned warm start)")
     ap.add_argument("--sur-train-cells", type=int, default=1 << 21)
     ap.add_argument("--sur-epochs", type=int, default=4)
-    ap.add_argument("--cpu-sample", type=int, default=2048,
-                    help="cells of the workload the CPU oracle baseline solves")
+    ap.add_argument("--cpu-sample", type=int, default=6144,
+                    help="cells of the workload the CPU oracle baseline solves (about 15 s on "
+                         "16 cores at 64 groups)")
     return ap.parse_args()
 
 
@@ -547,7 +548,7 @@ def run_reference(args, ws, rank):
         return None
     import oracle as O
     from paper_2407_18304_gb300 import synth
-    m = min(args.cpu_sample // 4, 512)
+    m = min(args.cpu_sample // 12, 512)
     if args.workload == BATCHED:
         g = synth.batched_grids(1, seed=1000 * (18304 + 2), max_side=16)[0]
         m = min(m, g.n_cells)
