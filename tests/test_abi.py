@@ -1,7 +1,6 @@
 """The C ABI without a GPU: the library loads, exports every function that
 include/rhd.h declares, and rejects bad arguments before touching a device."""
 import ctypes
-import math
 import os
 import re
 

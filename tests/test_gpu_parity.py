@@ -335,7 +335,6 @@ def test_ragged_group_counts_in_the_warp_mapping(G, precision):
 def test_imex_step_matches_the_oracle_composition(precision):
     """rhd_imex_step (two implicit stages, theta = 1 then 1/2 from the average)
     against the oracle's composition of the same two stages."""
-    import dataclasses
     w = synth.preset("mixed_128cube_ng16", n_cells=400, seed=61)
     st = {k: (None if v is None else v.cuda().clone()) for k, v in w.state.items()}
     n = st["rho"].shape[0]

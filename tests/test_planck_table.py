@@ -10,7 +10,6 @@ import re
 import struct
 
 import numpy as np
-import pytest
 
 import oracle as O
 
