@@ -159,6 +159,10 @@ def _check(t: torch.Tensor, name: str, shape, dtype=torch.float64, device: str =
     if t.dtype != dtype or tuple(t.shape) != tuple(shape) or not t.is_contiguous():
         raise ValueError(f"{name}: expected contiguous {dtype} {tuple(shape)}, got "
                          f"{t.dtype} {tuple(t.shape)}")
+    # the library launches on the current device: another device's pointers would fault
+    if device == "cuda" and t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device} but the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
 
 
 def make_law(law, mode: int = PPL_FIXED, khat_g=None, alpha_g=None, temp_exponent=0.0, T_ref=1.0):
@@ -189,6 +193,10 @@ def _state(state: dict, G: int, n: int, gs: int, *, c_v: float, consts: dict, th
     rho = state["rho"]
     d = device
     _check(rho, "rho", (rho.shape[0],), device=d)
+    # the per-cell arrays hold rho.shape[0] cells; the library reads n of them
+    if not 0 <= n <= rho.shape[0] or gs < n:
+        raise ValueError(f"n_cells = {n} with {rho.shape[0]} cells per array and group "
+                         f"stride {gs}")
     _check(state["mom"], "mom", (3, rho.shape[0]), device=d)
     _check(state["egas"], "egas", (rho.shape[0],), device=d)
     _check(state["erad"], "erad", (G, gs), device=d)

@@ -142,3 +142,17 @@ def test_profile_hooks_without_a_device(lib):
     assert lib.rhd_profile_stop(ctypes.byref(n), ctypes.byref(ms)) == 0
     assert n.value == 0 and ms.value == 0.0
     assert lib.rhd_profile_stop(None, None) == -1
+
+
+def test_binding_rejects_more_cells_than_the_arrays_hold():
+    """The C library cannot see tensor lengths: the binding refuses a cell
+    count above the per-cell arrays' length or a group stride below it."""
+    w = synth.preset("tiny", n_cells=10)
+    kw = dict(c_v=w.c_v, consts=w.consts, theta=1.0, precision=rhd.FP64, closure=rhd.M1, tol=0.0,
+              tol_outer=0.0, max_newton=0, max_outer=0, status=None, iters=None, flags=0,
+              device="cpu")
+    for n, gs in ((11, 11), (10, 9), (-1, 10)):
+        with pytest.raises(ValueError, match="n_cells"):
+            rhd._state(w.state, w.n_groups, n, gs, **kw)
+    st = rhd._state(w.state, w.n_groups, 10, 10, **kw)
+    assert st.group_stride == 10 and st.rho == w.state["rho"].data_ptr()
