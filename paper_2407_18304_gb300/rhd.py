@@ -532,7 +532,9 @@ class Surrogate:
 
     def targets(self, before, after, edges, law, *, dt, c_v, consts, stream=None) -> torch.Tensor:
         sa, gr, lw, keep, n = self._grid(before, edges, law, dt, c_v, consts)
-        sb, _, _, keep2, _ = self._grid(after, edges, law, dt, c_v, consts)
+        sb, _, _, keep2, n_after = self._grid(after, edges, law, dt, c_v, consts)
+        if n_after != n:
+            raise ValueError(f"before holds {n} cells, after {n_after}")
         y = torch.empty((n, self.n_outputs), dtype=torch.float32, device=before["rho"].device)
         _raise(lib().rhd_surrogate_targets(self._h, ctypes.byref(sa), ctypes.byref(sb),
                                            ctypes.byref(gr), ctypes.byref(lw), float(dt), n,
@@ -572,6 +574,10 @@ class Surrogate:
         return loss, grad
 
     def train_step(self, x, y, first, batch, mult, add, lr, loss=None, stream=None) -> None:
+        _check(x, "x", (x.shape[0], self.n_features), torch.float32)
+        _check(y, "y", (x.shape[0], self.n_outputs), torch.float32)
+        if loss is not None:
+            _check(loss, "loss", (1,), torch.float32)
         _raise(lib().rhd_surrogate_train_step(self._h, _ptr(x), _ptr(y), x.shape[0], int(first),
                                               int(batch), int(mult), int(add), float(lr),
                                               _ptr(loss), self._s(stream)))
