@@ -79,8 +79,8 @@ def test_fp64_variants(closure, c_hat_frac, theta, with_src):
 
 
 def test_fp64_many_groups_and_pc_edges_at_zero_and_infinity():
-    """N_g = 100 (the widest compiled bucket) in PC mode with a first edge at
-    0 and a last edge at infinity."""
+    """N_g = 100 (the warp mapping's widest bucket, 65..128 groups) in PC mode
+    with a first edge at 0 and a last edge at infinity."""
     G = 100
     inner = synth.NU0 * np.logspace(-2.5, 2.5, G - 1)
     w = synth.preset("tiny", n_cells=200, seed=5)
