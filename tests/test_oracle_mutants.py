@@ -221,4 +221,4 @@ def test_unmodified_copy_passes_the_pins(outcomes):
 def test_planted_mistake_fails_a_pin(outcomes, name, what):
     rc, why = outcomes[name]
     assert rc != 0, f"no pin fails when the oracle has this mistake: {what}"
-    assert rc == 1, f"the pins did not run to a verdict ({rc}): {why}"
+    assert rc == 1, f"the pins did not run to completion (exit code {rc}): {why}"
