@@ -5,9 +5,9 @@ make: a dropped term, a wrong sign, a wrong index, a transposed operand, a
 wrong constant.  The test copies the oracle (C and Python, the update and the
 warm start's network) and the pin tests into a scratch tree, plants the
 mistake in the copy, rebuilds the copy's library there and runs the pins
-(``test_oracle_mlp.py``, ``test_oracle_ppl_free.py``, ``test_oracle_pins.py``)
-against it.  The unmodified copy must pass; every mutant must make at least
-one pin fail.  Nothing is written to the repository: the mistakes exist only
+(``test_oracle_properties.py``, ``test_oracle_mlp.py``,
+``test_oracle_ppl_free.py``, ``test_oracle_pins.py``) against it.  The
+unmodified copy must pass; every mutant must make at least one pin fail.  Nothing is written to the repository: the mistakes exist only
 in the scratch copies, on the CPU.
 """
 from __future__ import annotations
@@ -168,7 +168,8 @@ _COPY = ["oracle/__init__.py", "oracle/mlp.py", "oracle/rhd_oracle.c", "oracle/r
          "paper_2407_18304_gb300/build.py", "paper_2407_18304_gb300/rhd.py",
          "paper_2407_18304_gb300/synth.py"]
 # fast pins first: -x stops a caught mutant at its first failure
-_PINS = ["tests/test_oracle_mlp.py", "tests/test_oracle_ppl_free.py", "tests/test_oracle_pins.py"]
+_PINS = ["tests/test_oracle_properties.py", "tests/test_oracle_mlp.py", "tests/test_oracle_ppl_free.py",
+         "tests/test_oracle_pins.py"]
 
 
 def _sandbox(base: str, edits) -> str:
