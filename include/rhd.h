@@ -288,14 +288,25 @@ int rhd_surrogate_predict(rhd_surrogate_t *s, const float *x, int64_t n, float *
 /* 1 if a tensor-core wait of this surrogate ever timed out (results then invalid). */
 int rhd_surrogate_error(rhd_surrogate_t *s, int32_t *flag);
 /* Save the network (parameters and standardisation, not the Adam moments) to a
- * file: the 8 bytes "RHDMLP1\0", int32 n_groups, n_features, n_outputs, int64
- * n_params, then n_params FP32 parameters and 2 (n_features + n_outputs) FP32
- * standardisation values, all little-endian.  Synchronises the device.
- * RHD_EIO when the file cannot be written. */
+ * file: a 32-byte header -- the 8 bytes "RHDMLP1\0", int32 n_groups,
+ * n_features, n_outputs, int32 0 (padding), int64 n_params -- then n_params FP32
+ * parameters and 2 (n_features + n_outputs) FP32 standardisation values, all
+ * little-endian.  Synchronises the device.  RHD_EIO when the file cannot be
+ * written. */
 int rhd_surrogate_save(rhd_surrogate_t *s, const char *path);
+/* Save the training state as well: the same header with the magic "RHDMLP2\0",
+ * the same parameters and standardisation, then the Adam first and second
+ * moments (n_params FP32 each) and the int64 count of Adam steps taken.  A
+ * surrogate loaded from it continues training exactly where this one stands
+ * (the training step is deterministic: the same batches give the same
+ * parameters bit for bit).  Synchronises the device.  RHD_EIO when the file
+ * cannot be written. */
+int rhd_surrogate_checkpoint(rhd_surrogate_t *s, const char *path);
 /* Create a surrogate on the current device from a file rhd_surrogate_save wrote
- * (Adam moments zero, so training resumes with a fresh optimiser state).
- * RHD_EIO when the file cannot be read or its header or length does not match. */
+ * (Adam moments zero and step count 0, so training resumes with a fresh
+ * optimiser state) or rhd_surrogate_checkpoint wrote (moments and step count
+ * restored).  RHD_EIO when the file cannot be read or its header or length does
+ * not match. */
 int rhd_surrogate_load(const char *path, rhd_surrogate_t **out);
 /* rhd_source_update (FP64 or mixed form, from state->precision) started from the
  * surrogate's guess; groups->n_groups must equal the surrogate's.  Same results to

@@ -890,6 +890,8 @@ extern "C" int rhd_surrogate_warm_start(rhd_surrogate_t *s, const rhd_state_t *s
 namespace rhd {
 namespace {
 constexpr char kMlpMagic[8] = {'R', 'H', 'D', 'M', 'L', 'P', '1', '\0'};
+// the same, followed by the Adam moments and step count (rhd_surrogate_checkpoint)
+constexpr char kMlpMagicTrain[8] = {'R', 'H', 'D', 'M', 'L', 'P', '2', '\0'};
 
 struct MlpHeader {
   char magic[8];
@@ -924,6 +926,34 @@ extern "C" int rhd_surrogate_save(rhd_surrogate_t *s, const char *path) {
   return (std::fclose(f) == 0 && ok) ? RHD_OK : RHD_EIO;
 }
 
+extern "C" int rhd_surrogate_checkpoint(rhd_surrogate_t *s, const char *path) {
+  int rc = rhd::check_surrogate(s);
+  if (rc != RHD_OK) return rc;
+  if (!path) return RHD_EINVAL;
+  const size_t np = (size_t)s->nparam, nn = 2 * (size_t)(s->kin + s->nout);
+  std::vector<float> buf(3 * np + nn);
+  const cudaMemcpyKind D2H = cudaMemcpyDeviceToHost;
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(buf.data(), s->params, sizeof(float) * np, D2H) != cudaSuccess ||
+      cudaMemcpy(buf.data() + np, s->norm, sizeof(float) * nn, D2H) != cudaSuccess ||
+      cudaMemcpy(buf.data() + np + nn, s->am, sizeof(float) * np, D2H) != cudaSuccess ||
+      cudaMemcpy(buf.data() + 2 * np + nn, s->av, sizeof(float) * np, D2H) != cudaSuccess)
+    return RHD_ECUDA;
+  rhd::MlpHeader h{};
+  std::memcpy(h.magic, rhd::kMlpMagicTrain, 8);
+  h.n_groups = s->G;
+  h.n_features = s->kin;
+  h.n_outputs = s->nout;
+  h.n_params = s->nparam;
+  const int64_t step = s->step;
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return RHD_EIO;
+  const bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+                  std::fwrite(buf.data(), sizeof(float), buf.size(), f) == buf.size() &&
+                  std::fwrite(&step, sizeof(step), 1, f) == 1;
+  return (std::fclose(f) == 0 && ok) ? RHD_OK : RHD_EIO;
+}
+
 extern "C" int rhd_surrogate_load(const char *path, rhd_surrogate_t **out) {
   if (!path || !out) return RHD_EINVAL;
   *out = nullptr;
@@ -931,16 +961,21 @@ extern "C" int rhd_surrogate_load(const char *path, rhd_surrogate_t **out) {
   if (!f) return RHD_EIO;
   rhd::MlpHeader h{};
   const bool head_ok = std::fread(&h, sizeof(h), 1, f) == 1 &&
-                       std::memcmp(h.magic, rhd::kMlpMagic, 8) == 0 && h.n_groups >= 1 &&
+                       (std::memcmp(h.magic, rhd::kMlpMagic, 8) == 0 ||
+                        std::memcmp(h.magic, rhd::kMlpMagicTrain, 8) == 0) &&
+                       h.n_groups >= 1 &&
                        h.n_groups <= rhd::mlp::kMaxGS && h.n_params > 0 &&
                        h.n_features == 2 * h.n_groups + 4 && h.n_outputs == h.n_groups + 1;
   if (!head_ok) {
     std::fclose(f);
     return RHD_EIO;
   }
+  const bool train = std::memcmp(h.magic, rhd::kMlpMagicTrain, 8) == 0;
   const size_t np = (size_t)h.n_params, nn = 2 * (size_t)(h.n_features + h.n_outputs);
-  std::vector<float> buf(np + nn);
+  std::vector<float> buf(np + nn + (train ? 2 * np : 0));
+  int64_t step = 0;
   const bool body_ok = std::fread(buf.data(), sizeof(float), buf.size(), f) == buf.size() &&
+                       (!train || (std::fread(&step, sizeof(step), 1, f) == 1 && step >= 0)) &&
                        std::fgetc(f) == EOF;
   std::fclose(f);
   if (!body_ok) return RHD_EIO;
@@ -951,14 +986,18 @@ extern "C" int rhd_surrogate_load(const char *path, rhd_surrogate_t **out) {
     rhd_surrogate_destroy(s);
     return RHD_EIO;
   }
-  if (cudaMemcpy(s->params, buf.data(), sizeof(float) * np, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemcpy(s->norm, buf.data() + np, sizeof(float) * nn, cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(s->am, 0, sizeof(float) * np) != cudaSuccess ||
-      cudaMemset(s->av, 0, sizeof(float) * np) != cudaSuccess) {
+  const cudaMemcpyKind H2D = cudaMemcpyHostToDevice;
+  const bool moments_ok =
+      train ? (cudaMemcpy(s->am, buf.data() + np + nn, sizeof(float) * np, H2D) == cudaSuccess &&
+               cudaMemcpy(s->av, buf.data() + 2 * np + nn, sizeof(float) * np, H2D) == cudaSuccess)
+            : (cudaMemset(s->am, 0, sizeof(float) * np) == cudaSuccess &&
+               cudaMemset(s->av, 0, sizeof(float) * np) == cudaSuccess);
+  if (cudaMemcpy(s->params, buf.data(), sizeof(float) * np, H2D) != cudaSuccess ||
+      cudaMemcpy(s->norm, buf.data() + np, sizeof(float) * nn, H2D) != cudaSuccess || !moments_ok) {
     rhd_surrogate_destroy(s);
     return RHD_ECUDA;
   }
-  s->step = 0;
+  s->step = train ? step : 0;
   rc = rhd::publish(s, nullptr);
   if (rc == RHD_OK && cudaDeviceSynchronize() != cudaSuccess) rc = RHD_ECUDA;
   if (rc != RHD_OK) {

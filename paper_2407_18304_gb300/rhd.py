@@ -117,6 +117,7 @@ def lib() -> ctypes.CDLL:
             "rhd_source_update_warm": [_P, ctypes.POINTER(State), ctypes.POINTER(Groups),
                                        ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _P],
             "rhd_surrogate_save": [_P, ctypes.c_char_p],
+            "rhd_surrogate_checkpoint": [_P, ctypes.c_char_p],
             "rhd_surrogate_load": [ctypes.c_char_p, ctypes.POINTER(_P)],
             "rhd_surrogate_warm_start": [_P, ctypes.POINTER(State), ctypes.POINTER(Groups),
                                          ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _F, _F,
@@ -474,6 +475,11 @@ class Surrogate:
     def save(self, path: str) -> None:
         """``rhd_surrogate_save``: parameters and standardisation to a file."""
         _raise(lib().rhd_surrogate_save(self._h, os.fsencode(path)))
+
+    def checkpoint(self, path: str) -> None:
+        """``rhd_surrogate_checkpoint``: the network and its Adam state, so that
+        a surrogate loaded from the file resumes training bit for bit."""
+        _raise(lib().rhd_surrogate_checkpoint(self._h, os.fsencode(path)))
 
     @classmethod
     def load(cls, path: str) -> "Surrogate":

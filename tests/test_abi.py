@@ -156,3 +156,38 @@ def test_binding_rejects_more_cells_than_the_arrays_hold():
             rhd._state(w.state, w.n_groups, n, gs, **kw)
     st = rhd._state(w.state, w.n_groups, 10, 10, **kw)
     assert st.group_stride == 10 and st.rho == w.state["rho"].data_ptr()
+
+
+def test_checkpoint_files_are_parsed_before_a_device_is_touched(lib, tmp_path):
+    """Both file versions: a well-formed body gets past the reader (the call
+    then fails only for want of a device, not with RHD_EIO); a training-state
+    file without its step count, with a negative one or with a byte too many
+    is RHD_EIO; a null surrogate to rhd_surrogate_checkpoint is RHD_EINVAL."""
+    import struct
+    load, ck = lib.rhd_surrogate_load, lib.rhd_surrogate_checkpoint
+    load.restype = ck.restype = ctypes.c_int
+    load.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+    ck.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
+    out = ctypes.c_void_p()
+    G, nf, no, npar = 4, 12, 5, 10
+    nn = 2 * (nf + no)
+    body = struct.pack(f"<{npar + nn}f", *np.linspace(-1, 1, npar + nn))
+    moments = struct.pack(f"<{2 * npar}f", *np.linspace(0, 1, 2 * npar))
+
+    def write(name, magic, payload):
+        p = tmp_path / name
+        p.write_bytes(magic + struct.pack("<iiiiq", G, nf, no, 0, npar) + payload)
+        return str(p).encode()
+
+    v1 = write("v1.bin", b"RHDMLP1\0", body)
+    v2 = write("v2.bin", b"RHDMLP2\0", body + moments + struct.pack("<q", 7))
+    for path in (v1, v2):
+        rc = load(path, ctypes.byref(out))
+        assert rc not in (0, -7), rc
+    assert load(write("v2_nostep.bin", b"RHDMLP2\0", body + moments), ctypes.byref(out)) == -7
+    assert load(write("v2_neg.bin", b"RHDMLP2\0", body + moments + struct.pack("<q", -1)),
+                ctypes.byref(out)) == -7
+    assert load(write("v2_long.bin", b"RHDMLP2\0", body + moments + struct.pack("<q", 7) + b"x"),
+                ctypes.byref(out)) == -7
+    assert load(write("v1_as_v2.bin", b"RHDMLP2\0", body), ctypes.byref(out)) == -7
+    assert ck(None, v2) == -1
