@@ -12,6 +12,7 @@ import math
 
 import numpy as np
 import pytest
+import torch
 
 import oracle as O
 from paper_2407_18304_gb300 import rhd, synth
@@ -68,3 +69,27 @@ def test_extreme_group_counts(G, precision):
     else:
         for k in ("T", "egas", "erad"):
             assert e[k] < MIXED_BOUND, (k, e[k])
+
+
+@pytest.mark.parametrize("preset", ["mixed_128cube_ng16", "full_256cube_ng64"])
+@pytest.mark.parametrize("precision", [rhd.FP64, rhd.MIXED], ids=["fp64", "mixed"])
+def test_transparent_cells_are_left_unchanged(preset, precision):
+    """kappa_0 = 0: no group couples to the gas (tau = 0), so R_g = 0 in
+    eq. Rnew, the flux update of eq. fupdate returns F_g^t, and the
+    write-back leaves E_g, E_gas and rho v as they were; every third cell is
+    transparent, among ordinary cells (one cell per thread at 16 groups, a
+    warp per cell at 64)."""
+    w = synth.preset(preset, n_cells=301, seed=91)
+    st = {k: (None if v is None else v.clone()) for k, v in w.state.items()}
+    clear = np.arange(301) % 3 == 0
+    st["kappa0"][torch.as_tensor(clear)] = 0.0
+    w = synth.Workload(w.name, st, w.edges, w.law)
+    g = run_gpu(w, precision=precision)
+    s0 = synth.to_numpy(st)
+    assert np.all(g["status"][clear] == 0), np.bincount(g["status"][clear])
+    for k in ("egas", "erad", "frad", "mom"):
+        np.testing.assert_allclose(g[k][..., clear], s0[k][..., clear], rtol=4 * 2.0 ** -52, atol=0,
+                                   err_msg=k)
+    # the oracle agrees on the transparent cells
+    o = run_oracle(w)
+    np.testing.assert_allclose(o["erad"][:, clear], s0["erad"][:, clear], rtol=1e-14, atol=0)
