@@ -932,4 +932,4 @@ extern "C" const char *rhd_strerror(int code) {
   }
 }
 
-extern "C" int rhd_version(void) { return 100; }
+extern "C" int rhd_version(void) { return 200; }
