@@ -56,41 +56,29 @@ def gas_T(st, rho, c_v):
     return (st["egas"] - ke) / (rho * c_v)
 
 
-def errors(a: dict, b: dict, st0: dict, c: float, c_v: float, edges=None,
-           h_over_k: float = synth.H_PLANCK / synth.K_BOLTZ, floor: float = 0.0) -> dict:
+def errors(a: dict, b: dict, st0: dict, c: float, c_v: float, floor: float = 0.0) -> dict:
     """Per-output differences of result ``a`` against reference ``b``.
 
-    E_gas: relative to the reference value.  T = (E_gas - E_kin)/(rho c_v) is
-    derived by a cancellation that magnifies any error in E_gas by
-    k_T = max(1, E_tot/E_int), so its error is taken relative to T k_T ("T";
-    the plain relative error is "T_plain").  E_g: relative to the reference
-    E_g times its condition number 1 + x_g+ k_T, where x_g+ = h nu_g+ / (k_B T)
-    bounds d ln b_g / d ln T - 4 (a group in the Wien tail magnifies the
-    rounding-level uncertainty of T by x).  F_g: relative to (c E_g + |F_g|)
-    times the same factor (|F| <= c E is the scale of a group's flux).  rho v:
-    relative to |rho v| + sum_g E_g / c (the gas plus radiation momentum scale
-    of the cell).  ``floor`` adds floor * E_tot (c E_tot for F_g) to the E_g and
-    F_g scales: the paper's stopping tests bound every group's residual by
-    tol E_tot in absolute terms, so a group far below E_tot is fixed only to
-    that absolute level; callers pass floor = 10 tol / bound.  Returns the
-    maximum over cells and groups of each."""
+    E_gas and T = (E_gas - E_kin)/(rho c_v): relative to the reference
+    value.  E_g: relative to the reference
+    |E_g| + floor E_tot.  F_g: relative to c |E_g| + |F_g| + floor c E_tot
+    (|F| <= c E is the scale of a group's flux).  rho v: relative to
+    |rho v| + sum_g E_g / c (the gas plus radiation momentum scale of the
+    cell).  ``floor`` is the absolute level the paper's stopping tests fix:
+    they bound every group's residual by tol E_tot (Sec. 3, the test after
+    eq. matrix), so a group far below E_tot is determined only to that
+    absolute level; callers pass floor = 10 tol / bound.  "erad_plain" is
+    |dE_g| / |E_g| with no floor (reported, not a bound).  Returns the maximum
+    over cells and groups of each."""
     rho = st0["rho"]
     Ta, Tb = gas_T(a, rho, c_v), gas_T(b, rho, c_v)
     src = 0.0 if st0.get("src") is None else st0["src"].sum(0)
     etot = st0["egas"] + st0["erad"].sum(0) + src
-    cond = np.maximum(1.0, etot / (Tb * rho * c_v))
-    if edges is None:
-        kg = np.ones_like(b["erad"])
-    else:
-        up = np.asarray(edges, float)[1:, None]
-        xg = np.where(np.isinf(up), 0.0, h_over_k * np.where(np.isinf(up), 0.0, up) / Tb[None])
-        kg = 1.0 + xg * cond[None]
-    out = {"T": np.max(np.abs(Ta - Tb) / Tb / cond), "T_plain": np.max(np.abs(Ta - Tb) / Tb),
+    out = {"T": np.max(np.abs(Ta - Tb) / Tb),
            "egas": np.max(np.abs(a["egas"] - b["egas"]) / np.abs(b["egas"])),
-           "erad": np.max(np.abs(a["erad"] - b["erad"])
-                          / (np.abs(b["erad"]) * kg + floor * etot[None])),
+           "erad": np.max(np.abs(a["erad"] - b["erad"]) / (np.abs(b["erad"]) + floor * etot[None])),
            "erad_plain": np.max(np.abs(a["erad"] - b["erad"]) / np.abs(b["erad"]))}
-    fs = (c * np.abs(b["erad"]) + np.linalg.norm(b["frad"], axis=0)) * kg + floor * c * etot[None]
+    fs = c * np.abs(b["erad"]) + np.linalg.norm(b["frad"], axis=0) + floor * c * etot[None]
     out["frad"] = np.max(np.abs(a["frad"] - b["frad"]) / fs[None])
     ms = np.linalg.norm(b["mom"], axis=0) + b["erad"].sum(0) / c
     out["mom"] = np.max(np.abs(a["mom"] - b["mom"]) / ms[None])
@@ -120,6 +108,32 @@ def converged(*results) -> np.ndarray:
     ok = np.ones(len(results[0]["status"]), bool)
     for r in results:
         ok &= r["status"] == 0
+    return ok
+
+
+def agreed(label: str, *gpu: dict, oracle: dict, fallback_ok: bool = False,
+           max_left_out: float = MAX_UNCONVERGED, gpu_caps_ok: bool = False) -> np.ndarray:
+    """Cells on which every GPU result and the oracle converged, for the
+    element-wise comparison; prints how many cells each side left out.  A cell
+    may be left out only where one of the two methods stops at its iteration
+    cap; the GPU stopping at a cap (status 2) on a cell the oracle solves is a
+    failure, and the cells left out are at most MAX_UNCONVERGED of the sample.
+    ``fallback_ok``: status 1 (converged after the warm start's cold restart)
+    counts as converged.  ``max_left_out`` and ``gpu_caps_ok`` loosen the two
+    bounds for a stress workload whose caps are themselves the measurement."""
+    ok = oracle["status"] == 0
+    n = len(ok)
+    for r in gpu:
+        st = r["status"]
+        ok &= (st == 0) | ((st == 1) if fallback_ok else False)
+        capped = (st == 2) & (oracle["status"] == 0)
+        assert gpu_caps_ok or not capped.any(), (f"{label}: the GPU stopped at an iteration cap on "
+                                  f"{int(capped.sum())} cells the oracle converges")
+    hist = " ".join(f"gpu{j}={np.bincount(r['status'], minlength=4).tolist()}"
+                    for j, r in enumerate(gpu))
+    print(f"{label}: {int((~ok).sum())} of {n} cells left out; "
+          f"oracle={np.bincount(oracle['status'], minlength=4).tolist()} {hist}")
+    assert (~ok).mean() <= max_left_out, (label, int((~ok).sum()), n)
     return ok
 
 

@@ -14,7 +14,7 @@ import pytest
 import torch
 
 from paper_2407_18304_gb300 import rhd, synth
-from parity import MAX_UNCONVERGED, conservation, converged, errors, run_gpu, run_oracle, select
+from parity import MAX_UNCONVERGED, agreed, conservation, converged, errors, run_gpu, run_oracle, select
 
 pytestmark = pytest.mark.gpu
 
@@ -31,14 +31,13 @@ def test_mixed_matches_oracle_within_stated_bound(preset, n):
     g = run_gpu(w, precision=rhd.MIXED)
     o = run_oracle(w)
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    ok = agreed("mixed_matches_oracle_within_stated_bound", g, oracle=o)
     g, o, st0 = select(g, ok), select(o, ok), select(st0, ok)
-    e = errors(g, o, st0, w.consts["c"], w.c_v, w.edges, floor=DEFAULT_FLOOR)
+    e = errors(g, o, st0, w.consts["c"], w.c_v, floor=DEFAULT_FLOOR)
     print(preset, "mixed", " ".join(f"{k}={v:.2e}" for k, v in e.items()))
     ce, cm = conservation(g, st0, w.consts["c"], w.consts["c_hat"])
     assert ce < 64 * 2.0 ** -52 and cm < 64 * 2.0 ** -52
-    assert e["T"] < MIXED_BOUND and e["T_plain"] < MIXED_BOUND and e["erad"] < MIXED_BOUND
+    assert e["T"] < MIXED_BOUND and e["erad"] < MIXED_BOUND
     assert e["egas"] < MIXED_BOUND
 
 
@@ -48,8 +47,7 @@ def test_mixed_default_tests_on_the_energy_scale(preset, n):
     g = run_gpu(w, precision=rhd.MIXED)
     o = run_oracle(w)
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    ok = agreed("mixed_default_tests_on_the_energy_scale", g, oracle=o)
     g, o, st0 = select(g, ok), select(o, ok), select(st0, ok)
     c = w.consts["c"]
     etot = st0["egas"] + st0["erad"].sum(0)
@@ -66,10 +64,9 @@ def test_mixed_to_tight_tolerance_matches_fp64_accuracy(preset, n):
     g = run_gpu(w, precision=rhd.MIXED, **TIGHT)
     o = run_oracle(w)
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    ok = agreed("mixed_to_tight_tolerance_matches_fp64_accuracy", g, oracle=o)
     g, o, st0 = select(g, ok), select(o, ok), select(st0, ok)
-    e = errors(g, o, st0, w.consts["c"], w.c_v, w.edges, floor=TIGHT_FLOOR)
+    e = errors(g, o, st0, w.consts["c"], w.c_v, floor=TIGHT_FLOOR)
     print(preset, "mixed-tight", " ".join(f"{k}={v:.2e}" for k, v in e.items()))
     for k, v in e.items():
         if not k.endswith("_plain"):
@@ -105,5 +102,5 @@ def test_mixed_variants_and_invalid_cells():
                        **{k: v for k, v in kw.items()})
         sub = {k: v[..., okk] for k, v in g.items() if k in ("mom", "egas", "erad", "frad")}
         st0 = synth.to_numpy(synth.take_cells(st, torch.as_tensor(np.flatnonzero(okk))))
-        e = errors(sub, o, st0, w.consts["c"], w.c_v, w.edges, floor=DEFAULT_FLOOR)
+        e = errors(sub, o, st0, w.consts["c"], w.c_v, floor=DEFAULT_FLOOR)
         assert e["T"] < MIXED_BOUND and e["erad"] < MIXED_BOUND

@@ -24,7 +24,7 @@ import torch
 
 import oracle as O
 from paper_2407_18304_gb300 import rhd, synth
-from parity import MAX_UNCONVERGED, conservation, converged, errors, run_gpu, run_oracle, select
+from parity import MAX_UNCONVERGED, agreed, conservation, converged, errors, run_gpu, run_oracle, select
 
 pytestmark = pytest.mark.gpu
 
@@ -44,10 +44,9 @@ def test_fp64_matches_oracle(preset, n):
     g = run_gpu(w, **TIGHT)
     o = run_oracle(w)
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    ok = agreed("fp64_matches_oracle", g, oracle=o)
     g, o, st0 = select(g, ok), select(o, ok), select(st0, ok)
-    e = errors(g, o, st0, w.consts["c"], w.c_v, w.edges, floor=FLOOR)
+    e = errors(g, o, st0, w.consts["c"], w.c_v, floor=FLOOR)
     _report(preset, e)
     ce, cm = conservation(g, st0, w.consts["c"], w.consts["c_hat"])
     assert ce < 64 * 2.0 ** -52 and cm < 64 * 2.0 ** -52
@@ -66,10 +65,9 @@ def test_fp64_variants(closure, c_hat_frac, theta, with_src):
     g = run_gpu(w, closure=closure, c_hat=chat, theta=theta, **TIGHT)
     o = run_oracle(w, closure=closure, c_hat=chat, theta=theta)
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    ok = agreed("fp64_variants", g, oracle=o)
     g, o, st0 = select(g, ok), select(o, ok), select(st0, ok)
-    e = errors(g, o, st0, w.consts["c"], w.c_v, w.edges, floor=FLOOR)
+    e = errors(g, o, st0, w.consts["c"], w.c_v, floor=FLOOR)
     _report(f"variant {closure} {c_hat_frac} {theta} {with_src}", e)
     ce, cm = conservation(g, st0, w.consts["c"], chat)
     assert ce < 64 * 2.0 ** -52 and cm < 64 * 2.0 ** -52
@@ -91,10 +89,9 @@ def test_fp64_many_groups_and_pc_edges_at_zero_and_infinity():
     g = run_gpu(w, mode=rhd.PC, **TIGHT)
     o = run_oracle(w, mode=O.PC)
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    ok = agreed("fp64_many_groups_and_pc_edges_at_zero_and_infinity", g, oracle=o)
     g, o, st0 = select(g, ok), select(o, ok), select(st0, ok)
-    e = errors(g, o, st0, w.consts["c"], w.c_v, w.edges, floor=FLOOR)
+    e = errors(g, o, st0, w.consts["c"], w.c_v, floor=FLOOR)
     _report("pc100", e)
     for k, v in e.items():
         if not k.endswith("_plain"):
@@ -109,10 +106,9 @@ def test_fp64_per_group_table_and_temperature_dependent_opacity():
     g = run_gpu(w, khat_g=kg, alpha_g=ag, temp_exponent=-0.5, T_ref=synth.T_REF, **TIGHT)
     o = run_oracle(w, khat_g=kg, alpha_g=ag, temp_exponent=-0.5, T_ref=synth.T_REF)
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    ok = agreed("fp64_per_group_table_and_temperature_dependent_opacity", g, oracle=o)
     g, o, st0 = select(g, ok), select(o, ok), select(st0, ok)
-    e = errors(g, o, st0, w.consts["c"], w.c_v, w.edges, floor=FLOOR)
+    e = errors(g, o, st0, w.consts["c"], w.c_v, floor=FLOOR)
     _report("table+tdep", e)
     for k, v in e.items():
         if not k.endswith("_plain"):
@@ -127,8 +123,7 @@ def test_fp64_default_tolerance_on_the_energy_scale(preset, n):
     g = run_gpu(w)
     o = run_oracle(w)
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    ok = agreed("fp64_default_tolerance_on_the_energy_scale", g, oracle=o)
     g, o, st0 = select(g, ok), select(o, ok), select(st0, ok)
     c = w.consts["c"]
     etot = st0["egas"] + st0["erad"].sum(0)
@@ -147,10 +142,12 @@ def test_group_test_tightens_every_group():
     st0 = synth.to_numpy(w.state)
     g0 = run_gpu(w)
     g1 = run_gpu(w, flags=rhd.GROUP_TEST, max_outer=64)
-    ok = converged(g0, g1, o)
-    assert (~ok).mean() <= 4 * MAX_UNCONVERGED
-    e0 = errors(select(g0, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, w.edges)
-    e1 = errors(select(g1, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, w.edges)
+    # the per-group test is stricter than the paper's: within 64 outer passes
+    # a few stiff cells do not meet it (measured: 5 of 1000)
+    ok = agreed("group test", g0, g1, oracle=o, max_left_out=4 * MAX_UNCONVERGED,
+                gpu_caps_ok=True)
+    e0 = errors(select(g0, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v)
+    e1 = errors(select(g1, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v)
     print("group test: plain E_g error", e0["erad_plain"], "->", e1["erad_plain"])
     assert e1["erad_plain"] <= e0["erad_plain"]
     assert e1["erad"] < 1e-6
@@ -266,10 +263,10 @@ def test_fp64_slow_outer_iteration_cells_converge():
     assert (plain["status"] == 0).mean() >= 1 - MAX_UNCONVERGED
     g = run_gpu(w, theta=0.5, flags=rhd.FLUX_TEST, **TIGHT)
     assert (g["status"] == 0).all(), np.bincount(g["status"])
-    e = errors(g, o, st0, w.consts["c"], w.c_v, w.edges, floor=FLOOR)
+    e = errors(g, o, st0, w.consts["c"], w.c_v, floor=FLOOR)
     _report("slow-outer flux-test", e)
     ep = errors(select(plain, plain["status"] == 0), select(o, plain["status"] == 0),
-                select(st0, plain["status"] == 0), w.consts["c"], w.c_v, w.edges, floor=FLOOR)
+                select(st0, plain["status"] == 0), w.consts["c"], w.c_v, floor=FLOOR)
     _report("slow-outer paper test", ep)
     for k, v in e.items():
         if not k.endswith("_plain"):
@@ -289,17 +286,16 @@ def test_both_cell_mappings_give_the_same_results(precision):
     b = run_gpu(w, precision=precision, flags=rhd.CELL_PER_THREAD, **kw)
     o = run_oracle(w)
     st0 = synth.to_numpy(w.state)
-    ok = converged(a, b, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED
+    ok = agreed("both_cell_mappings_give_the_same_results", a, b, oracle=o)
     floor = FLOOR if precision == rhd.FP64 else 10 * 1e-11 / 1e-6
     bound = FP64_TOL if precision == rhd.FP64 else 1e-6
     for x, label in ((a, "warp"), (b, "thread")):
-        e = errors(select(x, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, w.edges,
+        e = errors(select(x, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v,
                    floor=floor)
         _report(f"{label} vs oracle", e)
         for k in ("T", "egas", "erad"):
             assert e[k] < bound, (label, k, e[k])
-    e = errors(select(a, ok), select(b, ok), select(st0, ok), w.consts["c"], w.c_v, w.edges,
+    e = errors(select(a, ok), select(b, ok), select(st0, ok), w.consts["c"], w.c_v,
                floor=floor)
     _report("warp vs thread", e)
     for k in ("T", "egas", "erad"):
@@ -317,10 +313,9 @@ def test_ragged_group_counts_in_the_warp_mapping(G, precision):
     g = run_gpu(w, precision=precision, **kw)
     o = run_oracle(w)
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    ok = agreed("ragged_group_counts_in_the_warp_mapping", g, oracle=o)
     floor = FLOOR if precision == rhd.FP64 else 10 * 1e-11 / 1e-6
-    e = errors(select(g, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, w.edges,
+    e = errors(select(g, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v,
                floor=floor)
     _report(f"G={G} prec={precision}", e)
     ce, cm = conservation(select(g, ok), select(st0, ok), w.consts["c"], w.consts["c_hat"])
@@ -350,10 +345,9 @@ def test_imex_step_matches_the_oracle_composition(precision):
                  h=w.consts["h"], k_B=w.consts["k_B"], c_v=w.c_v, dt=w.dt, max_iter=200)
     o = O.imex_step(synth.to_numpy(w.state), p, oracle_groups(w))
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED
+    ok = agreed("imex_step_matches_the_oracle_composition", g, oracle=o)
     floor = FLOOR if precision == rhd.FP64 else 10 * 1e-11 / 1e-6
-    e = errors(select(g, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, w.edges,
+    e = errors(select(g, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v,
                floor=floor)
     _report(f"imex prec={precision}", e)
     ce, cm = conservation(select(g, ok), select(st0, ok), w.consts["c"], w.consts["c_hat"])
@@ -364,3 +358,38 @@ def test_imex_step_matches_the_oracle_composition(precision):
     with pytest.raises(rhd.RhdError):
         rhd.imex_step(dict(st, src=torch.zeros_like(st["erad"])), w.edges, w.law, dt=w.dt,
                       c_v=w.c_v, consts=w.consts)
+
+
+# left_out: the share of cells that may stop at an iteration cap on either side.
+# Measured at 64 groups, |v| up to 0.1 c and c kappa dt up to 1e6: the oracle's
+# coupled Newton converges on 144 of 200 cells, the paper's inner/outer
+# iteration (FP64 form) on 65 (status 2 on the rest); at 16 groups every cell
+# converges on both sides.
+@pytest.mark.parametrize("G,n,v_max,tau_max,left_out", [(16, 600, 1e-2, 1e4, 0.02),
+                                                        (64, 200, 0.1, 1e6, 0.75)])
+@pytest.mark.parametrize("precision", [rhd.FP64, rhd.MIXED])
+def test_breakpoints_inside_groups(G, n, v_max, tau_max, left_out, precision):
+    """The piecewise-powerlaw opacity with its 8 breakpoints drawn log-uniformly
+    over the whole group range, so that jumps of up to 10^+-2 fall inside
+    groups and the slope fitted from the edge values (Sec. 2.2.2) becomes
+    steep.  Both sides' status counts are printed; on the cells both converge
+    every output matches (FP64: 1e-10 at the tight tolerances; mixed: 1e-6)."""
+    edges = synth.log_edges(G)
+    law = synth.random_law_interior(edges, np.random.default_rng(700 + G))
+    st = synth.make_state(n, edges, law, v_max=v_max, tau_max=tau_max, seed=700 + G)
+    w = synth.Workload(f"interior{G}", st, edges, law)
+    kw = TIGHT if precision == rhd.FP64 else {}
+    g = run_gpu(w, precision=precision, **kw)
+    o = run_oracle(w)
+    st0 = synth.to_numpy(w.state)
+    ok = agreed(f"interior breakpoints G={G} prec={precision}", g, oracle=o, max_left_out=left_out,
+                gpu_caps_ok=True)
+    bound = FP64_TOL if precision == rhd.FP64 else 1e-6
+    floor = FLOOR if precision == rhd.FP64 else 10 * 1e-11 / 1e-6
+    e = errors(select(g, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, floor=floor)
+    _report(f"interior G={G} prec={precision}", e)
+    ce, cm = conservation(g, st0, w.consts["c"], w.consts["c_hat"])
+    assert ce < 64 * 2.0 ** -52 and cm < 64 * 2.0 ** -52
+    keys = [k for k in e if not k.endswith("_plain")] if precision == rhd.FP64 else ["T", "egas", "erad"]
+    for k in keys:
+        assert e[k] < bound, (k, e[k])

@@ -10,7 +10,7 @@ import torch
 
 import oracle as O
 from paper_2407_18304_gb300 import rhd, synth
-from parity import MAX_UNCONVERGED, conservation, converged, errors, run_gpu, run_oracle, select
+from parity import MAX_UNCONVERGED, agreed, conservation, converged, errors, run_gpu, run_oracle, select
 
 pytestmark = pytest.mark.gpu
 
@@ -31,10 +31,9 @@ def _workload(preset, n, G=None, seed=41):
 
 def _check(w, g, o, name):
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    ok = agreed("_check", g, oracle=o)
     g, o, st0 = select(g, ok), select(o, ok), select(st0, ok)
-    e = errors(g, o, st0, w.consts["c"], w.c_v, w.edges, floor=FLOOR)
+    e = errors(g, o, st0, w.consts["c"], w.c_v, floor=FLOOR)
     print(name, " ".join(f"{k}={v:.2e}" for k, v in e.items()))
     ce, cm = conservation(g, st0, w.consts["c"], w.consts["c_hat"])
     assert ce < 64 * 2.0 ** -52 and cm < 64 * 2.0 ** -52

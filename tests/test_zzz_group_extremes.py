@@ -16,7 +16,7 @@ import torch
 
 import oracle as O
 from paper_2407_18304_gb300 import rhd, synth
-from parity import MAX_UNCONVERGED, conservation, converged, errors, run_gpu, run_oracle, select
+from parity import MAX_UNCONVERGED, agreed, conservation, converged, errors, run_gpu, run_oracle, select
 
 pytestmark = pytest.mark.gpu
 
@@ -52,10 +52,9 @@ def test_extreme_group_counts(G, precision):
     kw = TIGHT if precision == rhd.FP64 else {}
     g = run_gpu(w, precision=precision, mode=mode, **kw)
     st0 = synth.to_numpy(w.state)
-    ok = converged(g, o)
-    assert (~ok).mean() <= MAX_UNCONVERGED, (np.bincount(g["status"]), np.bincount(o["status"]))
+    ok = agreed("extreme_group_counts", g, oracle=o)
     floor = FLOOR if precision == rhd.FP64 else MIXED_FLOOR
-    e = errors(select(g, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, w.edges,
+    e = errors(select(g, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v,
                floor=floor)
     print(f"G={w.n_groups} {w.name} precision={precision}",
           " ".join(f"{k}={v:.2e}" for k, v in e.items()))
