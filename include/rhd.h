@@ -362,9 +362,9 @@ int rhd_profile_stop(int32_t *launches, double *total_ms);
  * (state->precision is ignored) but keeps the FP32 pass's warm start in a
  * file-scope device array of RHD_NOALLOC_BYTES that every GPU loading the
  * library holds until process exit.  The caller still passes all inputs and
- * outputs.  Size limit: n_cells * (16 * n_groups + 33) + 1024 <=
- * RHD_NOALLOC_BYTES (64 MiB; e.g. 64K cells at 64 groups); larger calls return
- * RHD_ESIZE and launch nothing.  The paper has no counterpart: this is a
+ * outputs.  Size limit: n_cells * (32 * n_groups + 33) + 1024 <=
+ * RHD_NOALLOC_BYTES (64 MiB; at most 32,247 cells at 64 groups, 123,133 at 16);
+ * larger calls return RHD_ESIZE and launch nothing.  The paper has no counterpart: this is a
  * deployment variant of the same kernels.  The first call on a device looks up
  * the array's device address (and initialises the constant tables), so make
  * it before any stream capture.  All calls share the one array and nothing in

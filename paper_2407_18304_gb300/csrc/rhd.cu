@@ -17,6 +17,7 @@
 #include "rhd_batched.cuh"
 #include "rhd_warp.cuh"
 #include "rhd_warp32.cuh"
+#include "rhd_correct.cuh"
 
 namespace rhd {
 namespace {
@@ -31,17 +32,22 @@ void *g_ws[kMaxDevices];
 size_t g_ws_bytes[kMaxDevices];
 
 size_t warm_bytes(int64_t n, int G) {
-  return (size_t)n * (4 * sizeof(double) + 1) + (size_t)n * G * 4 * sizeof(float) + 1024;
+  return (size_t)n * (4 * sizeof(double) + 1) + (size_t)n * G * 8 * sizeof(float) + 1024;
 }
 
-// Carve the warm-start arrays out of a workspace starting at p.
+// Carve the warm-start arrays out of a workspace starting at p: E_int and
+// momentum (FP64), the FP32 iterate R_g / E_tot and F_g / (c E_tot), the
+// correction step in the same layout, the FP32 iteration counts.  The
+// WarmStart leaves the step out (ur = uf = null) until a correction has run.
 void carve(char *p, int64_t n, int G, WarmOut *w, WarmStart *r) {
   w->eint = reinterpret_cast<double *>(p);
   w->mom = w->eint + n;
   w->r = reinterpret_cast<float *>(w->mom + 3 * n);
   w->f = w->r + (size_t)G * n;
-  w->nit = reinterpret_cast<uint8_t *>(w->f + (size_t)3 * G * n);
-  *r = WarmStart{w->eint, w->mom, w->r, w->f, w->nit, 1};
+  w->ur = w->f + (size_t)3 * G * n;
+  w->uf = w->ur + (size_t)G * n;
+  w->nit = reinterpret_cast<uint8_t *>(w->uf + (size_t)3 * G * n);
+  *r = WarmStart{w->eint, w->mom, w->r, w->f, w->nit, 1, nullptr, nullptr};
 }
 
 int workspace(int64_t n, int G, WarmOut *w, WarmStart *r) {
@@ -348,28 +354,56 @@ void launch_fp32_passes(const KParams &kp, const WarmOut &wo, const WarmStart &S
   warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo, S);
 }
 
+template <int L, int GPL>
+void launch_correct_k(const KParams &kp, const WarmOut &wo, int sms, cudaStream_t st) {
+  const int threads = 128;
+  const size_t smem = table_bytes(kp.G);
+  const int b = persistent_blocks(correct_warp_kernel<L, GPL>, smem, sms, kp.n * L, threads);
+  correct_warp_kernel<L, GPL><<<b, threads, smem, st>>>(kp, wo, CorrOut{wo.ur, wo.uf});
+}
+
+// The correction step after the FP32 passes (rhd_correct.cuh): L lanes per
+// cell with GPL groups each (up to 128 groups); returns the warm start of the
+// FP64 passes, with the step when it ran.
+WarmStart launch_correct(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int sms,
+                         cudaStream_t st) {
+  WarmStart w = wi;
+  if (kp.G > 128) return w;
+  if (kp.G <= 16) launch_correct_k<8, 2>(kp, wo, sms, st);
+  else if (kp.G <= 32) launch_correct_k<16, 2>(kp, wo, sms, st);
+  else if (kp.G <= 64) launch_correct_k<32, 2>(kp, wo, sms, st);
+  else launch_correct_k<32, 4>(kp, wo, sms, st);
+  w.ur = wo.ur;
+  w.uf = wo.uf;
+  return w;
+}
+
 template <int MAXG>
 int launch_mixed(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int sms,
                  cudaStream_t st) {
-  const WarmStart none{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+  const WarmStart none{nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
   if (kp.mode == RHD_PPL_FREE) {  // no FP32 passes for free slopes: FP64 from the cold start
     launch_fp64_passes(kp, none, sms, st);
     return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
   }
   launch_fp32_passes<MAXG>(kp, wo, none, sms, st);
-  launch_fp64_passes(kp, wi, sms, st);
+  launch_fp64_passes(kp, launch_correct(kp, wo, wi, sms, st), sms, st);
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
 }
 
 // Solve from a warm start already in the workspace (wo/wi view the same
 // arrays): FP64 form directly from it; mixed form FP32 passes from it (in
-// place), then the FP64 passes from their result.  Cold restart on failure.
+// place), the correction step, then the FP64 passes from their result.  Cold
+// restart on failure.
 template <int MAXG>
 int launch_warm_g(const KParams &kp, int precision, const WarmOut &wo, const WarmStart &wi,
                   int sms, cudaStream_t st) {
-  if (precision == RHD_MIXED && kp.mode != RHD_PPL_FREE)
+  if (precision == RHD_MIXED && kp.mode != RHD_PPL_FREE) {
     launch_fp32_passes<MAXG>(kp, wo, wi, sms, st);
-  launch_fp64_passes(kp, wi, sms, st);
+    launch_fp64_passes(kp, launch_correct(kp, wo, wi, sms, st), sms, st);
+  } else {
+    launch_fp64_passes(kp, wi, sms, st);
+  }
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
 }
 
@@ -382,7 +416,7 @@ int launch_warm(const KParams &kp, int precision, const WarmOut &wo, const WarmS
 template <int MAXG>
 int launch_g(const KParams &kp, int precision, int sms, cudaStream_t st) {
   if (precision == RHD_FP64) {
-    const WarmStart cold{nullptr, nullptr, nullptr, nullptr, nullptr, 0};
+    const WarmStart cold{nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
     launch_fp64_passes(kp, cold, sms, st);
   } else {
     WarmOut wo;

@@ -190,6 +190,19 @@ __device__ __forceinline__ float scaled_f(double x, int sh) {
   return __int_as_float((int)(sign | ((unsigned)fe << 23) | frac));
 }
 
+// A float widened to double from its bit pattern (exact for normal numbers;
+// zero and FP32 subnormals give 0, which at E_tot scale is below FP64's
+// resolution of the sums they enter).  No FP64 instruction.
+__device__ __forceinline__ double f2d(float f) {
+  const int b = __float_as_int(f);
+  const int e = (b >> 23) & 0xFF;
+  if (e == 0) return 0.0;
+  const unsigned sign = (unsigned)b & 0x80000000u;
+  const unsigned man = (unsigned)b & 0x7FFFFFu;
+  const unsigned he = e == 0xFF ? 0x7FFu : (unsigned)(e + 896);
+  return __hiloint2double((int)(sign | (he << 20) | (man >> 3)), (int)((man & 7u) << 29));
+}
+
 // A group energy that carries a feature: positive, finite, not below about
 // 1.3e-290 (exponent field >= 60), tested on the bits.
 __device__ __forceinline__ bool usable_energy(double x) {

@@ -1,0 +1,510 @@
+// rhd_correct.cuh -- the correction step of the mixed form: one FP64
+// evaluation of the residual of the fully coupled per-cell system at the FP32
+// passes' result, and one Newton step on that system whose Jacobian is built
+// and solved in FP32 (iterative refinement: the residual carries the FP64
+// accuracy, the Jacobian only the rate).
+//
+// The paper's inner/outer iteration (Sec. 3) converges to the root of
+//   F_G   = E_int + E_kin(m) - E_gas^t + (c/c_hat) sum_g R_g               (eq. FGFR)
+//   F_R,g = E_g(T, R_g, w_g) - (E_g^t + S_g) - R_g,   E_g from eq. Rnew,
+//           w_g = v.F_g / c^2                                             (eq. FGFR)
+//   F_F,g = F_g - base_g - kap_g v.P_g(E_g^t + S_g + R_g, F_g)            (eq. fupdate,
+//           base_g = (F_g^t + c_hat theta dt v (chi_B b_g - delta chi_g/3)) / (1 + c_hat theta dt chi_F),
+//           kap_g = c_hat theta dt (1 + alpha) chi_E / (1 + c_hat theta dt chi_F))   eq. numF1)
+// with the momentum of eq. vupdate, m = m^t - (c c_hat)^-1 sum_g (F_g - F_g^t),
+// v = m / rho, and T = E_int / (rho c_v).  Unknowns: E_int, R_g, F_g.
+//
+// Its Jacobian is bordered block-diagonal: a group's four unknowns (R_g, F_g)
+// couple to one another, and to the other groups only through E_int (by T)
+// and through v (by the sum of the fluxes).  So each group's 4x4 block is
+// eliminated with its five right-hand sides (the residual, the E_int column,
+// the three v columns): u_g = p_g + q_g x + S_g beta.  The sums over the groups
+// turn the E_int row and the momentum relation into a 4x4 system for
+// (x, beta); then every group's step follows -- O(N_g) work, like the
+// paper's arrowhead elimination of eq. matrix.
+//
+// Scaled FP32 variables: x = dE_int / E_tot, r_g = dR_g / E_tot,
+// f_g = dF_g / (c E_tot), beta = dv / c; residual rows F_G and F_R,g divided
+// by E_tot, F_F,g by c E_tot.  The step is left in a second workspace (U,
+// FP32) beside the FP32 iterate (W); the FP64 passes start from W + U, which
+// together carry the corrected iterate to FP64 precision.
+#pragma once
+#include "rhd_warp32.cuh"
+
+namespace rhd {
+
+// The correction step's output: per cell-group the step (r_g, f_g); zero for
+// a cell the step is not taken for.
+struct CorrOut {
+  float *ur;  // [G][n]
+  float *uf;  // [3][G][n]
+};
+
+// FP32 copy of the Planck polynomials cut to degree kDeg32 (as the FP32
+// passes use them), loaded into shared memory by all threads.
+__device__ __forceinline__ void load_planck32(const GroupTable &tab, float *pf) {
+  using namespace planck_table;
+  for (int t = threadIdx.x; t < kPlanckF; t += blockDim.x) {
+    const int k = t / kSeg, s = t % kSeg;
+    const int src = k <= kDeg32 ? k * kSeg + s : (kDeg + 1 + (k - kDeg32 - 1)) * kSeg + s;
+    pf[t] = (float)tab.pc[src];
+  }
+}
+
+// The closure in units with c = 1 (E, F / c, v / c): v.P, M = d(v.P)/dF at
+// fixed E, dE = d(v.P)/dE at fixed F, and P itself (d(v.P)/dv).  M1 as in
+// closure_vP_jac (Levermore's chi(f), f held at 1); Eddington P = E/3 I.
+__device__ __forceinline__ void closure_full32(int closure, float E, const float F[3],
+                                               const float v[3], float vP[3], float M[9],
+                                               float Pm[9], float dE[3]) {
+  const float fn2 = F[0] * F[0] + F[1] * F[1] + F[2] * F[2];
+  if (closure != RHD_M1 || !(E > 0.0f) || !(fn2 > 0.0f)) {
+    const float e3 = E * (1.0f / 3.0f);
+    for (int k = 0; k < 3; ++k) {
+      vP[k] = e3 * v[k];
+      dE[k] = v[k] * (1.0f / 3.0f);
+    }
+    for (int k = 0; k < 9; ++k) {
+      M[k] = 0.0f;
+      Pm[k] = (k % 4 == 0) ? e3 : 0.0f;
+    }
+    return;
+  }
+  const float fn = sqrtf(fn2), inv = 1.0f / fn;
+  float f = fn / E;
+  const bool held = f > 1.0f;
+  if (held) f = 1.0f;
+  const float f2 = f * f;
+  const float sq = sqrtf(4.0f - 3.0f * f2), num = 3.0f + 4.0f * f2, den = 5.0f + 2.0f * sq;
+  const float chi = num / den;
+  const float dchi = held ? 0.0f : (8.0f * f * den + 6.0f * f * num / sq) / (den * den);
+  const float iso = 0.5f * (1.0f - chi), dir = 0.5f * (3.0f * chi - 1.0f);
+  const float n[3] = {F[0] * inv, F[1] * inv, F[2] * inv};
+  const float vn = v[0] * n[0] + v[1] * n[1] + v[2] * n[2];
+  const float a = -0.5f * dchi, b = 1.5f * dchi * vn, e = E * dir * inv;
+  // dE: d/dE of E (iso v + dir vn n) at fixed F, with df/dE = -f/E
+  const float ie = iso + 0.5f * f * dchi, de = dir - 1.5f * f * dchi;
+  for (int r = 0; r < 3; ++r) {
+    vP[r] = E * (iso * v[r] + dir * vn * n[r]);
+    dE[r] = ie * v[r] + de * vn * n[r];
+    for (int q = 0; q < 3; ++q) {
+      const float id = r == q ? 1.0f : 0.0f;
+      M[3 * r + q] = a * v[r] * n[q] + b * n[r] * n[q] +
+                     e * (n[r] * (v[q] - vn * n[q]) + vn * (id - n[r] * n[q]));
+      Pm[3 * r + q] = E * (iso * id + dir * n[r] * n[q]);
+    }
+  }
+}
+
+// One group's block of the bordered system, u = (r_g, f_g):
+//   [A00 A0^T] u = rhs - c x - B beta
+//   [Af0 Aff ]
+// eliminated through its (r_g) row (A00 <= -1 never vanishes): the 3x3 Schur
+// complement K = Aff - Af0 A0^T / A00 is inverted by its adjugate.  Output:
+// u = p + q x + S beta (S row-major 4x3).  false when K is singular.
+struct GBlock {
+  float p[4], q[4], S[12];
+};
+
+__device__ __forceinline__ bool group_block(float A00, const float A0[3], const float Af0[3],
+                                            const float Aff[9], float c0, const float cF[3],
+                                            const float B0[3], const float BF[9], float rhs0,
+                                            const float rhsF[3], GBlock &o) {
+  const float ia = 1.0f / A00;
+  float K[9];
+  for (int r = 0; r < 3; ++r)
+    for (int q = 0; q < 3; ++q) K[3 * r + q] = Aff[3 * r + q] - Af0[r] * A0[q] * ia;
+  const float k00 = K[4] * K[8] - K[5] * K[7], k01 = K[2] * K[7] - K[1] * K[8],
+              k02 = K[1] * K[5] - K[2] * K[4];
+  const float k10 = K[5] * K[6] - K[3] * K[8], k11 = K[0] * K[8] - K[2] * K[6],
+              k12 = K[2] * K[3] - K[0] * K[5];
+  const float k20 = K[3] * K[7] - K[4] * K[6], k21 = K[1] * K[6] - K[0] * K[7],
+              k22 = K[0] * K[4] - K[1] * K[3];
+  const float det = K[0] * k00 + K[1] * k10 + K[2] * k20;
+  if (!(fabsf(det) > 1e-30f) || !isfinite(det)) return false;
+  const float id = 1.0f / det;
+  const float Ki[9] = {k00 * id, k01 * id, k02 * id, k10 * id, k11 * id,
+                       k12 * id, k20 * id, k21 * id, k22 * id};
+  auto col = [&](float t0, const float tF[3], float &o0, float o1[3]) {
+    // solve [A00 A0; Af0 Aff] y = (t0, tF)
+    const float s[3] = {tF[0] - Af0[0] * t0 * ia, tF[1] - Af0[1] * t0 * ia,
+                        tF[2] - Af0[2] * t0 * ia};
+    for (int r = 0; r < 3; ++r) o1[r] = Ki[3 * r] * s[0] + Ki[3 * r + 1] * s[1] + Ki[3 * r + 2] * s[2];
+    o0 = (t0 - A0[0] * o1[0] - A0[1] * o1[1] - A0[2] * o1[2]) * ia;
+  };
+  float y1[3];
+  col(rhs0, rhsF, o.p[0], y1);
+  o.p[1] = y1[0];
+  o.p[2] = y1[1];
+  o.p[3] = y1[2];
+  const float ncF[3] = {-cF[0], -cF[1], -cF[2]};
+  col(-c0, ncF, o.q[0], y1);
+  o.q[1] = y1[0];
+  o.q[2] = y1[1];
+  o.q[3] = y1[2];
+  for (int l = 0; l < 3; ++l) {
+    const float nB[3] = {-BF[l], -BF[3 + l], -BF[6 + l]};
+    col(-B0[l], nB, o.S[l], y1);
+    o.S[3 + l] = y1[0];
+    o.S[6 + l] = y1[1];
+    o.S[9 + l] = y1[2];
+  }
+  return true;
+}
+
+// The FP32 Jacobian block of one group at the iterate, with the FP64
+// residual (scaled) as right-hand side.  Edge values (P or Q, D, x dD/dx) at
+// the lower (L) and upper (U) edge at the iterate's T; aT4s = a_R T^4 / E_tot,
+// dTs = a_R T^3 / (rho c_v) (d/dx of the scaled Planck terms per unit x);
+// tau = c_hat theta dt chi_E (0: the group is uncoupled); Eg = E_g / E_tot;
+// f = F_g / (c E_tot); be = v / c.
+__device__ __forceinline__ bool group_jac32(int closure, float tau, float a, float rm, float rp,
+                                            float pqL, bool lowL, float dL, float eL, float pqU,
+                                            bool lowU, float dU, float eU, float aT4s, float dTs,
+                                            float Eg, const float f[3], const float be[3],
+                                            float rR, const float rF[3], GBlock &o) {
+  const float rhsF[3] = {-rF[0], -rF[1], -rF[2]};
+  if (!(tau > 0.0f)) {  // uncoupled: R_g = 0, F_g = F_g^t, no coupling
+    const float z3[3] = {0.0f, 0.0f, 0.0f};
+    const float I9[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    const float z9[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    return group_block(-1.0f, z3, z3, I9, 0.0f, z3, z3, z9, -rR, rhsF, o);
+  }
+  const float dP = band_fp32(pqL, lowL, pqU, lowU);
+  const float dD = dU - dL;
+  const float b = aT4s * dP;
+  const float dbs = dTs * (4.0f * dP - dD);
+  float dq;
+  const float q = chiF_ratio<float>(b, aT4s, dD, a, rm, rp, dL, dU, dbs, dTs, eL, eU, dq);
+  const float X = rp * dU - rm * dL;
+  const float s = b - aT4s * X * (1.0f / 3.0f);                       // (chi_B b - dchi/3) / chi_E
+  const float ds = dbs - dTs * (4.0f * X - (rp * eU - rm * eL)) * (1.0f / 3.0f);
+  const float inv = 1.0f / (1.0f + tau * q);
+  const float kap = (1.0f + a) * tau * inv;
+  const float a1 = (1.0f + a) * q;
+  float vP[3], M[9], Pm[9], dE[3];
+  closure_full32(closure, Eg, f, be, vP, M, Pm, dE);
+  const float w = be[0] * f[0] + be[1] * f[1] + be[2] * f[2];
+  const float A0[3] = {a1 * be[0], a1 * be[1], a1 * be[2]};
+  const float Af0[3] = {-kap * dE[0], -kap * dE[1], -kap * dE[2]};
+  float Aff[9], BF[9];
+  const float ts = inv * tau * s;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 3; ++c) {
+      Aff[3 * r + c] = (r == c ? 1.0f : 0.0f) - kap * M[3 * r + c];
+      BF[3 * r + c] = -((r == c ? ts : 0.0f) + kap * Pm[3 * r + c]);
+    }
+  const float c0 = dbs + (1.0f + a) * dq * w;
+  // d F_F / dx: through chi_F (q) in both the denominator and kap, and
+  // through the source term; base + kap v.P is F_g at the root
+  const float cF[3] = {inv * tau * (dq * f[0] - be[0] * ds), inv * tau * (dq * f[1] - be[1] * ds),
+                       inv * tau * (dq * f[2] - be[2] * ds)};
+  const float B0[3] = {a1 * f[0], a1 * f[1], a1 * f[2]};
+  return group_block(-(1.0f + 1.0f / tau), A0, Af0, Aff, c0, cF, B0, BF, -rR, rhsF, o);
+}
+
+// The 4x4 system in (x, beta) after the groups are eliminated:
+//   (1 + cr sum q_R) x + (m c / E_tot + cr sum S_R) . beta = -F_G / E_tot - cr sum p_R
+//   mu sum q_F x + (I + mu sum S_F) beta = -mu sum p_F,   mu = E_tot / (rho c c_hat)
+// sums: [0] p_R, [1] q_R, [2..4] S_R, [5..7] p_F, [8..10] q_F, [11..19] S_F.
+// Gaussian elimination with partial pivoting; false if singular.
+__device__ __forceinline__ bool global_solve(const float s[20], float rG, float cr,
+                                             const float mc[3], float mu, float &x,
+                                             float beta[3]) {
+  float A[4][5];
+  A[0][0] = 1.0f + cr * s[1];
+  for (int k = 0; k < 3; ++k) A[0][1 + k] = mc[k] + cr * s[2 + k];
+  A[0][4] = -rG - cr * s[0];
+  for (int r = 0; r < 3; ++r) {
+    A[1 + r][0] = mu * s[8 + r];
+    for (int k = 0; k < 3; ++k) A[1 + r][1 + k] = (r == k ? 1.0f : 0.0f) + mu * s[11 + 3 * r + k];
+    A[1 + r][4] = -mu * s[5 + r];
+  }
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < 4; ++r)
+      if (fabsf(A[r][c]) > fabsf(A[piv][c])) piv = r;
+    if (!(fabsf(A[piv][c]) > 0.0f)) return false;
+    if (piv != c)
+      for (int k = 0; k < 5; ++k) {
+        const float t = A[c][k];
+        A[c][k] = A[piv][k];
+        A[piv][k] = t;
+      }
+    const float ip = 1.0f / A[c][c];
+    for (int r = c + 1; r < 4; ++r) {
+      const float fct = A[r][c] * ip;
+      for (int k = c; k < 5; ++k) A[r][k] -= fct * A[c][k];
+    }
+  }
+  float y[4];
+  for (int r = 3; r >= 0; --r) {
+    float t = A[r][4];
+    for (int k = r + 1; k < 4; ++k) t -= A[r][k] * y[k];
+    y[r] = t / A[r][r];
+  }
+  x = y[0];
+  beta[0] = y[1];
+  beta[1] = y[2];
+  beta[2] = y[3];
+  return isfinite(x) && isfinite(beta[0]) && isfinite(beta[1]) && isfinite(beta[2]);
+}
+
+// A step is taken only when it is small against the cell's energy scale: the
+// FP32 passes leave the iterate at FP32 accuracy, so a larger step means the
+// FP32 passes stopped at a cap, and the FP64 passes take the cell from W.
+constexpr float kMaxStep = 1e-2f;
+
+// The correction step with L lanes per cell (the layout of rhd_warp.cuh).
+// Reads the state and the FP32 iterate in W; writes the step to U and the
+// corrected E_int and momentum to W (FP64); a cell the step is not taken for
+// gets U = 0 and keeps W.
+template <int L, int GPL>
+__global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant__ KParams P,
+                                                           const WarmOut W, const CorrOut U) {
+  extern __shared__ double sm[];
+  __shared__ float pf[kPlanckF];
+  const GroupTable tab = build_table(P, sm);
+  load_planck32(tab, pf);
+  __syncthreads();
+  constexpr int NE = GPL + 1;
+  const int lane = threadIdx.x & 31, seg = lane / L, l = lane % L, lane0 = seg * L;
+  const unsigned mask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << lane0);
+  constexpr int CPW = 32 / L;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+  const int G = P.G;
+  const int64_t n = P.n;
+  const double c = P.c, tdt = P.c_hat * P.theta * P.dt;
+  const int src_lane = lane0 + (l + 1) % L;
+  for (int64_t i = warp * CPW + seg; i < n; i += nwarps * CPW) {
+    // ---- the cell and its FP32 iterate (an invalid cell or one without an
+    // iterate is left to the FP64 passes, which never read U for it)
+    const double Eint = W.eint[i];
+    const double rho = P.rho[i];
+    const double k0 = P.kappa0 ? P.kappa0[i] : 1.0;
+    if (!(Eint > 0.0) || !(rho > 0.0) || !isfinite(rho) || !isfinite(k0) || !(k0 >= 0.0))
+      continue;
+    const double m0[3] = {P.mom[0][i], P.mom[1][i], P.mom[2][i]};
+    const double eg0 = P.egas[i];
+    double E0[GPL], R[GPL], F[GPL][3], ft[GPL][3];
+    float rw[GPL], fw[GPL][3];
+    double sumE0 = 0.0;
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      const int g = l + L * j;
+      E0[j] = 0.0;
+      rw[j] = 0.0f;
+      for (int d = 0; d < 3; ++d) {
+        fw[j][d] = 0.0f;
+        ft[j][d] = 0.0;
+      }
+      if (g < G) {
+        const int64_t o = (int64_t)g * P.gs + i;
+        E0[j] = P.erad[o] + (P.src ? P.src[o] : 0.0);
+        sumE0 += E0[j];
+        const int64_t ow = (int64_t)g * n + i;
+        rw[j] = W.r[ow];
+        for (int d = 0; d < 3; ++d) {
+          ft[j][d] = P.frad[d][o];
+          fw[j][d] = W.f[(int64_t)d * G * n + ow];
+        }
+      }
+    }
+    sumE0 = seg_sum<L>(sumE0, mask);
+    const double Et = eg0 + P.cr * sumE0;
+    int shE;
+    const float imE = 1.0f / frexp_f(Et, shE);
+    const double fs = c * Et;
+    // ---- FP64 residual at the iterate (momentum from the fluxes, eq. vupdate)
+    double dF[3] = {0.0, 0.0, 0.0}, sumR = 0.0;
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      R[j] = f2d(rw[j]) * Et;
+      for (int d = 0; d < 3; ++d) {
+        F[j][d] = f2d(fw[j][d]) * fs;
+        if (l + L * j < G) dF[d] += F[j][d] - ft[j][d];
+      }
+      if (l + L * j < G) sumR += R[j];
+    }
+    for (int d = 0; d < 3; ++d) dF[d] = seg_sum<L>(dF[d], mask);
+    sumR = seg_sum<L>(sumR, mask);
+    const double irho = 1.0 / rho;
+    double m[3], v[3];
+    for (int d = 0; d < 3; ++d) {
+      m[d] = m0[d] - dF[d] * P.icc;
+      v[d] = m[d] * irho;
+    }
+    const double KE = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) * irho;
+    const double rcv = rho * P.c_v;
+    const double T = Eint / rcv;
+    double cs = rho * k0;
+    if (P.temp_exp != 0.0) cs *= pow(T / P.T_ref, P.temp_exp);
+    const double its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
+    const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
+    const double invT = 1.0 / T;
+    double pqE[NE], dE_[NE], eE[NE];
+    bool lowE[NE];
+#pragma unroll
+    for (int jj = 0; jj < NE; ++jj) {
+      const int e = l + L * jj;
+      if (jj == NE - 1 && G == L * GPL) {  // the top edge alone (see winner_step)
+        const double xg = tab.xe[G] * invT;
+        if (xg >= 40.0 && xg < HUGE_VAL) {
+          const double em = exp(-xg);
+          const double x2 = xg * xg;
+          pqE[jj] = kPlanckNorm * em * (x2 * xg + 3.0 * x2 + 6.0 * xg + 6.0);
+          dE_[jj] = kPlanckNorm * em * x2 * x2;
+          eE[jj] = 0.0;
+          lowE[jj] = false;
+          continue;
+        }
+      }
+      edge_tab(tab.pc, e <= G ? tab.xe[e] * invT : 1.0, pqE[jj], dE_[jj], eE[jj], lowE[jj]);
+    }
+    const double FG = Eint + KE - eg0 + P.cr * sumR;
+    float rR[GPL], rF[GPL][3];
+    const float imEc = imE * (float)P.ic;
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      const double pa = __shfl_sync(mask, pqE[j], src_lane), pb = __shfl_sync(mask, pqE[j + 1], src_lane);
+      const double da = __shfl_sync(mask, dE_[j], src_lane), db_ = __shfl_sync(mask, dE_[j + 1], src_lane);
+      const int la = __shfl_sync(mask, (int)lowE[j], src_lane),
+                lb = __shfl_sync(mask, (int)lowE[j + 1], src_lane);
+      const bool last = l == L - 1;
+      const double pqU = last ? pb : pa, dU = last ? db_ : da;
+      const bool lowU = (last ? lb : la) != 0;
+      const int g = l + L * j;
+      rR[j] = 0.0f;
+      rF[j][0] = rF[j][1] = rF[j][2] = 0.0f;
+      if (g >= G) continue;
+      const double dP = band_fp64(pqE[j], lowE[j], pqU, lowU);
+      const double dD = dU - dE_[j];
+      const double b = aT4 * dP;
+      const double a = tab.alpha[g], rm = tab.rm[g], rp = tab.rp[g];
+      const double q = chiF_q<double>(b, aT4, dD, a, rm, rp, dE_[j], dU);
+      const double dnx = aT4 * (rp * dU - rm * dE_[j]);
+      const double chiB = cs * tab.kbar[g];
+      const double Enew = E0[j] + R[j];
+      const double w = (v[0] * F[j][0] + v[1] * F[j][1] + v[2] * F[j][2]) * P.inv_c2;
+      const double FR = chiB > 0.0 ? b + (1.0 + a) * q * w - R[j] * its * tab.ikbar[g] - Enew
+                                   : -R[j];
+      // the flux residual F - (eq. numF1 at this iterate), as wouter_end forms it
+      double ca, kn, kd;
+      closure_vP_parts<double>(P.closure, c, P.ic, Enew, F[j][0], F[j][1], F[j][2], v[0], v[1],
+                               v[2], ca, kn, kd);
+      const double srcg = chiB * (b - dnx * (1.0 / 3.0));
+      const double den = 1.0 + tdt * chiB * q;
+      const double dk = den * kd;
+      double inv, kf;
+      if (dk > 1e-290) {
+        const double rr = 1.0 / dk;
+        inv = kd * rr;
+        kf = kn * den * rr;
+      } else {
+        inv = 1.0 / den;
+        kf = kn / kd;
+      }
+      const double kap = tdt * (1.0 + a) * chiB * inv;
+      double FF[3];
+      for (int d = 0; d < 3; ++d) {
+        const double vp = ca * v[d] + kf * F[j][d];
+        FF[d] = F[j][d] - ((ft[j][d] + tdt * v[d] * srcg) * inv + kap * vp);
+      }
+      rR[j] = scaled_f(FR, shE) * imE;
+      for (int d = 0; d < 3; ++d) rF[j][d] = scaled_f(FF[d], shE) * imEc;
+    }
+    const float rG = scaled_f(FG, shE) * imE;
+    // ---- FP32 Jacobian at the same iterate, group blocks, sums
+    const float Tf = scaled_f(T, 0);
+    const float invTf = 1.0f / Tf;
+    const float eint = scaled_f(Eint, shE) * imE;
+    const float aT4s = scaled_f(aT4, shE) * imE;
+    const float dTs = aT4s / eint;
+    int shV;
+    const float imV = 1.0f / frexp_f(rho * c, shV);
+    const float be[3] = {scaled_f(m[0], shV) * imV, scaled_f(m[1], shV) * imV,
+                         scaled_f(m[2], shV) * imV};
+    int et = 0;
+    const double tcs = tdt * cs;
+    const float mt = tcs > 0.0 ? frexp_f(tcs, et) : 0.0f;
+    float pqF[NE], dF_[NE], eF[NE];
+    bool lowF[NE];
+#pragma unroll
+    for (int jj = 0; jj < NE; ++jj) {
+      const int e = l + L * jj;
+      edge_tab32(pf, e <= G ? tab.xef[e] * invTf : 1.0f, pqF[jj], dF_[jj], eF[jj], lowF[jj]);
+    }
+    float sums[20];
+    for (int k = 0; k < 20; ++k) sums[k] = 0.0f;
+    GBlock blk[GPL];
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      const float pa = __shfl_sync(mask, pqF[j], src_lane), pb = __shfl_sync(mask, pqF[j + 1], src_lane);
+      const float da = __shfl_sync(mask, dF_[j], src_lane), db_ = __shfl_sync(mask, dF_[j + 1], src_lane);
+      const float ea = __shfl_sync(mask, eF[j], src_lane), eb = __shfl_sync(mask, eF[j + 1], src_lane);
+      const int la = __shfl_sync(mask, (int)lowF[j], src_lane),
+                lb = __shfl_sync(mask, (int)lowF[j + 1], src_lane);
+      const bool last = l == L - 1;
+      const int g = l + L * j;
+      if (g >= G) {
+        for (int k = 0; k < 4; ++k) blk[j].p[k] = blk[j].q[k] = 0.0f;
+        for (int k = 0; k < 12; ++k) blk[j].S[k] = 0.0f;
+        continue;
+      }
+      const float tau = mt * scaled_f(tab.kbar[g], -et);
+      const float Eg = scaled_f(E0[j], shE) * imE + rw[j];
+      ok = group_jac32(P.closure, tau, tab.alphaf[g], tab.rmf[g], tab.rpf[g], pqF[j], lowF[j],
+                       dF_[j], eF[j], last ? pb : pa, (last ? lb : la) != 0, last ? db_ : da,
+                       last ? eb : ea, aT4s, dTs, Eg, fw[j], be, rR[j], rF[j], blk[j]) && ok;
+      sums[0] += blk[j].p[0];
+      sums[1] += blk[j].q[0];
+      for (int k = 0; k < 3; ++k) {
+        sums[2 + k] += blk[j].S[k];
+        sums[5 + k] += blk[j].p[1 + k];
+        sums[8 + k] += blk[j].q[1 + k];
+        for (int c2 = 0; c2 < 3; ++c2) sums[11 + 3 * k + c2] += blk[j].S[3 * (1 + k) + c2];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 20; ++k) sums[k] = seg_sumf<L>(sums[k], mask);
+    // ---- (x, beta), then each group's step
+    const float mc[3] = {scaled_f(m[0] * c, shE) * imE, scaled_f(m[1] * c, shE) * imE,
+                         scaled_f(m[2] * c, shE) * imE};
+    const float mu = scaled_f(Et * irho * P.icc, 0);
+    float x = 0.0f, beta[3] = {0.0f, 0.0f, 0.0f};
+    ok = global_solve(sums, rG, (float)P.cr, mc, mu, x, beta) && ok;
+    ok = ok && fabsf(x) < kMaxStep;
+    float u[GPL][4];
+#pragma unroll
+    for (int j = 0; j < GPL; ++j)
+      for (int k = 0; k < 4; ++k) {
+        u[j][k] = blk[j].p[k] + blk[j].q[k] * x + blk[j].S[3 * k] * beta[0] +
+                  blk[j].S[3 * k + 1] * beta[1] + blk[j].S[3 * k + 2] * beta[2];
+        ok = ok && fabsf(u[j][k]) < kMaxStep;
+      }
+    ok = __all_sync(mask, ok);
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      const int g = l + L * j;
+      if (g >= G) continue;
+      const int64_t o = (int64_t)g * n + i;
+      U.ur[o] = ok ? u[j][0] : 0.0f;
+      for (int d = 0; d < 3; ++d) U.uf[(int64_t)d * G * n + o] = ok ? u[j][1 + d] : 0.0f;
+    }
+    if (ok && l == 0) {
+      W.eint[i] = Eint + f2d(x) * Et;
+      // sum_g f_g of the step, from the sums and (x, beta)
+      const double ms = Et / P.c_hat;
+      for (int d = 0; d < 3; ++d) {
+        const float sf = sums[5 + d] + sums[8 + d] * x + sums[11 + 3 * d] * beta[0] +
+                         sums[11 + 3 * d + 1] * beta[1] + sums[11 + 3 * d + 2] * beta[2];
+        W.mom[(int64_t)d * n + i] = m[d] - ms * f2d(sf);
+      }
+    }
+  }
+}
+
+}  // namespace rhd

@@ -494,6 +494,8 @@ struct WarmStart {
   const float *f;      // [3][G][n] F_g / (c E_tot)
   const uint8_t *nit;  // [n] FP32 Newton iterations
   int fallback;        // a cell whose warm-started solve fails is solved again from the cold start
+  const float *ur;     // [G][n] correction step of R_g / E_tot (rhd_correct.cuh), or null
+  const float *uf;     // [3][G][n] correction step of F_g / (c E_tot), or null
 };
 
 template <int MAXG>
@@ -509,6 +511,14 @@ __device__ __forceinline__ void apply_warm(const KParams &P, const WarmStart &W,
   const double fs = P.c * C.Etot;
   for (int g = 0; g < P.G; ++g) {
     const int64_t o = (int64_t)g * n + i;
+    if (W.ur) {  // the FP32 iterate plus the correction step, both exact in FP64
+      A.R[g] = fma(f2d(W.r[o]), C.Etot, f2d(W.ur[o]) * C.Etot);
+      for (int d = 0; d < 3; ++d) {
+        const int64_t od = (int64_t)d * P.G * n + o;
+        A.Fk[3 * g + d] = fma(f2d(W.f[od]), fs, f2d(W.uf[od]) * fs);
+      }
+      continue;
+    }
     A.R[g] = (double)W.r[o] * C.Etot;
     A.Fk[3 * g] = (double)W.f[o] * fs;
     A.Fk[3 * g + 1] = (double)W.f[(int64_t)P.G * n + o] * fs;

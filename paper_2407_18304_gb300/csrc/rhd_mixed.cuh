@@ -308,6 +308,7 @@ struct WarmOut {
   double *eint, *mom;
   float *r, *f;
   uint8_t *nit;
+  float *ur, *uf;  // the correction step (rhd_correct.cuh)
 };
 
 template <int MAXG>

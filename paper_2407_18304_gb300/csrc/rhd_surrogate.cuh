@@ -558,19 +558,20 @@ int launch_fused(rhd_surrogate *s, const KParams &kp, const WarmOut &W, bool ful
   N.full = full ? 1 : 0;
   N.err = s->err;
   const size_t smem = mlp::fused_bytes(N.k1, N.n4);
-  static size_t attr = 0;  // per process; the attribute is per function
-  if (smem > attr) {
-    if (cudaFuncSetAttribute(mlp::infer_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return RHD_ECUDA;
-    attr = smem;
-  }
+  if (tc::allow_smem<mlp::infer_fused_kernel>(smem) != cudaSuccess) return RHD_ECUDA;
   const int64_t tiles = (kp.n + tc::kTileM - 1) / tc::kTileM;
   const int64_t pairs = (tiles + mlp::kFusedGroups - 1) / mlp::kFusedGroups;
   const int blocks = (int)(pairs < sms ? pairs : sms);
   if (blocks > 0)
     mlp::infer_fused_kernel<<<blocks, 128 * mlp::kFusedGroups, smem, st>>>(kp, N, W);
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
+}
+
+// Parameters of the network for n_groups groups: (2 N_g + 4) -> H -> H -> H
+// -> N_g + 1, weights and biases.
+int64_t param_count(int n_groups) {
+  const int64_t H = mlp::kH, kin = 2 * (int64_t)n_groups + 4, nout = (int64_t)n_groups + 1;
+  return kin * H + H + 2 * (H * H + H) + H * nout + nout;
 }
 
 int check_surrogate(const rhd_surrogate *s) {
@@ -971,6 +972,12 @@ extern "C" int rhd_surrogate_load(const char *path, rhd_surrogate_t **out) {
     return RHD_EIO;
   }
   const bool train = std::memcmp(h.magic, rhd::kMlpMagicTrain, 8) == 0;
+  // the parameter count is fixed by the group count: a header that says
+  // otherwise is corrupt (and must not size the buffer below)
+  if ((int64_t)h.n_params != rhd::param_count(h.n_groups)) {
+    std::fclose(f);
+    return RHD_EIO;
+  }
   const size_t np = (size_t)h.n_params, nn = 2 * (size_t)(h.n_features + h.n_outputs);
   std::vector<float> buf(np + nn + (train ? 2 * np : 0));
   int64_t step = 0;

@@ -135,6 +135,14 @@ __device__ __forceinline__ void wapply_warm(const KParams &P, const WarmStart &W
     const int g = l + L * j;
     if (g >= P.G) continue;
     const int64_t o = (int64_t)g * n + i;
+    if (W.ur) {  // the FP32 iterate plus the correction step, both exact in FP64
+      C.R[j] = fma(f2d(W.r[o]), C.Etot, f2d(W.ur[o]) * C.Etot);
+      for (int d = 0; d < 3; ++d) {
+        const int64_t od = (int64_t)d * P.G * n + o;
+        C.Fk[j][d] = fma(f2d(W.f[od]), fs, f2d(W.uf[od]) * fs);
+      }
+      continue;
+    }
     C.R[j] = (double)W.r[o] * C.Etot;
     C.Fk[j][0] = (double)W.f[o] * fs;
     C.Fk[j][1] = (double)W.f[(int64_t)P.G * n + o] * fs;

@@ -169,7 +169,8 @@ def test_checkpoint_files_are_parsed_before_a_device_is_touched(lib, tmp_path):
     load.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
     ck.argtypes = [ctypes.c_void_p, ctypes.c_char_p]
     out = ctypes.c_void_p()
-    G, nf, no, npar = 4, 12, 5, 10
+    G, nf, no = 4, 12, 5
+    npar = nf * 128 + 128 + 2 * (128 * 128 + 128) + 128 * no + no  # (2G+4)->128->128->128->(G+1)
     nn = 2 * (nf + no)
     body = struct.pack(f"<{npar + nn}f", *np.linspace(-1, 1, npar + nn))
     moments = struct.pack(f"<{2 * npar}f", *np.linspace(0, 1, 2 * npar))
@@ -191,3 +192,23 @@ def test_checkpoint_files_are_parsed_before_a_device_is_touched(lib, tmp_path):
                 ctypes.byref(out)) == -7
     assert load(write("v1_as_v2.bin", b"RHDMLP2\0", body), ctypes.byref(out)) == -7
     assert ck(None, v2) == -1
+
+
+def test_a_header_with_a_wrong_parameter_count_is_a_file_error(lib, tmp_path):
+    """The parameter count follows from the group count; a header claiming
+    another one -- one short, or 2^40 (which must not size an allocation) --
+    is RHD_EIO before any body is read, and so is a truncated body."""
+    import struct
+    load = lib.rhd_surrogate_load
+    load.restype = ctypes.c_int
+    load.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_void_p)]
+    out = ctypes.c_void_p()
+    G, nf, no = 4, 12, 5
+    npar = nf * 128 + 128 + 2 * (128 * 128 + 128) + 128 * no + no
+    for claimed in (npar - 1, 1 << 40):
+        p = tmp_path / f"claims{claimed}.bin"
+        p.write_bytes(b"RHDMLP1\0" + struct.pack("<iiiiq", G, nf, no, 0, claimed) + bytes(64))
+        assert load(str(p).encode(), ctypes.byref(out)) == -7
+    p = tmp_path / "truncated.bin"
+    p.write_bytes(b"RHDMLP1\0" + struct.pack("<iiiiq", G, nf, no, 0, npar) + bytes(4 * npar))
+    assert load(str(p).encode(), ctypes.byref(out)) == -7

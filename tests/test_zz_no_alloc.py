@@ -2,8 +2,8 @@
 library allocate device memory (a host whose memory pool owns all of HBM, a
 latency-bound loop where a first-call cudaMalloc would synchronize the device,
 a run that must not fail for lack of memory midway).  It keeps the FP32
-warm start in the library's fixed 64 MiB device array instead of a cudaMalloc'd
-workspace, and must give the same result as rhd_source_update with
+iterate and the correction step in the library's fixed 64 MiB device array
+instead of a cudaMalloc'd workspace, and must give the same result as rhd_source_update with
 precision = RHD_MIXED, call after call (the array keeps the previous call's
 contents).  This file is collected last, so a failure here comes after every
 other test has run; it also passes on its own in a fresh process.
@@ -40,10 +40,19 @@ def _close(a, b):
     np.testing.assert_array_equal(a["status"], b["status"])
 
 
-@pytest.mark.parametrize("preset,n", [("mixed_128cube_ng16", 3001), ("full_256cube_ng64", 60000)])
+def _bytes(n, G):
+    """The array a call of n cells at G groups needs (the documented limit)."""
+    return n * (32 * G + 33) + 1024
+
+
+def _largest(G):
+    return (rhd.NOALLOC_BYTES - 1024) // (32 * G + 33)
+
+
+@pytest.mark.parametrize("preset,n", [("mixed_128cube_ng16", 3001), ("full_256cube_ng64", 30000)])
 def test_noalloc_matches_the_allocating_entry_point_twice(preset, n):
     w = synth.preset(preset, n_cells=n, seed=2024)
-    assert n * (16 * w.n_groups + 33) + 1024 <= rhd.NOALLOC_BYTES
+    assert _bytes(n, w.n_groups) <= rhd.NOALLOC_BYTES
     ref = _run(rhd.source_update, w, precision=rhd.MIXED)
     assert (ref["status"] == 0).mean() > 0.99
     for _ in range(2):  # the second call finds the first call's contents in the array
@@ -51,9 +60,22 @@ def test_noalloc_matches_the_allocating_entry_point_twice(preset, n):
         _close(out, ref)
 
 
+def test_noalloc_takes_exactly_the_largest_call_that_fits():
+    """At 64 groups: the largest cell count the array holds runs and matches
+    the allocating entry; one cell more is refused."""
+    n = _largest(64)
+    assert n == 32247 and _bytes(n, 64) <= rhd.NOALLOC_BYTES < _bytes(n + 1, 64)
+    w = synth.preset("full_256cube_ng64", n_cells=n, seed=77)
+    _close(_run(rhd.source_update_noalloc, w), _run(rhd.source_update, w, precision=rhd.MIXED))
+    w1 = synth.preset("full_256cube_ng64", n_cells=n + 1, seed=77)
+    with pytest.raises(rhd.RhdError) as ei:
+        _run(rhd.source_update_noalloc, w1)
+    assert ei.value.code == -6
+
+
 def test_noalloc_rejects_calls_beyond_its_array():
     w = synth.preset("full_256cube_ng64", n_cells=70000, seed=1)
-    assert 70000 * (16 * 64 + 33) + 1024 > rhd.NOALLOC_BYTES
+    assert _bytes(70000, 64) > rhd.NOALLOC_BYTES
     st = _state(w)
     before = st["erad"].clone()
     with pytest.raises(rhd.RhdError) as ei:
