@@ -159,33 +159,51 @@ def fp_peaks() -> dict:
         return {"error": str(e)}
 
 
-# Algorithmic FP64 work per cell-group, from the SASS instruction counts ncu
-# reports on a 65536-cell sample of the same workload with one cell per thread
-# (RHD_CELL_PER_THREAD: every instruction is one cell's own work; the default
-# warp-per-cell mapping executes about 30 % more, the per-cell scalar work that
-# every lane of the cell repeats).
-# FP64 arithmetic instructions (DFMA, DADD, DMUL: one issue each) of the
-# FP64-pass kernel (the one that dominates a call, timed live below):
-FP64_PASS_INST_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 715.8,
-                         ("full_256cube_ng64", "mixed"): 718.8,
-                         ("full_256cube_ng64", "fp64"): 1294.4,
-                         ("full_256cube_ng64", "fp64+surrogate"): 1186.9}
-# ... the same as flops (DFMA counted twice)
-FP64_PASS_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1066.6,
-                          ("full_256cube_ng64", "mixed"): 1071.3,
-                          ("full_256cube_ng64", "fp64"): 1955.0,
-                          ("full_256cube_ng64", "fp64+surrogate"): 1782.7}
-# ... and the flops of the whole call (inference, FP32 passes, FP64 passes)
-CALL_FLOPS_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 1081.3,
-                     ("full_256cube_ng64", "mixed"): 1085.7,
-                     ("full_256cube_ng64", "fp64"): 1955.0,
-                     ("full_256cube_ng64", "fp64+surrogate"): 1783.5}
-# DRAM bytes (read + write) per cell-group of one launch of the FP64-pass
-# kernel in the default mapping (ncu on the same sample, the current kernel)
-FP64_PASS_TRAFFIC_PER_CG = {("full_256cube_ng64", "mixed+surrogate"): 69.1,
-                            ("full_256cube_ng64", "mixed"): 68.2,
-                            ("full_256cube_ng64", "fp64"): 51.6,
-                            ("full_256cube_ng64", "fp64+surrogate"): 68.4}
+# The roofline's numerator: algorithmic operations of a call = the events the
+# kernels report (rhd_events_start/stop: inner evaluations, outer passes,
+# coupled residuals and Newton steps, ...) times the operations per event and
+# cell-group of the counting model (oracle/opcount.py, a plain statement of the
+# method's steps; its table is tests/golden/opcounts.json, regenerated by
+# python -m oracle.opcount), the special functions weighted by their measured
+# issue cost (fp_peak).  The kernels' own instruction streams do not enter.
+OPCOUNTS = os.path.join(ROOT, "tests", "golden", "opcounts.json")
+# events of each kind of launch (the names of rhd.EVENT_NAMES and of the table)
+KERNEL_EVENTS = {"fp32_passes": ("eval32", "outer32"),
+                 "correction": ("resid64", "step32", "finish64"),
+                 "fp64_passes": ("eval64", "cached64", "outer64")}
+# the per-update setup (tau_g and its reciprocals) once per cell of these counters
+KERNEL_CELLS = {"correction": "cellsc", "fp64_passes": "cells64"}
+# DRAM bytes (read + write) per cell-group of one launch of the dominant kernel,
+# ncu on a 65536-cell sample of the same workload
+# (profiles/correct_warp_kernel_65536cells_ng64.md); None once the kernel changed
+DOMINANT_TRAFFIC_PER_CG = {("full_256cube_ng64", "correction"): None}
+
+
+def op_slots(counts: dict, weights: dict) -> float:
+    """Issue slots of a tally {kind: n}: add, mul, fma and compares one each,
+    div / sqrt / exp the measured multiple of an FMA."""
+    return sum(v * (weights.get(k, 1.0) if k in ("div", "sqrt", "exp") else 1.0)
+               for k, v in counts.items())
+
+
+def algorithmic_ops(workload: str, events: dict, G: int, peaks: dict) -> dict:
+    """{kernel: {"f64": slots, "f32": slots}} of the algorithm for the events counted."""
+    with open(OPCOUNTS) as f:
+        table = json.load(f)["events"].get(workload)
+    if table is None:
+        return {}
+    w64 = peaks.get("fp64_op_slots", {})
+    w32 = peaks.get("fp32_op_slots", {})
+    out = {}
+    for kern, evs in KERNEL_EVENTS.items():
+        f64 = f32 = 0.0
+        for e in evs:
+            f64 += events.get(e, 0) * G * op_slots(table[e]["f64"], w64)
+            f32 += events.get(e, 0) * G * op_slots(table[e]["f32"], w32)
+        if kern in KERNEL_CELLS:
+            f64 += events.get(KERNEL_CELLS[kern], 0) * G * op_slots(table["setup64"]["f64"], w64)
+        out[kern] = {"f64": f64, "f32": f32}
+    return out
 
 
 def train_surrogate(args, w, dev, rank):
@@ -238,8 +256,6 @@ def run_ours(args, ws, rank):
         else:
             rhd.source_update(st, w.edges, w.law, **args_)
 
-    kernel_ms = [0.0, 0]  # mean FP64-pass kernel duration of the headline loop, launches
-
     def timed(p, warm, steps, warmup, sample_clocks=False):
         """warmup + steps solves; per-step CUDA-event times and outcome."""
         for _ in range(warmup):
@@ -254,7 +270,7 @@ def run_ours(args, ws, rank):
         barrier(ws)
         torch.cuda.synchronize()
         if sample_clocks:
-            rhd.profile_start()  # events around the FP64-pass kernel of each call
+            rhd.profile_start()  # events around each launch of each call
         t0 = time.perf_counter()
         for k in range(steps):
             restore()
@@ -271,8 +287,7 @@ def run_ours(args, ws, rank):
         wall = time.perf_counter() - t0
         clk = clocks.stop() if sample_clocks else None
         if sample_clocks:
-            nl, kms = rhd.profile_stop()
-            kernel_ms[:] = [kms / max(1, nl), nl]
+            rhd.profile_stop()  # per kind: rhd.profile_kernel
         ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
         stat = status.cpu().numpy()
         it = iters.cpu().numpy().astype(np.int64)
@@ -294,7 +309,7 @@ def run_ours(args, ws, rank):
     t_max = allmax(t_dev, ws)
     units = float(n) * G * args.steps
     total_units = allsum(units, ws)
-    launches = (1 if prec == rhd.FP64 else 2) + (1 if use_sur else 0)
+    launches = (1 if prec == rhd.FP64 else 3) + (1 if use_sur else 0)
     form = ("mixed" if prec == rhd.MIXED else "fp64") + ("+surrogate" if use_sur else "")
 
     res = {"metric": METRIC, "value": total_units / t_max, "unit": UNIT, "n_gpus": ws,
@@ -321,49 +336,59 @@ def run_ours(args, ws, rank):
             res["mixed_form"] = side(rhd.MIXED, False, args.fp64_steps)
             res["fp64_surrogate_form"] = side(rhd.FP64, True, args.fp64_steps)
 
-    # roofline of the dominant kernel (the FP64 passes), its duration measured
-    # live with CUDA events.  The kernel is bound by the issue rate of the FP64
-    # pipe: GB300 issues two FP64 lanes per SM per clock,
-    # and a DADD or DMUL takes an issue slot as a DFMA does, so the roofline is
-    # algorithmic FP64 instructions per second against the measured DFMA
-    # instruction rate; the flop form (DFMA = 2 flops, against the DFMA flop
-    # peak) is reported beside it.
+    # ---- roofline: algorithmic operations of the call (counting model x the
+    # events the kernels report in one untimed counted call) against the
+    # measured FP64 / FP32 issue rates and HBM bandwidth
     peaks = fp_peaks()
     res["fp_peaks_measured"] = peaks
+    restore()
+    torch.cuda.synchronize()
+    rhd.events_start()
+    call(prec, use_sur)
+    events = rhd.events_stop()
+    res["events_per_cell"] = {k: v / n for k, v in events.items() if v}
+    ops = algorithmic_ops(name, events, G, peaks)
     mean_call_s = t_dev / args.steps
     bytes_alg = n * (G * 64 + 82)  # in+out FP64 SoA per call: E_g, F_g and the per-cell fields
-    hbm_frac = bytes_alg / mean_call_s / 1e9 / _measured_hbm()
-    key = (name, form)
-    per_inst = FP64_PASS_INST_PER_CG.get(key)
-    if per_inst is not None and kernel_ms[1] > 0:
-        peak_tf = peaks.get("fp64_fma_tflops") or 1.25
-        k_s = kernel_ms[0] / 1e3
-        ach_i = per_inst * n * G / k_s / 1e9
-        peak_i = peak_tf * 1e3 / 2.0
-        ach_f = FP64_PASS_FLOPS_PER_CG[key] * n * G / k_s / 1e12
-        tr = FP64_PASS_TRAFFIC_PER_CG.get(key)
+    hbm = _measured_hbm()
+    p64 = (peaks.get("fp64_fma_tflops") or 1.25) * 1e12 / 2.0  # FMA issue slots / s
+    p32 = (peaks.get("fp32_fma_tflops") or 78.0) * 1e12 / 2.0
+    kinds = {kname: rhd.profile_kernel(k) for k, kname in enumerate(rhd.KERNEL_NAMES)}
+    kern_s = {k: v[1] / 1e3 / max(1, v[0]) for k, v in kinds.items() if v[0] > 0}
+    res["kernel_ms_per_call"] = {k: 1e3 * v for k, v in kern_s.items()}
+    if ops and kern_s:
+        dom = max(kern_s, key=kern_s.get)
+        o = ops.get(dom, {"f64": 0.0, "f32": 0.0})
+        t = kern_s[dom]
+        ach64, ach32 = o["f64"] / t / 1e9, o["f32"] / t / 1e9
+        tr = DOMINANT_TRAFFIC_PER_CG.get((name, dom))
+        tot64 = sum(v["f64"] for v in ops.values())
+        tot32 = sum(v["f32"] for v in ops.values())
+        t_roof = {"hbm": bytes_alg / (hbm * 1e9), "fp64": tot64 / p64, "fp32": tot32 / p32}
         res["roofline"] = {
-            "bound": "alu", "achieved": ach_i, "peak": peak_i, "unit": "G FP64 inst/s",
-            "frac": ach_i / peak_i,
+            "bound": "alu", "achieved": ach64, "peak": p64 / 1e9, "unit": "G FP64 slots/s",
+            "frac": ach64 / (p64 / 1e9),
             "traffic": tr * n * G if tr is not None else None,
-            "kernel": "FP64 passes (solve_warp_kernel<32,2>)",
-            "kernel_ms": kernel_ms[0], "kernel_launches_timed": kernel_ms[1],
-            "what": "algorithmic FP64 arithmetic instructions (DFMA, DADD, DMUL) of the kernel "
-                    "per launch / its CUDA-event duration, vs the measured DFMA instruction rate",
-            "peak_source": ("measured fp_peak DFMA loop / 2 flops per DFMA (nominal 152 SMs x "
-                            "2 FP64 lanes/clk x 2.07 GHz = 629 G inst/s)" if "fp64_fma_tflops" in peaks
-                            else "nominal 1.25 TFLOP/s / 2"),
-            "fp64_inst_per_cell_group": per_inst,
-            "flops": {"achieved": ach_f, "peak": peak_tf, "unit": "TFLOP/s",
-                      "frac": ach_f / peak_tf,
-                      "fp64_flops_per_cell_group": FP64_PASS_FLOPS_PER_CG[key]},
-            "call_fp64_tflops": CALL_FLOPS_PER_CG.get(key, 0.0) * n * G / mean_call_s / 1e12,
-            "hbm_frac_of_call": hbm_frac}
+            "kernel": dom, "kernel_ms": 1e3 * t,
+            "what": ("algorithmic FP64 operations of the kernel per launch (counting model "
+                     "tests/golden/opcounts.json x the events the kernel reports; div, sqrt and "
+                     "exp at their measured issue cost) / its CUDA-event duration, against the "
+                     "measured FP64 FMA issue rate (fp_peak, of measured)"),
+            "fp64_slots_per_cell_group": o["f64"] / (n * G),
+            "fp32": {"achieved": ach32, "peak": p32 / 1e9, "unit": "G FP32 slots/s",
+                     "frac": ach32 / (p32 / 1e9), "slots_per_cell_group": o["f32"] / (n * G)},
+            "hbm": {"achieved": bytes_alg / t / 1e9, "peak": hbm, "unit": "GB/s",
+                    "frac": bytes_alg / t / 1e9 / hbm},
+            "call": {"ms": 1e3 * mean_call_s,
+                     "roofline_ms": {k: 1e3 * v for k, v in t_roof.items()},
+                     "frac": max(t_roof.values()) / mean_call_s,
+                     "fp64_slots_per_cell_group": tot64 / (n * G),
+                     "fp32_slots_per_cell_group": tot32 / (n * G),
+                     "hbm_frac": t_roof["hbm"] / mean_call_s}}
     else:
-        peak = _measured_hbm()
         ach = bytes_alg / mean_call_s / 1e9
-        res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
-                           "frac": ach / peak, "traffic": None,
+        res["roofline"] = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                           "frac": ach / hbm, "traffic": None,
                            "peak_source": "MEASURED_PEAKS.json hbm_gbs"}
 
     if not args.no_e2e:

@@ -344,14 +344,51 @@ int rhd_source_update_host(rhd_state_t *state, const rhd_groups_t *groups,
                            rhd_surrogate_t *surrogate, int64_t chunk_cells);
 
 /* ---- Benchmark support -------------------------------------------------------
- * Time the FP64-pass kernel of every rhd_source_update / rhd_source_update_warm
+ * Time the solver launches of every rhd_source_update / rhd_source_update_warm
  * call this thread makes between rhd_profile_start and rhd_profile_stop, with
- * CUDA events recorded on the call's stream right before and after that launch
- * (the kernel that dominates a call).  rhd_profile_stop synchronizes those
- * events and returns the number of timed launches and their summed duration in
- * milliseconds.  Not part of the method; no counterpart in the paper. */
+ * CUDA events recorded on the call's stream right before and after each launch.
+ * rhd_profile_stop synchronizes those events and returns the number of timed
+ * launches and their summed duration in milliseconds, over all kinds of launch.
+ * Not part of the method; no counterpart in the paper. */
 int rhd_profile_start(void);
 int rhd_profile_stop(int32_t *launches, double *total_ms);
+
+/* The same events around each kind of launch: after rhd_profile_stop,
+ * rhd_profile_kernel returns the launches of one kind and their summed
+ * duration (RHD_EINVAL for an unknown kind). */
+#define RHD_KERNEL_FP32 0       /* the mixed form's FP32 passes */
+#define RHD_KERNEL_CORRECTION 1 /* its correction step (FP64 residual, FP32 Newton step) */
+#define RHD_KERNEL_FP64 2       /* the FP64 passes (the FP64 form; the mixed form's fallback) */
+#define RHD_KERNEL_INFERENCE 3  /* the learned warm start's fused inference */
+#define RHD_KERNELS 4
+int rhd_profile_kernel(int32_t kind, int32_t *launches, double *total_ms);
+
+/* ---- Event counts ------------------------------------------------------------
+ * Counters of what the update calls of this thread did between rhd_events_start
+ * and rhd_events_stop, summed over cells (a cell of N_g groups contributes each
+ * event once, not per group): the benchmark multiplies them by the operations
+ * per event of the counting model to get the algorithmic operations of a call.
+ * rhd_events_start zeroes the counters of the current device; rhd_events_stop
+ * synchronizes the device and copies RHD_EVENTS counters to counts.  Counting
+ * costs one atomic add per event and cell; calls on other threads and the
+ * batched entry are not counted.  Not part of the method; no counterpart in the
+ * paper. */
+#define RHD_EV_CELLS32 0     /* cells through the FP32 passes */
+#define RHD_EV_EVAL32 1      /* FP32 inner evaluations (a4-a8) */
+#define RHD_EV_OUTER32 2     /* FP32 outer passes (a9-a12) */
+#define RHD_EV_CELLSC 3      /* cells through the correction step */
+#define RHD_EV_RESID64 4     /* FP64 evaluations of the coupled residual */
+#define RHD_EV_STEP32 5      /* FP32 Newton steps on the coupled system */
+#define RHD_EV_FINISH64 6    /* cells the correction step finished */
+#define RHD_EV_CELLS64 7     /* cells through the FP64 passes */
+#define RHD_EV_EVAL64 8      /* FP64 inner evaluations */
+#define RHD_EV_CACHED64 9    /* FP64 inner iterations taken from cached group terms */
+#define RHD_EV_OUTER64 10    /* FP64 outer passes */
+#define RHD_EV_FLUXNEWTON 11 /* group flux updates solved by Newton steps (slow cells) */
+#define RHD_EV_INFER 12      /* cells through the warm start's inference */
+#define RHD_EVENTS 13
+int rhd_events_start(void);
+int rhd_events_stop(uint64_t *counts);
 
 /* The mixed-precision form without any device allocation.  Some callers
  * cannot let a library call cudaMalloc: a host that hands every byte of HBM
@@ -362,8 +399,8 @@ int rhd_profile_stop(int32_t *launches, double *total_ms);
  * (state->precision is ignored) but keeps the FP32 pass's warm start in a
  * file-scope device array of RHD_NOALLOC_BYTES that every GPU loading the
  * library holds until process exit.  The caller still passes all inputs and
- * outputs.  Size limit: n_cells * (32 * n_groups + 33) + 1024 <=
- * RHD_NOALLOC_BYTES (64 MiB; at most 32,247 cells at 64 groups, 123,133 at 16);
+ * outputs.  Size limit: n_cells * (32 * n_groups + 34) + 1024 <=
+ * RHD_NOALLOC_BYTES (64 MiB; at most 32,232 cells at 64 groups, 122,908 at 16);
  * larger calls return RHD_ESIZE and launch nothing.  The paper has no counterpart: this is a
  * deployment variant of the same kernels.  The first call on a device looks up
  * the array's device address (and initialises the constant tables), so make

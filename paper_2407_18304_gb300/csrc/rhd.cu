@@ -32,7 +32,7 @@ void *g_ws[kMaxDevices];
 size_t g_ws_bytes[kMaxDevices];
 
 size_t warm_bytes(int64_t n, int G) {
-  return (size_t)n * (4 * sizeof(double) + 1) + (size_t)n * G * 8 * sizeof(float) + 1024;
+  return (size_t)n * (4 * sizeof(double) + 2) + (size_t)n * G * 8 * sizeof(float) + 1024;
 }
 
 // Carve the warm-start arrays out of a workspace starting at p: E_int and
@@ -47,7 +47,8 @@ void carve(char *p, int64_t n, int G, WarmOut *w, WarmStart *r) {
   w->ur = w->f + (size_t)3 * G * n;
   w->uf = w->ur + (size_t)G * n;
   w->nit = reinterpret_cast<uint8_t *>(w->uf + (size_t)3 * G * n);
-  *r = WarmStart{w->eint, w->mom, w->r, w->f, w->nit, 1, nullptr, nullptr};
+  w->done = w->nit + n;
+  *r = WarmStart{w->eint, w->mom, w->r, w->f, w->nit, 1, nullptr, nullptr, nullptr};
 }
 
 int workspace(int64_t n, int G, WarmOut *w, WarmStart *r) {
@@ -156,6 +157,31 @@ int ensure_device(int *sms) {
 
 bool pos_finite(double x) { return std::isfinite(x) && x > 0.0; }
 
+// rhd_events_start/stop: the update calls of this thread add their events to
+// g_events (pack sets KParams::count); the inference's cells are counted here.
+thread_local bool t_counting = false;
+thread_local unsigned long long t_infer_cells = 0;
+
+// rhd_profile_start/stop: event pairs around the launches of this thread, by kind.
+thread_local bool t_profiling = false;
+thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_events[RHD_KERNELS];
+thread_local int32_t t_prof_n[RHD_KERNELS];
+thread_local double t_prof_ms[RHD_KERNELS];
+
+// Run launch() between two events on st when profiling (kind: RHD_KERNEL_*).
+template <typename F>
+void timed_launch(int kind, cudaStream_t st, F &&launch) {
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (t_profiling && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
+    cudaEventRecord(a, st);
+    launch();
+    cudaEventRecord(b, st);
+    t_events[kind].emplace_back(a, b);
+    return;
+  }
+  launch();
+}
+
 // Fill the launch parameters from the public structs; RHD_OK or an error.
 int pack(const rhd_state_t *s, const rhd_groups_t *gr, const rhd_opacity_law_t *law, double dt,
          int64_t n, KParams *kp) {
@@ -255,6 +281,7 @@ int pack(const rhd_state_t *s, const rhd_groups_t *gr, const rhd_opacity_law_t *
   kp->flags = s->flags;
   kp->G = G;
   kp->mode = law->mode;
+  kp->count = t_counting ? 1 : 0;
   return RHD_OK;
 }
 
@@ -295,22 +322,10 @@ void launch_thread(const KParams &kp, const WarmStart &W, int sms, cudaStream_t 
   solve_fp64_kernel<MAXG, CACHE><<<b, threads, smem, st>>>(kp, W);
 }
 
-// rhd_profile_start/stop: event pairs around the FP64-pass launches of this thread.
-thread_local bool t_profiling = false;
-thread_local std::vector<std::pair<cudaEvent_t, cudaEvent_t>> t_events;
-
 void launch_fp64_passes_impl(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st);
 
 void launch_fp64_passes(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
-  cudaEvent_t a = nullptr, b = nullptr;
-  if (t_profiling && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess) {
-    cudaEventRecord(a, st);
-    launch_fp64_passes_impl(kp, W, sms, st);
-    cudaEventRecord(b, st);
-    t_events.emplace_back(a, b);
-    return;
-  }
-  launch_fp64_passes_impl(kp, W, sms, st);
+  timed_launch(RHD_KERNEL_FP64, st, [&] { launch_fp64_passes_impl(kp, W, sms, st); });
 }
 
 // The FP64 passes (cold, or from the warm start in W): one cell per thread
@@ -341,8 +356,8 @@ void launch_fp64_passes_impl(const KParams &kp, const WarmStart &W, int sms, cud
 // from S where S.r is set): one cell per thread up to 32 groups and past 64,
 // a warp per cell in between (rhd_warp32.cuh).
 template <int MAXG>
-void launch_fp32_passes(const KParams &kp, const WarmOut &wo, const WarmStart &S, int sms,
-                        cudaStream_t st) {
+void launch_fp32_passes_impl(const KParams &kp, const WarmOut &wo, const WarmStart &S, int sms,
+                             cudaStream_t st) {
   const int threads = 128;
   const size_t smem = table_bytes(kp.G);
   if (kp.G > 32 && kp.G <= 64 && !(kp.flags & RHD_CELL_PER_THREAD)) {
@@ -354,34 +369,43 @@ void launch_fp32_passes(const KParams &kp, const WarmOut &wo, const WarmStart &S
   warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo, S);
 }
 
+template <int MAXG>
+void launch_fp32_passes(const KParams &kp, const WarmOut &wo, const WarmStart &S, int sms,
+                        cudaStream_t st) {
+  timed_launch(RHD_KERNEL_FP32, st, [&] { launch_fp32_passes_impl<MAXG>(kp, wo, S, sms, st); });
+}
+
 template <int L, int GPL>
 void launch_correct_k(const KParams &kp, const WarmOut &wo, int sms, cudaStream_t st) {
   const int threads = 128;
   const size_t smem = table_bytes(kp.G);
   const int b = persistent_blocks(correct_warp_kernel<L, GPL>, smem, sms, kp.n * L, threads);
-  correct_warp_kernel<L, GPL><<<b, threads, smem, st>>>(kp, wo, CorrOut{wo.ur, wo.uf});
+  correct_warp_kernel<L, GPL><<<b, threads, smem, st>>>(kp, wo, CorrOut{wo.ur, wo.uf, wo.done});
 }
 
 // The correction step after the FP32 passes (rhd_correct.cuh): L lanes per
-// cell with GPL groups each (up to 128 groups); returns the warm start of the
-// FP64 passes, with the step when it ran.
+// cell with GPL groups each (up to 128 groups); it finishes most cells and
+// returns the warm start of the FP64 passes for the rest.
 WarmStart launch_correct(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int sms,
                          cudaStream_t st) {
   WarmStart w = wi;
   if (kp.G > 128) return w;
-  if (kp.G <= 16) launch_correct_k<8, 2>(kp, wo, sms, st);
-  else if (kp.G <= 32) launch_correct_k<16, 2>(kp, wo, sms, st);
-  else if (kp.G <= 64) launch_correct_k<32, 2>(kp, wo, sms, st);
-  else launch_correct_k<32, 4>(kp, wo, sms, st);
+  timed_launch(RHD_KERNEL_CORRECTION, st, [&] {
+    if (kp.G <= 16) launch_correct_k<8, 2>(kp, wo, sms, st);
+    else if (kp.G <= 32) launch_correct_k<16, 2>(kp, wo, sms, st);
+    else if (kp.G <= 64) launch_correct_k<32, 2>(kp, wo, sms, st);
+    else launch_correct_k<32, 4>(kp, wo, sms, st);
+  });
   w.ur = wo.ur;
   w.uf = wo.uf;
+  w.done = wo.done;
   return w;
 }
 
 template <int MAXG>
 int launch_mixed(const KParams &kp, const WarmOut &wo, const WarmStart &wi, int sms,
                  cudaStream_t st) {
-  const WarmStart none{nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
+  const WarmStart none{nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr};
   if (kp.mode == RHD_PPL_FREE) {  // no FP32 passes for free slopes: FP64 from the cold start
     launch_fp64_passes(kp, none, sms, st);
     return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
@@ -416,7 +440,7 @@ int launch_warm(const KParams &kp, int precision, const WarmOut &wo, const WarmS
 template <int MAXG>
 int launch_g(const KParams &kp, int precision, int sms, cudaStream_t st) {
   if (precision == RHD_FP64) {
-    const WarmStart cold{nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr};
+    const WarmStart cold{nullptr, nullptr, nullptr, nullptr, nullptr, 0, nullptr, nullptr, nullptr};
     launch_fp64_passes(kp, cold, sms, st);
   } else {
     WarmOut wo;
@@ -923,11 +947,15 @@ extern "C" int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids,
 #include "rhd_host.cuh"
 
 extern "C" int rhd_profile_start(void) {
-  for (auto &e : rhd::t_events) {
-    cudaEventDestroy(e.first);
-    cudaEventDestroy(e.second);
+  for (int k = 0; k < RHD_KERNELS; ++k) {
+    for (auto &e : rhd::t_events[k]) {
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    rhd::t_events[k].clear();
+    rhd::t_prof_n[k] = 0;
+    rhd::t_prof_ms[k] = 0.0;
   }
-  rhd::t_events.clear();
   rhd::t_profiling = true;
   return RHD_OK;
 }
@@ -935,21 +963,59 @@ extern "C" int rhd_profile_start(void) {
 extern "C" int rhd_profile_stop(int32_t *launches, double *total_ms) {
   if (!launches || !total_ms) return RHD_EINVAL;
   rhd::t_profiling = false;
-  double sum = 0.0;
   int rc = RHD_OK;
-  for (auto &e : rhd::t_events) {
-    float ms = 0.0f;
-    if (cudaEventSynchronize(e.second) != cudaSuccess ||
-        cudaEventElapsedTime(&ms, e.first, e.second) != cudaSuccess)
-      rc = RHD_ECUDA;
-    sum += ms;
-    cudaEventDestroy(e.first);
-    cudaEventDestroy(e.second);
+  int32_t n = 0;
+  double sum = 0.0;
+  for (int k = 0; k < RHD_KERNELS; ++k) {
+    double s = 0.0;
+    for (auto &e : rhd::t_events[k]) {
+      float ms = 0.0f;
+      if (cudaEventSynchronize(e.second) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e.first, e.second) != cudaSuccess)
+        rc = RHD_ECUDA;
+      s += ms;
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    rhd::t_prof_n[k] = (int32_t)rhd::t_events[k].size();
+    rhd::t_prof_ms[k] = s;
+    rhd::t_events[k].clear();
+    n += rhd::t_prof_n[k];
+    sum += s;
   }
-  *launches = (int32_t)rhd::t_events.size();
+  *launches = n;
   *total_ms = sum;
-  rhd::t_events.clear();
   return rc;
+}
+
+extern "C" int rhd_profile_kernel(int32_t kind, int32_t *launches, double *total_ms) {
+  if (kind < 0 || kind >= RHD_KERNELS || !launches || !total_ms) return RHD_EINVAL;
+  *launches = rhd::t_prof_n[kind];
+  *total_ms = rhd::t_prof_ms[kind];
+  return RHD_OK;
+}
+
+extern "C" int rhd_events_start(void) {
+  int sms = 0;
+  const int rc = rhd::ensure_device(&sms);
+  if (rc != RHD_OK) return rc;
+  const unsigned long long zero[RHD_EVENTS] = {};
+  if (cudaMemcpyToSymbol(rhd::g_events, zero, sizeof(zero)) != cudaSuccess) return RHD_ECUDA;
+  rhd::t_infer_cells = 0;
+  rhd::t_counting = true;
+  return RHD_OK;
+}
+
+extern "C" int rhd_events_stop(uint64_t *counts) {
+  if (!counts) return RHD_EINVAL;
+  rhd::t_counting = false;
+  unsigned long long c[RHD_EVENTS];
+  if (cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpyFromSymbol(c, rhd::g_events, sizeof(c)) != cudaSuccess)
+    return RHD_ECUDA;
+  for (int k = 0; k < RHD_EVENTS; ++k) counts[k] = (uint64_t)c[k];
+  counts[RHD_EV_INFER] += rhd::t_infer_cells;
+  return RHD_OK;
 }
 
 extern "C" const char *rhd_strerror(int code) {

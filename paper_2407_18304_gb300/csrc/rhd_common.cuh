@@ -43,6 +43,7 @@ struct KParams {
   double tol, tol_outer;
   int max_newton, max_outer, closure, flags;
   int G, mode, n_seg, has_table;
+  int count;  // 1: add this launch's events to g_events (rhd_events_start/stop)
   double nu_ref, temp_exp, T_ref;
   double edges[kMaxG + 1];
   double nu_break[kMaxSeg];
@@ -81,6 +82,14 @@ __host__ __device__ __forceinline__ size_t table_bytes(int G) {
 }
 
 __constant__ double c_planck[kPlanckWords];
+
+// Event counters of the update (include/rhd.h, RHD_EV_*): what each launch
+// did, per cell, added once per cell by one lane when KParams::count is set.
+__device__ unsigned long long g_events[RHD_EVENTS];
+
+__device__ __forceinline__ void count_event(const KParams &P, int k, unsigned long long v) {
+  if (P.count && v) atomicAdd(&g_events[k], v);
+}
 
 // Copy the Planck polynomials to sm (all threads; the caller synchronises).
 __device__ __forceinline__ void load_planck(double *sm) {
@@ -385,6 +394,7 @@ struct Vec3 {
 // absolute values (l1).
 struct FluxDelta {
   double x, y, z, l1;
+  unsigned n;  // groups solved by Newton steps
 };
 
 // Newton steps of flux_update from F (kept out of line: taken by few groups,

@@ -33,11 +33,13 @@
 
 namespace rhd {
 
-// The correction step's output: per cell-group the step (r_g, f_g); zero for
-// a cell the step is not taken for.
+// The correction kernel's output for the cells it does not finish: the
+// accumulated step (r_g, f_g) from the FP32 iterate, and per cell whether the
+// cell is finished (1: its final state is written; the FP64 passes skip it).
 struct CorrOut {
-  float *ur;  // [G][n]
-  float *uf;  // [3][G][n]
+  float *ur;      // [G][n]
+  float *uf;      // [3][G][n]
+  uint8_t *done;  // [n]
 };
 
 // FP32 copy of the Planck polynomials cut to degree kDeg32 (as the FP32
@@ -251,15 +253,33 @@ __device__ __forceinline__ bool global_solve(const float s[20], float rG, float 
   return isfinite(x) && isfinite(beta[0]) && isfinite(beta[1]) && isfinite(beta[2]);
 }
 
-// A step is taken only when it is small against the cell's energy scale: the
-// FP32 passes leave the iterate at FP32 accuracy, so a larger step means the
-// FP32 passes stopped at a cap, and the FP64 passes take the cell from W.
+// A step is taken only when it is small against the cell's energy scale:
+// the FP32 passes leave the iterate at FP32 accuracy, so a larger step means
+// they stopped at a cap, and the FP64 passes take the cell from there.
 constexpr float kMaxStep = 1e-2f;
+// Newton steps on the coupled system before a cell is left to the FP64 passes.
+constexpr int kMaxCorrections = 3;
 
-// The correction step with L lanes per cell (the layout of rhd_warp.cuh).
-// Reads the state and the FP32 iterate in W; writes the step to U and the
-// corrected E_int and momentum to W (FP64); a cell the step is not taken for
-// gets U = 0 and keeps W.
+// The cell's state and iterate of the correction kernel, per lane: groups
+// g = l + L j (the layout of rhd_warp.cuh).
+template <int GPL>
+struct CCell {
+  double E0[GPL], R[GPL], F[GPL][3], ft[GPL][3];  // E^t + S, iterate, F^t
+  double Fn[GPL][3];                               // eq. numF1 at the iterate
+  float rw[GPL], fw[GPL][3];                       // the FP32 iterate (scaled)
+  float rR[GPL], rF[GPL][3], q[GPL], qe[GPL];      // scaled residual, chi_F/chi_E, tau/(1+tau)
+};
+
+// The correction step with L lanes per cell: from the FP32 passes' iterate
+// (W), Newton steps on the coupled system -- each an FP64 evaluation of the
+// residual followed, unless the paper's tests already hold, by an FP32
+// Jacobian step -- until the paper's inner test (after eq. matrix) and outer
+// test (the change one more outer pass would make, readings of Sec. 3) hold
+// on the FP64 residual.  A cell that meets them is finished here exactly as
+// an FP64 pass finishes it: each R_g from its own row, the flux update of
+// eq. numF1, the conservative write-back of E_g, E_gas and the momentum in
+// FP64.  Any other cell is left to the FP64 passes with its iterate in
+// W + U.
 template <int L, int GPL>
 __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant__ KParams P,
                                                            const WarmOut W, const CorrOut U) {
@@ -278,231 +298,341 @@ __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant
   const int64_t n = P.n;
   const double c = P.c, tdt = P.c_hat * P.theta * P.dt;
   const int src_lane = lane0 + (l + 1) % L;
+  const float tol = (float)P.tol, tol_o = (float)P.tol_outer, crf = (float)P.cr;
+  CCell<GPL> C;
   for (int64_t i = warp * CPW + seg; i < n; i += nwarps * CPW) {
-    // ---- the cell and its FP32 iterate (an invalid cell or one without an
-    // iterate is left to the FP64 passes, which never read U for it)
-    const double Eint = W.eint[i];
+    // ---- the cell, validated as the FP64 passes validate it; an invalid
+    // cell or one without an FP32 iterate is left to them
+    const double Eint0 = W.eint[i];
     const double rho = P.rho[i];
     const double k0 = P.kappa0 ? P.kappa0[i] : 1.0;
-    if (!(Eint > 0.0) || !(rho > 0.0) || !isfinite(rho) || !isfinite(k0) || !(k0 >= 0.0))
-      continue;
     const double m0[3] = {P.mom[0][i], P.mom[1][i], P.mom[2][i]};
     const double eg0 = P.egas[i];
-    double E0[GPL], R[GPL], F[GPL][3], ft[GPL][3];
-    float rw[GPL], fw[GPL][3];
+    bool valid = Eint0 > 0.0 && rho > 0.0 && isfinite(rho) && isfinite(eg0) && isfinite(k0) &&
+                 k0 >= 0.0 && isfinite(m0[0]) && isfinite(m0[1]) && isfinite(m0[2]);
+    valid = valid && eg0 - 0.5 * (m0[0] * m0[0] + m0[1] * m0[1] + m0[2] * m0[2]) / rho > 0.0;
     double sumE0 = 0.0;
 #pragma unroll
     for (int j = 0; j < GPL; ++j) {
       const int g = l + L * j;
-      E0[j] = 0.0;
-      rw[j] = 0.0f;
+      C.E0[j] = 0.0;
+      C.rw[j] = 0.0f;
       for (int d = 0; d < 3; ++d) {
-        fw[j][d] = 0.0f;
-        ft[j][d] = 0.0;
+        C.fw[j][d] = 0.0f;
+        C.ft[j][d] = 0.0;
       }
-      if (g < G) {
+      if (g < G && valid) {
         const int64_t o = (int64_t)g * P.gs + i;
-        E0[j] = P.erad[o] + (P.src ? P.src[o] : 0.0);
-        sumE0 += E0[j];
+        const double e = P.erad[o], sg = P.src ? P.src[o] : 0.0;
+        C.E0[j] = e + sg;
+        valid = valid && isfinite(e) && isfinite(sg);
+        sumE0 += C.E0[j];
         const int64_t ow = (int64_t)g * n + i;
-        rw[j] = W.r[ow];
+        C.rw[j] = W.r[ow];
         for (int d = 0; d < 3; ++d) {
-          ft[j][d] = P.frad[d][o];
-          fw[j][d] = W.f[(int64_t)d * G * n + ow];
+          C.ft[j][d] = P.frad[d][o];
+          valid = valid && isfinite(C.ft[j][d]);
+          C.fw[j][d] = W.f[(int64_t)d * G * n + ow];
         }
       }
+    }
+    if (!__all_sync(mask, valid)) {
+      if (l == 0) U.done[i] = 0;
+      continue;
     }
     sumE0 = seg_sum<L>(sumE0, mask);
     const double Et = eg0 + P.cr * sumE0;
     int shE;
     const float imE = 1.0f / frexp_f(Et, shE);
-    const double fs = c * Et;
-    // ---- FP64 residual at the iterate (momentum from the fluxes, eq. vupdate)
-    double dF[3] = {0.0, 0.0, 0.0}, sumR = 0.0;
-#pragma unroll
-    for (int j = 0; j < GPL; ++j) {
-      R[j] = f2d(rw[j]) * Et;
-      for (int d = 0; d < 3; ++d) {
-        F[j][d] = f2d(fw[j][d]) * fs;
-        if (l + L * j < G) dF[d] += F[j][d] - ft[j][d];
-      }
-      if (l + L * j < G) sumR += R[j];
-    }
-    for (int d = 0; d < 3; ++d) dF[d] = seg_sum<L>(dF[d], mask);
-    sumR = seg_sum<L>(sumR, mask);
-    const double irho = 1.0 / rho;
-    double m[3], v[3];
-    for (int d = 0; d < 3; ++d) {
-      m[d] = m0[d] - dF[d] * P.icc;
-      v[d] = m[d] * irho;
-    }
-    const double KE = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) * irho;
-    const double rcv = rho * P.c_v;
-    const double T = Eint / rcv;
-    double cs = rho * k0;
-    if (P.temp_exp != 0.0) cs *= pow(T / P.T_ref, P.temp_exp);
-    const double its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
-    const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
-    const double invT = 1.0 / T;
-    double pqE[NE], dE_[NE], eE[NE];
-    bool lowE[NE];
-#pragma unroll
-    for (int jj = 0; jj < NE; ++jj) {
-      const int e = l + L * jj;
-      if (jj == NE - 1 && G == L * GPL) {  // the top edge alone (see winner_step)
-        const double xg = tab.xe[G] * invT;
-        if (xg >= 40.0 && xg < HUGE_VAL) {
-          const double em = exp(-xg);
-          const double x2 = xg * xg;
-          pqE[jj] = kPlanckNorm * em * (x2 * xg + 3.0 * x2 + 6.0 * xg + 6.0);
-          dE_[jj] = kPlanckNorm * em * x2 * x2;
-          eE[jj] = 0.0;
-          lowE[jj] = false;
-          continue;
-        }
-      }
-      edge_tab(tab.pc, e <= G ? tab.xe[e] * invT : 1.0, pqE[jj], dE_[jj], eE[jj], lowE[jj]);
-    }
-    const double FG = Eint + KE - eg0 + P.cr * sumR;
-    float rR[GPL], rF[GPL][3];
     const float imEc = imE * (float)P.ic;
+    const double fs = c * Et;
+    // the iterate in FP64
 #pragma unroll
     for (int j = 0; j < GPL; ++j) {
-      const double pa = __shfl_sync(mask, pqE[j], src_lane), pb = __shfl_sync(mask, pqE[j + 1], src_lane);
-      const double da = __shfl_sync(mask, dE_[j], src_lane), db_ = __shfl_sync(mask, dE_[j + 1], src_lane);
-      const int la = __shfl_sync(mask, (int)lowE[j], src_lane),
-                lb = __shfl_sync(mask, (int)lowE[j + 1], src_lane);
-      const bool last = l == L - 1;
-      const double pqU = last ? pb : pa, dU = last ? db_ : da;
-      const bool lowU = (last ? lb : la) != 0;
-      const int g = l + L * j;
-      rR[j] = 0.0f;
-      rF[j][0] = rF[j][1] = rF[j][2] = 0.0f;
-      if (g >= G) continue;
-      const double dP = band_fp64(pqE[j], lowE[j], pqU, lowU);
-      const double dD = dU - dE_[j];
-      const double b = aT4 * dP;
-      const double a = tab.alpha[g], rm = tab.rm[g], rp = tab.rp[g];
-      const double q = chiF_q<double>(b, aT4, dD, a, rm, rp, dE_[j], dU);
-      const double dnx = aT4 * (rp * dU - rm * dE_[j]);
-      const double chiB = cs * tab.kbar[g];
-      const double Enew = E0[j] + R[j];
-      const double w = (v[0] * F[j][0] + v[1] * F[j][1] + v[2] * F[j][2]) * P.inv_c2;
-      const double FR = chiB > 0.0 ? b + (1.0 + a) * q * w - R[j] * its * tab.ikbar[g] - Enew
-                                   : -R[j];
-      // the flux residual F - (eq. numF1 at this iterate), as wouter_end forms it
-      double ca, kn, kd;
-      closure_vP_parts<double>(P.closure, c, P.ic, Enew, F[j][0], F[j][1], F[j][2], v[0], v[1],
-                               v[2], ca, kn, kd);
-      const double srcg = chiB * (b - dnx * (1.0 / 3.0));
-      const double den = 1.0 + tdt * chiB * q;
-      const double dk = den * kd;
-      double inv, kf;
-      if (dk > 1e-290) {
-        const double rr = 1.0 / dk;
-        inv = kd * rr;
-        kf = kn * den * rr;
-      } else {
-        inv = 1.0 / den;
-        kf = kn / kd;
-      }
-      const double kap = tdt * (1.0 + a) * chiB * inv;
-      double FF[3];
-      for (int d = 0; d < 3; ++d) {
-        const double vp = ca * v[d] + kf * F[j][d];
-        FF[d] = F[j][d] - ((ft[j][d] + tdt * v[d] * srcg) * inv + kap * vp);
-      }
-      rR[j] = scaled_f(FR, shE) * imE;
-      for (int d = 0; d < 3; ++d) rF[j][d] = scaled_f(FF[d], shE) * imEc;
+      C.R[j] = f2d(C.rw[j]) * Et;
+      for (int d = 0; d < 3; ++d) C.F[j][d] = f2d(C.fw[j][d]) * fs;
     }
-    const float rG = scaled_f(FG, shE) * imE;
-    // ---- FP32 Jacobian at the same iterate, group blocks, sums
-    const float Tf = scaled_f(T, 0);
-    const float invTf = 1.0f / Tf;
-    const float eint = scaled_f(Eint, shE) * imE;
-    const float aT4s = scaled_f(aT4, shE) * imE;
-    const float dTs = aT4s / eint;
+    double Eint = Eint0;
+    const double irho = 1.0 / rho;
+    const double rcv = rho * P.c_v, irc = 1.0 / rcv;
     int shV;
     const float imV = 1.0f / frexp_f(rho * c, shV);
-    const float be[3] = {scaled_f(m[0], shV) * imV, scaled_f(m[1], shV) * imV,
-                         scaled_f(m[2], shV) * imV};
-    int et = 0;
-    const double tcs = tdt * cs;
-    const float mt = tcs > 0.0 ? frexp_f(tcs, et) : 0.0f;
-    float pqF[NE], dF_[NE], eF[NE];
-    bool lowF[NE];
+    const float mu = scaled_f(Et * irho * P.icc, 0);  // E_tot / (rho c c_hat)
+    int nit = W.nit[i], steps = 0, nres = 0;
+    bool finished = false, ok = true;
+    for (int k = 0; k <= kMaxCorrections; ++k) {
+      ++nres;
+      // ---- FP64 residual at the iterate: its momentum (eq. vupdate) and the
+      // sum of R_g, summed exactly
+      double dF[3] = {0.0, 0.0, 0.0}, sumR = 0.0;
 #pragma unroll
-    for (int jj = 0; jj < NE; ++jj) {
-      const int e = l + L * jj;
-      edge_tab32(pf, e <= G ? tab.xef[e] * invTf : 1.0f, pqF[jj], dF_[jj], eF[jj], lowF[jj]);
+      for (int j = 0; j < GPL; ++j) {
+        if (l + L * j >= G) continue;
+        sumR += C.R[j];
+        for (int d = 0; d < 3; ++d) dF[d] += C.F[j][d] - C.ft[j][d];
+      }
+      for (int d = 0; d < 3; ++d) dF[d] = seg_sum<L>(dF[d], mask);
+      sumR = seg_sum<L>(sumR, mask);
+      const double m[3] = {m0[0] - dF[0] * P.icc, m0[1] - dF[1] * P.icc, m0[2] - dF[2] * P.icc};
+      const double v[3] = {m[0] * irho, m[1] * irho, m[2] * irho};
+      const double KE = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) * irho;
+      const double T = Eint * irc;
+      double cs = rho * k0;
+      if (P.temp_exp != 0.0) cs *= pow(T / P.T_ref, P.temp_exp);
+      const double its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
+      int et = 0;
+      const double tcs = tdt * cs;
+      const float mt = tcs > 0.0 ? frexp_f(tcs, et) : 0.0f;
+      const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
+      const double invT = 1.0 / T;
+      double pqE[NE], dE_[NE], eE[NE];
+      bool lowE[NE];
+#pragma unroll
+      for (int jj = 0; jj < NE; ++jj) {
+        const int e = l + L * jj;
+        if (jj == NE - 1 && G == L * GPL) {  // the top edge alone (see winner_step)
+          const double xg = tab.xe[G] * invT;
+          if (xg >= 40.0 && xg < HUGE_VAL) {
+            const double em = exp(-xg);
+            const double x2 = xg * xg;
+            pqE[jj] = kPlanckNorm * em * (x2 * xg + 3.0 * x2 + 6.0 * xg + 6.0);
+            dE_[jj] = kPlanckNorm * em * x2 * x2;
+            eE[jj] = 0.0;
+            lowE[jj] = false;
+            continue;
+          }
+        }
+        edge_tab(tab.pc, e <= G ? tab.xe[e] * invT : 1.0, pqE[jj], dE_[jj], eE[jj], lowE[jj]);
+      }
+      const float be[3] = {scaled_f(m[0], shV) * imV, scaled_f(m[1], shV) * imV,
+                           scaled_f(m[2], shV) * imV};
+      float sabs = 0.0f, sdf[3] = {0.0f, 0.0f, 0.0f}, sfl = 0.0f;
+#pragma unroll
+      for (int j = 0; j < GPL; ++j) {
+        const double pa = __shfl_sync(mask, pqE[j], src_lane), pb = __shfl_sync(mask, pqE[j + 1], src_lane);
+        const double da = __shfl_sync(mask, dE_[j], src_lane), db_ = __shfl_sync(mask, dE_[j + 1], src_lane);
+        const int la = __shfl_sync(mask, (int)lowE[j], src_lane),
+                  lb = __shfl_sync(mask, (int)lowE[j + 1], src_lane);
+        const bool last = l == L - 1;
+        const double pqU = last ? pb : pa, dU = last ? db_ : da;
+        const bool lowU = (last ? lb : la) != 0;
+        const int g = l + L * j;
+        C.rR[j] = 0.0f;
+        C.rF[j][0] = C.rF[j][1] = C.rF[j][2] = 0.0f;
+        C.q[j] = 0.0f;
+        C.qe[j] = 0.0f;
+        if (g >= G) continue;
+        const double dP = band_fp64(pqE[j], lowE[j], pqU, lowU);
+        const double dD = dU - dE_[j];
+        const double b = aT4 * dP;
+        const double a = tab.alpha[g], rm = tab.rm[g], rp = tab.rp[g];
+        const double q = chiF_q<double>(b, aT4, dD, a, rm, rp, dE_[j], dU);
+        const double dnx = aT4 * (rp * dU - rm * dE_[j]);
+        const double chiB = cs * tab.kbar[g];
+        const double Enew = C.E0[j] + C.R[j];
+        const double w = (v[0] * C.F[j][0] + v[1] * C.F[j][1] + v[2] * C.F[j][2]) * P.inv_c2;
+        const double FR = chiB > 0.0 ? b + (1.0 + a) * q * w - C.R[j] * its * tab.ikbar[g] - Enew
+                                     : -C.R[j];
+        // the flux residual F - (eq. numF1 at this iterate), as wouter_end forms it
+        double ca, kn, kd;
+        closure_vP_parts<double>(P.closure, c, P.ic, Enew, C.F[j][0], C.F[j][1], C.F[j][2], v[0],
+                                 v[1], v[2], ca, kn, kd);
+        const double srcg = chiB * (b - dnx * (1.0 / 3.0));
+        const double den = 1.0 + tdt * chiB * q;
+        const double dk = den * kd;
+        double inv, kf;
+        if (dk > 1e-290) {
+          const double rr = 1.0 / dk;
+          inv = kd * rr;
+          kf = kn * den * rr;
+        } else {
+          inv = 1.0 / den;
+          kf = kn / kd;
+        }
+        const double kap = tdt * (1.0 + a) * chiB * inv;
+        C.rR[j] = scaled_f(FR, shE) * imE;
+        for (int d = 0; d < 3; ++d) {
+          const double vp = ca * v[d] + kf * C.F[j][d];
+          C.Fn[j][d] = (C.ft[j][d] + tdt * v[d] * srcg) * inv + kap * vp;
+          const double FF = C.F[j][d] - C.Fn[j][d];
+          C.rF[j][d] = scaled_f(FF, shE) * imEc;
+          sdf[d] += C.rF[j][d];
+          sfl += fabsf(C.rF[j][d]);
+        }
+        const float tau = mt * scaled_f(tab.kbar[g], -et);
+        C.q[j] = scaled_f(q, 0);
+        C.qe[j] = tau > 0.0f ? tau / (1.0f + tau) : 0.0f;
+        sabs += fabsf(C.rR[j]);
+      }
+      // ---- the paper's tests on this residual: the inner test, and the
+      // outer test on the change one more outer pass would make (fluxes
+      // F - F_F, momentum and kinetic energy from them, the v.F terms of R_g
+      // after the implicit solve), taken to first order in the change
+      const double FG = Eint + KE - eg0 + P.cr * sumR;
+      sabs = seg_sumf<L>(sabs, mask);
+      for (int d = 0; d < 3; ++d) sdf[d] = seg_sumf<L>(sdf[d], mask);
+      const float db[3] = {mu * sdf[0], mu * sdf[1], mu * sdf[2]};  // d(v/c)
+      const float mc[3] = {scaled_f(m[0] * c, shE) * imE, scaled_f(m[1] * c, shE) * imE,
+                           scaled_f(m[2] * c, shE) * imE};
+      float cg = 0.0f;
+      bool gok = true;
+#pragma unroll
+      for (int j = 0; j < GPL; ++j) {
+        const int g = l + L * j;
+        if (g >= G) continue;
+        float dw = 0.0f;
+        for (int d = 0; d < 3; ++d)
+          dw += db[d] * (C.fw[j][d] - C.rF[j][d]) - be[d] * C.rF[j][d];
+        const float cgg = fabsf((1.0f + tab.alphaf[g]) * C.q[j] * dw) * C.qe[j];
+        cg += cgg;
+        if (P.flags & RHD_GROUP_TEST) {
+          const float e0 = scaled_f(C.E0[j], shE) * imE;
+          gok = gok && cgg <= tol_o * (fabsf(e0) + fabsf(e0 + C.rw[j]));
+        }
+      }
+      float chg = fabsf(mc[0] * db[0] + mc[1] * db[1] + mc[2] * db[2]) + seg_sumf<L>(cg, mask);
+      if (P.flags & RHD_FLUX_TEST) chg += seg_sumf<L>(sfl, mask);
+      gok = __all_sync(mask, gok);
+      if (fabs(FG) < P.tol * Et && crf * sabs < tol && chg <= tol_o && gok) {
+        finished = true;
+        break;
+      }
+      if (k == kMaxCorrections || !ok) break;
+      // ---- FP32 Jacobian at the iterate, group blocks, sums, the step
+      const float rG = scaled_f(FG, shE) * imE;
+      const float Tf = scaled_f(T, 0);
+      const float invTf = 1.0f / Tf;
+      const float eint = scaled_f(Eint, shE) * imE;
+      const float aT4s = scaled_f(aT4, shE) * imE;
+      const float dTs = aT4s / eint;
+      float pqF[NE], dF_[NE], eF[NE];
+      bool lowF[NE];
+#pragma unroll
+      for (int jj = 0; jj < NE; ++jj) {
+        const int e = l + L * jj;
+        edge_tab32(pf, e <= G ? tab.xef[e] * invTf : 1.0f, pqF[jj], dF_[jj], eF[jj], lowF[jj]);
+      }
+      float sums[20];
+      for (int t = 0; t < 20; ++t) sums[t] = 0.0f;
+      GBlock blk[GPL];
+#pragma unroll
+      for (int j = 0; j < GPL; ++j) {
+        const float pa = __shfl_sync(mask, pqF[j], src_lane), pb = __shfl_sync(mask, pqF[j + 1], src_lane);
+        const float da = __shfl_sync(mask, dF_[j], src_lane), db_ = __shfl_sync(mask, dF_[j + 1], src_lane);
+        const float ea = __shfl_sync(mask, eF[j], src_lane), eb = __shfl_sync(mask, eF[j + 1], src_lane);
+        const int la = __shfl_sync(mask, (int)lowF[j], src_lane),
+                  lb = __shfl_sync(mask, (int)lowF[j + 1], src_lane);
+        const bool last = l == L - 1;
+        const int g = l + L * j;
+        if (g >= G) {
+          for (int t = 0; t < 4; ++t) blk[j].p[t] = blk[j].q[t] = 0.0f;
+          for (int t = 0; t < 12; ++t) blk[j].S[t] = 0.0f;
+          continue;
+        }
+        const float tau = mt * scaled_f(tab.kbar[g], -et);
+        const float Eg = scaled_f(C.E0[j] + C.R[j], shE) * imE;
+        const float fcur[3] = {scaled_f(C.F[j][0], shE) * imEc, scaled_f(C.F[j][1], shE) * imEc,
+                               scaled_f(C.F[j][2], shE) * imEc};
+        ok = group_jac32(P.closure, tau, tab.alphaf[g], tab.rmf[g], tab.rpf[g], pqF[j], lowF[j],
+                         dF_[j], eF[j], last ? pb : pa, (last ? lb : la) != 0, last ? db_ : da,
+                         last ? eb : ea, aT4s, dTs, Eg, fcur, be, C.rR[j], C.rF[j], blk[j]) && ok;
+        sums[0] += blk[j].p[0];
+        sums[1] += blk[j].q[0];
+        for (int t = 0; t < 3; ++t) {
+          sums[2 + t] += blk[j].S[t];
+          sums[5 + t] += blk[j].p[1 + t];
+          sums[8 + t] += blk[j].q[1 + t];
+          for (int c2 = 0; c2 < 3; ++c2) sums[11 + 3 * t + c2] += blk[j].S[3 * (1 + t) + c2];
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 20; ++t) sums[t] = seg_sumf<L>(sums[t], mask);
+      float x = 0.0f, beta[3] = {0.0f, 0.0f, 0.0f};
+      ok = global_solve(sums, rG, crf, mc, mu, x, beta) && ok;
+      ok = ok && fabsf(x) < kMaxStep;
+      float u[GPL][4];
+#pragma unroll
+      for (int j = 0; j < GPL; ++j)
+        for (int t = 0; t < 4; ++t) {
+          u[j][t] = blk[j].p[t] + blk[j].q[t] * x + blk[j].S[3 * t] * beta[0] +
+                    blk[j].S[3 * t + 1] * beta[1] + blk[j].S[3 * t + 2] * beta[2];
+          ok = ok && fabsf(u[j][t]) < kMaxStep;
+        }
+      ok = __all_sync(mask, ok);
+      if (!ok) break;  // the iterate stays the last good one
+      // ---- take the step (FP64)
+      Eint += f2d(x) * Et;
+#pragma unroll
+      for (int j = 0; j < GPL; ++j) {
+        if (l + L * j >= G) continue;
+        C.R[j] += f2d(u[j][0]) * Et;
+        for (int d = 0; d < 3; ++d) C.F[j][d] += f2d(u[j][1 + d]) * fs;
+      }
+      ++nit;
+      ++steps;
     }
-    float sums[20];
-    for (int k = 0; k < 20; ++k) sums[k] = 0.0f;
-    GBlock blk[GPL];
-    bool ok = true;
-#pragma unroll
-    for (int j = 0; j < GPL; ++j) {
-      const float pa = __shfl_sync(mask, pqF[j], src_lane), pb = __shfl_sync(mask, pqF[j + 1], src_lane);
-      const float da = __shfl_sync(mask, dF_[j], src_lane), db_ = __shfl_sync(mask, dF_[j + 1], src_lane);
-      const float ea = __shfl_sync(mask, eF[j], src_lane), eb = __shfl_sync(mask, eF[j + 1], src_lane);
-      const int la = __shfl_sync(mask, (int)lowF[j], src_lane),
-                lb = __shfl_sync(mask, (int)lowF[j + 1], src_lane);
-      const bool last = l == L - 1;
-      const int g = l + L * j;
-      if (g >= G) {
-        for (int k = 0; k < 4; ++k) blk[j].p[k] = blk[j].q[k] = 0.0f;
-        for (int k = 0; k < 12; ++k) blk[j].S[k] = 0.0f;
-        continue;
-      }
-      const float tau = mt * scaled_f(tab.kbar[g], -et);
-      const float Eg = scaled_f(E0[j], shE) * imE + rw[j];
-      ok = group_jac32(P.closure, tau, tab.alphaf[g], tab.rmf[g], tab.rpf[g], pqF[j], lowF[j],
-                       dF_[j], eF[j], last ? pb : pa, (last ? lb : la) != 0, last ? db_ : da,
-                       last ? eb : ea, aT4s, dTs, Eg, fw[j], be, rR[j], rF[j], blk[j]) && ok;
-      sums[0] += blk[j].p[0];
-      sums[1] += blk[j].q[0];
-      for (int k = 0; k < 3; ++k) {
-        sums[2 + k] += blk[j].S[k];
-        sums[5 + k] += blk[j].p[1 + k];
-        sums[8 + k] += blk[j].q[1 + k];
-        for (int c2 = 0; c2 < 3; ++c2) sums[11 + 3 * k + c2] += blk[j].S[3 * (1 + k) + c2];
-      }
+    if (l == 0) {
+      count_event(P, RHD_EV_CELLSC, 1);
+      count_event(P, RHD_EV_RESID64, nres);
+      count_event(P, RHD_EV_STEP32, steps);
+      count_event(P, RHD_EV_FINISH64, finished ? 1 : 0);
     }
+    if (finished) {
+      // ---- the end of a converged pass, as the FP64 passes end it: each
+      // R_g from its own row, the flux update (F - F_F), the conservative
+      // write-back of E_g, E_gas and the momentum in FP64
+      double sR = 0.0, sF[3] = {0.0, 0.0, 0.0};
 #pragma unroll
-    for (int k = 0; k < 20; ++k) sums[k] = seg_sumf<L>(sums[k], mask);
-    // ---- (x, beta), then each group's step
-    const float mc[3] = {scaled_f(m[0] * c, shE) * imE, scaled_f(m[1] * c, shE) * imE,
-                         scaled_f(m[2] * c, shE) * imE};
-    const float mu = scaled_f(Et * irho * P.icc, 0);
-    float x = 0.0f, beta[3] = {0.0f, 0.0f, 0.0f};
-    ok = global_solve(sums, rG, (float)P.cr, mc, mu, x, beta) && ok;
-    ok = ok && fabsf(x) < kMaxStep;
-    float u[GPL][4];
-#pragma unroll
-    for (int j = 0; j < GPL; ++j)
-      for (int k = 0; k < 4; ++k) {
-        u[j][k] = blk[j].p[k] + blk[j].q[k] * x + blk[j].S[3 * k] * beta[0] +
-                  blk[j].S[3 * k + 1] * beta[1] + blk[j].S[3 * k + 2] * beta[2];
-        ok = ok && fabsf(u[j][k]) < kMaxStep;
+      for (int j = 0; j < GPL; ++j) {
+        const int g = l + L * j;
+        if (g >= G) continue;
+        const double R = C.R[j] + f2d(C.rR[j] * C.qe[j]) * Et;
+        const int64_t o = (int64_t)g * P.gs + i;
+        P.erad[o] = C.E0[j] + R;
+        sR += R;
+        for (int d = 0; d < 3; ++d) {
+          P.frad[d][o] = C.Fn[j][d];
+          sF[d] += C.Fn[j][d] - C.ft[j][d];
+        }
       }
-    ok = __all_sync(mask, ok);
+      sR = seg_sum<L>(sR, mask);
+      for (int d = 0; d < 3; ++d) sF[d] = seg_sum<L>(sF[d], mask);
+      if (l == 0) {
+        P.egas[i] = eg0 - P.cr * sR;
+        for (int d = 0; d < 3; ++d) P.mom[d][i] = m0[d] - sF[d] * P.icc;
+        if (P.status) P.status[i] = RHD_STATUS_OK;
+        if (P.iters) P.iters[i] = (uint8_t)(nit > 255 ? 255 : nit);
+        U.done[i] = 1;
+      }
+      continue;
+    }
+    // ---- not finished: the FP64 passes start from W + U (the FP32 iterate
+    // and the steps taken here; none when no step was taken)
 #pragma unroll
     for (int j = 0; j < GPL; ++j) {
       const int g = l + L * j;
       if (g >= G) continue;
       const int64_t o = (int64_t)g * n + i;
-      U.ur[o] = ok ? u[j][0] : 0.0f;
-      for (int d = 0; d < 3; ++d) U.uf[(int64_t)d * G * n + o] = ok ? u[j][1 + d] : 0.0f;
+      U.ur[o] = steps ? scaled_f(C.R[j] - f2d(C.rw[j]) * Et, shE) * imE : 0.0f;
+      for (int d = 0; d < 3; ++d)
+        U.uf[(int64_t)d * G * n + o] =
+            steps ? scaled_f(C.F[j][d] - f2d(C.fw[j][d]) * fs, shE) * imEc : 0.0f;
     }
-    if (ok && l == 0) {
-      W.eint[i] = Eint + f2d(x) * Et;
-      // sum_g f_g of the step, from the sums and (x, beta)
-      const double ms = Et / P.c_hat;
-      for (int d = 0; d < 3; ++d) {
-        const float sf = sums[5 + d] + sums[8 + d] * x + sums[11 + 3 * d] * beta[0] +
-                         sums[11 + 3 * d + 1] * beta[1] + sums[11 + 3 * d + 2] * beta[2];
-        W.mom[(int64_t)d * n + i] = m[d] - ms * f2d(sf);
+    double dF[3] = {0.0, 0.0, 0.0};
+    if (steps) {
+#pragma unroll
+      for (int j = 0; j < GPL; ++j)
+        if (l + L * j < G)
+          for (int d = 0; d < 3; ++d) dF[d] += C.F[j][d] - C.ft[j][d];
+      for (int d = 0; d < 3; ++d) dF[d] = seg_sum<L>(dF[d], mask);
+    }
+    if (l == 0) {
+      if (steps) {
+        W.eint[i] = Eint;
+        for (int d = 0; d < 3; ++d) W.mom[(int64_t)d * n + i] = m0[d] - dF[d] * P.icc;
+        W.nit[i] = (uint8_t)(nit > 255 ? 255 : nit);
       }
+      U.done[i] = 0;
     }
   }
 }

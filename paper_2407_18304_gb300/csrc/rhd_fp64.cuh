@@ -81,6 +81,7 @@ struct Cell {
   int fresh;       // the last inner step converged: FR_g ~ 0 at the current T, R_g
   int cached;      // A.FR holds the residual at the current T, R_g (see inner_cached)
   int use_cache;   // take the cached first iteration of a pass (see outer_end)
+  unsigned nfn;    // group flux updates solved by Newton steps
 };
 
 // Thread-local per-group arrays of the FP64 passes.
@@ -311,13 +312,14 @@ __device__ __noinline__ FluxDelta flux_newton_pass(
     const double *R, const double *bq, const double *dnx, const double *qF, double *Fk, double c,
     double tdt, double cs, double v0, double v1, double v2) {
   const double vmag = sqrt(v0 * v0 + v1 * v1 + v2 * v2);
-  FluxDelta d = {0.0, 0.0, 0.0, 0.0};
+  FluxDelta d = {0.0, 0.0, 0.0, 0.0, 0};
   for (int g = 0; g < G; ++g) {
     const int64_t o = (int64_t)g * gs + i;
     const double chiE = cs * kE[g];
     const double inv = 1.0 / (1.0 + tdt * chiE * qF[g]);
     const double kap = tdt * (1.0 + alpha[g]) * chiE * inv;
     if (!(10.0 * fabs(kap) * vmag > c)) continue;
+    ++d.n;
     const double s = src ? src[o] : 0.0;
     const double Enew = erad[o] + R[g] + s;
     const double srcg = chiE * (bq[g] - dnx[g] * (1.0 / 3.0));
@@ -409,6 +411,7 @@ __device__ __forceinline__ bool outer_end(const KParams &P, const GroupTable &ta
     dF[1] += d.y;
     dF[2] += d.z;
     fchg += d.l1;
+    C.nfn += d.n;
   }
   // ---- a11: momentum update
   const double mn[3] = {C.m0[0] - dF[0] * icc, C.m0[1] - dF[1] * icc, C.m0[2] - dF[2] * icc};
@@ -496,6 +499,7 @@ struct WarmStart {
   int fallback;        // a cell whose warm-started solve fails is solved again from the cold start
   const float *ur;     // [G][n] correction step of R_g / E_tot (rhd_correct.cuh), or null
   const float *uf;     // [3][G][n] correction step of F_g / (c E_tot), or null
+  const uint8_t *done; // [n] 1: the correction step finished the cell (skip it), or null
 };
 
 template <int MAXG>
@@ -546,8 +550,11 @@ __global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const bool warm = W.r != nullptr;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
+    if (W.done && W.done[i]) continue;
     if (!load_cell(P, i, C, A)) continue;
     C.use_cache = CACHE;
+    C.nfn = 0;
+    unsigned ne = 0, nc = 0, no = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
       int nit0 = 0;
       if (attempt == 1) {
@@ -560,9 +567,12 @@ __global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__
       if (warm && attempt == 0) apply_warm(P, W, C, A);
       outer_begin(P, C, A);
       for (;;) {
+        if (CACHE && C.cached) ++nc;
+        else ++ne;
         const int r = inner_step<MAXG, CACHE>(P, tab, C, A);
         if (r == 0) continue;
         if (r == 2) C.stat = RHD_STATUS_MAXITER;
+        ++no;
         if (outer_end(P, tab, C, A)) break;
       }
       if (attempt == 1) {
@@ -571,6 +581,11 @@ __global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__
       }
     }
     store_cell(P, C, A);
+    count_event(P, RHD_EV_CELLS64, 1);
+    count_event(P, RHD_EV_EVAL64, ne);
+    count_event(P, RHD_EV_CACHED64, nc);
+    count_event(P, RHD_EV_OUTER64, no);
+    count_event(P, RHD_EV_FLUXNEWTON, C.nfn);
   }
 }
 

@@ -183,7 +183,7 @@ __device__ __forceinline__ int inner_step32(const KParams &P, const GroupTable &
   const int G = P.G;
   const float cr = (float)P.cr;
   const double Etot = C.Etot, sE = D.sE;
-  const float tol32 = 2e-6f;
+  const float tol32 = 1e-7f;  // near FP32 resolution: the correction step then needs one Newton step
   const int max_it = P.max_newton < 32 ? P.max_newton : 32;
   const double T = C.Eint * C.irc;
   if (P.temp_exp != 0.0) set_tau32(P, tab, B, C.chi0s * pow(T / P.T_ref, P.temp_exp));
@@ -298,7 +298,7 @@ __device__ __forceinline__ bool outer_end32(const KParams &P, const GroupTable &
   C.Eint = egas_new - KEn;  // start of the next pass (or of the FP64 phase)
   if (!(C.Eint > 0.0)) C.Eint = C.eg0 - C.KE;
   ++C.outer;
-  if (chg <= 1e-6f || C.outer >= P.max_outer) return true;
+  if (chg <= 3e-8f || C.outer >= P.max_outer) return true;
   outer_begin32(P, C, D, B);
   return false;
 }
@@ -309,6 +309,7 @@ struct WarmOut {
   float *r, *f;
   uint8_t *nit;
   float *ur, *uf;  // the correction step (rhd_correct.cuh)
+  uint8_t *done;   // [n] cells the correction step finished
 };
 
 template <int MAXG>
@@ -343,7 +344,9 @@ __global__ void __launch_bounds__(128) warm_fp32_kernel(const __grid_constant__ 
   Cell32 D;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned ne = 0, no = 0;
   auto next = [&]() -> bool {
+    ne = no = 0;
     while (i < P.n) {
       if (load_cell32(P, tab, i, C, D, B)) {
         if (S.r && S.eint[i] > 0.0) {
@@ -361,8 +364,13 @@ __global__ void __launch_bounds__(128) warm_fp32_kernel(const __grid_constant__ 
   while (__any_sync(0xffffffffu, active)) {
     if (active) {
       const int r = inner_step32(P, tab, C, D, B);
+      ++ne;
+      if (r != 0) ++no;
       if (r != 0 && outer_end32(P, tab, C, D, B)) {
         store_warm(P, W, C, B);
+        count_event(P, RHD_EV_CELLS32, 1);
+        count_event(P, RHD_EV_EVAL32, ne);
+        count_event(P, RHD_EV_OUTER32, no);
         i += stride;
         active = next();
       }

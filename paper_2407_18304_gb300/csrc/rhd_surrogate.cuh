@@ -563,7 +563,10 @@ int launch_fused(rhd_surrogate *s, const KParams &kp, const WarmOut &W, bool ful
   const int64_t pairs = (tiles + mlp::kFusedGroups - 1) / mlp::kFusedGroups;
   const int blocks = (int)(pairs < sms ? pairs : sms);
   if (blocks > 0)
-    mlp::infer_fused_kernel<<<blocks, 128 * mlp::kFusedGroups, smem, st>>>(kp, N, W);
+    timed_launch(RHD_KERNEL_INFERENCE, st, [&] {
+      mlp::infer_fused_kernel<<<blocks, 128 * mlp::kFusedGroups, smem, st>>>(kp, N, W);
+    });
+  if (kp.count) t_infer_cells += (unsigned long long)kp.n;
   return cudaGetLastError() == cudaSuccess ? RHD_OK : RHD_ECUDA;
 }
 

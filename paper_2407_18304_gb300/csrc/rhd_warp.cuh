@@ -24,6 +24,7 @@ struct WCell {
   double m[3], v[3], KE, Eint, egas_new, cs, its, chg_prev;
   int nit, stat, it, outer, slow;
   int fresh, cached;  // as Cell::fresh, Cell::cached
+  unsigned nfn;       // group flux updates this lane solved by Newton steps
   double R[GPL], w[GPL], FR[GPL], dg[GPL], qe[GPL], bq[GPL], dnx[GPL], qF[GPL];
   double itau[GPL];   // 1/tau_E of the group (0 when uncoupled)
   double E0[GPL];     // E_g^t + S_g
@@ -384,6 +385,7 @@ __device__ __forceinline__ bool wouter_end(const KParams &P, const GroupTable &t
       if (!(kap * kap * v2c > c2)) continue;
       const double srcg = chiB * (C.bq[j] - C.dnx[j] * (1.0 / 3.0));
       const int64_t o = (int64_t)g * P.gs + C.i;
+      ++C.nfn;
       const Vec3<double> F = flux_newton<double>(
           c, C.E0[j] + C.R[j], kap, (P.frad[0][o] + tdt * v[0] * srcg) * inv,
           (P.frad[1][o] + tdt * v[1] * srcg) * inv, (P.frad[2][o] + tdt * v[2] * srcg) * inv, v[0],
@@ -489,7 +491,10 @@ __global__ void __launch_bounds__(128) solve_warp_kernel(const __grid_constant__
   const bool warm = W.r != nullptr;
   WCell<L, GPL> C;
   for (int64_t i = warp * CPW + seg; i < P.n; i += nwarps * CPW) {
+    if (W.done && W.done[i]) continue;
     if (!wload(P, i, l, mask, C)) continue;
+    unsigned ne = 0, nc = 0, no = 0;
+    C.nfn = 0;
     for (int attempt = 0; attempt < 2; ++attempt) {
       int nit0 = 0;
       if (attempt == 1) {
@@ -501,9 +506,12 @@ __global__ void __launch_bounds__(128) solve_warp_kernel(const __grid_constant__
       if (warm && attempt == 0) wapply_warm(P, W, l, C);
       wouter_begin(P, C);
       for (;;) {
+        if (C.cached) ++nc;
+        else ++ne;
         const int r = winner_step(P, tab, l, lane0, mask, C);
         if (r == 0) continue;
         if (r == 2) C.stat = RHD_STATUS_MAXITER;
+        ++no;
         if (wouter_end(P, tab, l, mask, C)) break;
       }
       if (attempt == 1) {
@@ -512,6 +520,16 @@ __global__ void __launch_bounds__(128) solve_warp_kernel(const __grid_constant__
       }
     }
     wstore(P, l, C);
+    if (P.count) {
+      const unsigned nfn = __reduce_add_sync(mask, C.nfn);
+      if (l == 0) {
+        count_event(P, RHD_EV_CELLS64, 1);
+        count_event(P, RHD_EV_EVAL64, ne);
+        count_event(P, RHD_EV_CACHED64, nc);
+        count_event(P, RHD_EV_OUTER64, no);
+        count_event(P, RHD_EV_FLUXNEWTON, nfn);
+      }
+    }
   }
 }
 

@@ -202,7 +202,7 @@ __device__ __forceinline__ int w32_inner_step(const KParams &P, const GroupTable
   constexpr int NE = GPL + 1;
   const int G = P.G;
   const float cr = (float)P.cr;
-  const float tol32 = 2e-6f;
+  const float tol32 = 1e-7f;  // near FP32 resolution: the correction step then needs one Newton step
   const int max_it = P.max_newton < 32 ? P.max_newton : 32;
   const float eint = C.eb + C.dlt;          // E_int / E_tot
   const float t = eint / C.eb;              // T / T0
@@ -344,7 +344,7 @@ __device__ __forceinline__ bool w32_outer_end(const KParams &P, const GroupTable
   C.Eint = egas_new - KEn;  // the next pass's base (or the FP64 phase's start)
   if (!(C.Eint > 0.0)) C.Eint = C.eg0 - C.KE;
   ++C.outer;
-  if (chg <= 1e-6f || C.outer >= P.max_outer) return true;
+  if (chg <= 3e-8f || C.outer >= P.max_outer) return true;
   w32_outer_begin(P, C);
   return false;
 }
@@ -407,11 +407,20 @@ __global__ void __launch_bounds__(128) warm_warp32_kernel(const __grid_constant_
       }
     }
     w32_outer_begin(P, C);
+    unsigned ne = 0, no = 0;
     for (;;) {
       const int r = w32_inner_step(P, tab, pf, l, lane0, mask, C);
-      if (r != 0 && w32_outer_end(P, tab, l, mask, C)) break;
+      ++ne;
+      if (r == 0) continue;
+      ++no;
+      if (w32_outer_end(P, tab, l, mask, C)) break;
     }
     w32_store(P, W, l, C);
+    if (l == 0) {
+      count_event(P, RHD_EV_CELLS32, 1);
+      count_event(P, RHD_EV_EVAL32, ne);
+      count_event(P, RHD_EV_OUTER32, no);
+    }
   }
 }
 

@@ -136,6 +136,13 @@ def lib() -> ctypes.CDLL:
                                        ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _P]
         _lib.rhd_profile_start.restype = ctypes.c_int
         _lib.rhd_profile_start.argtypes = []
+        _lib.rhd_profile_kernel.restype = ctypes.c_int
+        _lib.rhd_profile_kernel.argtypes = [ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                            ctypes.POINTER(ctypes.c_double)]
+        _lib.rhd_events_start.restype = ctypes.c_int
+        _lib.rhd_events_start.argtypes = []
+        _lib.rhd_events_stop.restype = ctypes.c_int
+        _lib.rhd_events_stop.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
         _lib.rhd_profile_stop.restype = ctypes.c_int
         _lib.rhd_profile_stop.argtypes = [ctypes.POINTER(ctypes.c_int32),
                                           ctypes.POINTER(ctypes.c_double)]
@@ -620,8 +627,14 @@ class Surrogate:
         del keep
 
 
+KERNEL_FP32, KERNEL_CORRECTION, KERNEL_FP64, KERNEL_INFERENCE = 0, 1, 2, 3
+KERNEL_NAMES = ("fp32_passes", "correction", "fp64_passes", "inference")
+EVENT_NAMES = ("cells32", "eval32", "outer32", "cellsc", "resid64", "step32", "finish64",
+               "cells64", "eval64", "cached64", "outer64", "fluxnewton", "infer")
+
+
 def profile_start() -> None:
-    """Start timing the FP64-pass kernel of this thread's update calls."""
+    """Start timing the solver launches of this thread's update calls."""
     _raise(lib().rhd_profile_start())
 
 
@@ -630,6 +643,25 @@ def profile_stop() -> tuple[int, float]:
     n, ms = ctypes.c_int32(), ctypes.c_double()
     _raise(lib().rhd_profile_stop(ctypes.byref(n), ctypes.byref(ms)))
     return n.value, ms.value
+
+
+def profile_kernel(kind: int) -> tuple[int, float]:
+    """(launches, summed ms) of one kind of launch (KERNEL_*) at the last profile_stop."""
+    n, ms = ctypes.c_int32(), ctypes.c_double()
+    _raise(lib().rhd_profile_kernel(int(kind), ctypes.byref(n), ctypes.byref(ms)))
+    return n.value, ms.value
+
+
+def events_start() -> None:
+    """Zero the device's event counters and count this thread's update calls."""
+    _raise(lib().rhd_events_start())
+
+
+def events_stop() -> dict:
+    """Stop counting; {event name: count} (include/rhd.h, RHD_EV_*)."""
+    buf = (ctypes.c_uint64 * len(EVENT_NAMES))()
+    _raise(lib().rhd_events_stop(buf))
+    return dict(zip(EVENT_NAMES, (int(x) for x in buf)))
 
 
 def strerror(code: int) -> str:

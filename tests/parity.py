@@ -140,3 +140,24 @@ def agreed(label: str, *gpu: dict, oracle: dict, fallback_ok: bool = False,
 def select(r: dict, ok: np.ndarray) -> dict:
     return {k: (v[..., ok] if isinstance(v, np.ndarray) and v.shape[-1] == len(ok) else v)
             for k, v in r.items()}
+
+
+def root_residual(res: dict, st0: dict, w, i: int, groups=None) -> tuple[float, float]:
+    """The residual of the fully coupled per-cell system (eqs. FGFR, Rnew and
+    fupdate with the momentum of eq. vupdate; the oracle side's FP64
+    evaluation in oracle/opcount.py) at cell i of a result: (sum_g |F_R,g| /
+    E_tot, max |F_F,g| / (c E_tot)).  Both are at round-off for a root."""
+    from oracle import opcount as OC
+    groups = oracle_groups(w) if groups is None else groups
+    p = O.Params(c=w.consts["c"], c_hat=w.consts["c_hat"], a_rad=w.consts["a_rad"],
+                 h=w.consts["h"], k_B=w.consts["k_B"], c_v=w.c_v, dt=w.dt)
+    cell = OC.make_cell(st0, i, p, groups)
+    OC.setup(cell)
+    ms = res["mom"][:, i]
+    cell.Eint = OC.Num(res["egas"][i] - 0.5 * ms @ ms / cell.rho)
+    cell.R = [OC.Num(res["erad"][g, i] - cell.E0[g]) for g in range(cell.G)]
+    cell.F = [[OC.Num(res["frad"][d, g, i]) for d in range(3)] for g in range(cell.G)]
+    _, r = OC.coupled_residual(cell, 0.0, 0.0)
+    et = st0["egas"][i] + st0["erad"][:, i].sum()
+    return (sum(abs(x.v) for x in r["FR"]) / et,
+            max(abs(x.v) for f in r["FF"] for x in f) / (w.consts["c"] * et))

