@@ -378,7 +378,8 @@ void launch_fp32_passes(const KParams &kp, const WarmOut &wo, const WarmStart &S
 template <int L, int GPL>
 void launch_correct_k(const KParams &kp, const WarmOut &wo, int sms, cudaStream_t st) {
   const int threads = 128;
-  const size_t smem = table_bytes(kp.G);
+  const size_t smem = correct_smem_bytes(kp.G, GPL, threads);
+  if (smem > 48 * 1024) allow_smem<correct_warp_kernel<L, GPL>>(smem);
   const int b = persistent_blocks(correct_warp_kernel<L, GPL>, smem, sms, kp.n * L, threads);
   correct_warp_kernel<L, GPL><<<b, threads, smem, st>>>(kp, wo, CorrOut{wo.ur, wo.uf, wo.done});
 }

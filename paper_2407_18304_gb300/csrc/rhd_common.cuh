@@ -10,6 +10,7 @@
 // chi_0(nu_g-) D(x_g-)] with chi_0 at each edge from group g's own powerlaw.
 #pragma once
 #include <cstdint>
+#include <mutex>
 #include <cuda_runtime.h>
 
 #include "../../include/rhd.h"
@@ -217,6 +218,26 @@ __device__ __forceinline__ double f2d(float f) {
 __device__ __forceinline__ bool usable_energy(double x) {
   const int hi = __double2hiint(x);
   return hi >= 0 && ((hi >> 20) & 0x7FF) >= 60 && ((hi >> 20) & 0x7FF) < 0x7FF;
+}
+
+// Allow `kernel` smem bytes of dynamic shared memory on the current device.
+// The attribute belongs to the (kernel, device) pair, so the largest size set
+// so far is remembered per device (one table per kernel instance, under a
+// lock: launches may come from several host threads).
+constexpr int kAttrDevices = 64;
+template <auto kernel>
+cudaError_t allow_smem(size_t smem) {
+  static std::mutex mu;
+  static size_t done[kAttrDevices];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kAttrDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev] >= smem) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) done[dev] = smem;
+  return e;
 }
 
 // (This header is compiled into exactly one translation unit, rhd.cu.)

@@ -42,17 +42,6 @@ struct CorrOut {
   uint8_t *done;  // [n]
 };
 
-// FP32 copy of the Planck polynomials cut to degree kDeg32 (as the FP32
-// passes use them), loaded into shared memory by all threads.
-__device__ __forceinline__ void load_planck32(const GroupTable &tab, float *pf) {
-  using namespace planck_table;
-  for (int t = threadIdx.x; t < kPlanckF; t += blockDim.x) {
-    const int k = t / kSeg, s = t % kSeg;
-    const int src = k <= kDeg32 ? k * kSeg + s : (kDeg + 1 + (k - kDeg32 - 1)) * kSeg + s;
-    pf[t] = (float)tab.pc[src];
-  }
-}
-
 // The closure in units with c = 1 (E, F / c, v / c): v.P, M = d(v.P)/dF at
 // fixed E, dE = d(v.P)/dE at fixed F, and P itself (d(v.P)/dv).  M1 as in
 // closure_vP_jac (Levermore's chi(f), f held at 1); Eddington P = E/3 I.
@@ -253,6 +242,15 @@ __device__ __forceinline__ bool global_solve(const float s[20], float rG, float 
   return isfinite(x) && isfinite(beta[0]) && isfinite(beta[1]) && isfinite(beta[2]);
 }
 
+// Dynamic shared memory of the correction kernel: the group table, then
+// GPL * 20 floats per thread for the group blocks.
+__host__ __device__ __forceinline__ size_t correct_smem_bytes(int G, int GPL, int threads) {
+  return ((table_bytes(G) + 15) & ~(size_t)15) + sizeof(float) * 20 * GPL * threads;
+}
+__device__ __forceinline__ float *correct_blocks(double *sm, int G) {
+  return reinterpret_cast<float *>(reinterpret_cast<char *>(sm) + ((table_bytes(G) + 15) & ~(size_t)15));
+}
+
 // A step is taken only when it is small against the cell's energy scale:
 // the FP32 passes leave the iterate at FP32 accuracy, so a larger step means
 // they stopped at a cap, and the FP64 passes take the cell from there.
@@ -265,7 +263,6 @@ constexpr int kMaxCorrections = 3;
 template <int GPL>
 struct CCell {
   double E0[GPL], R[GPL], F[GPL][3], ft[GPL][3];  // E^t + S, iterate, F^t
-  double Fn[GPL][3];                               // eq. numF1 at the iterate
   float rw[GPL], fw[GPL][3];                       // the FP32 iterate (scaled)
   float rR[GPL], rF[GPL][3], q[GPL], qe[GPL];      // scaled residual, chi_F/chi_E, tau/(1+tau)
 };
@@ -284,12 +281,12 @@ template <int L, int GPL>
 __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant__ KParams P,
                                                            const WarmOut W, const CorrOut U) {
   extern __shared__ double sm[];
-  __shared__ float pf[kPlanckF];
   const GroupTable tab = build_table(P, sm);
-  load_planck32(tab, pf);
-  __syncthreads();
   constexpr int NE = GPL + 1;
   const int lane = threadIdx.x & 31, seg = lane / L, l = lane % L, lane0 = seg * L;
+  // each lane's group blocks (p, q, S: 20 floats per group slot) between the
+  // elimination and the step, lane-fastest (no bank conflicts)
+  float *gb = correct_blocks(sm, P.G) + (threadIdx.x / 32) * (GPL * 20 * 32);
   const unsigned mask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << lane0);
   constexpr int CPW = 32 / L;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
@@ -358,6 +355,10 @@ __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant
     int shV;
     const float imV = 1.0f / frexp_f(rho * c, shV);
     const float mu = scaled_f(Et * irho * P.icc, 0);  // E_tot / (rho c c_hat)
+    double cs = rho * k0;  // rho kappa0 (T/T_ref)^p
+    double its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
+    int et = 0;
+    float mt = tdt * cs > 0.0 ? frexp_f(tdt * cs, et) : 0.0f;  // c_hat theta dt cs = mt 2^et
     int nit = W.nit[i], steps = 0, nres = 0;
     bool finished = false, ok = true;
     for (int k = 0; k <= kMaxCorrections; ++k) {
@@ -377,12 +378,11 @@ __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant
       const double v[3] = {m[0] * irho, m[1] * irho, m[2] * irho};
       const double KE = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) * irho;
       const double T = Eint * irc;
-      double cs = rho * k0;
-      if (P.temp_exp != 0.0) cs *= pow(T / P.T_ref, P.temp_exp);
-      const double its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
-      int et = 0;
-      const double tcs = tdt * cs;
-      const float mt = tcs > 0.0 ? frexp_f(tcs, et) : 0.0f;
+      if (P.temp_exp != 0.0) {  // the opacity scale follows T (otherwise set once per cell)
+        cs = rho * k0 * pow(T / P.T_ref, P.temp_exp);
+        its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
+        mt = tdt * cs > 0.0 ? frexp_f(tdt * cs, et) : 0.0f;
+      }
       const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
       const double invT = 1.0 / T;
       double pqE[NE], dE_[NE], eE[NE];
@@ -397,12 +397,22 @@ __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant
             const double x2 = xg * xg;
             pqE[jj] = kPlanckNorm * em * (x2 * xg + 3.0 * x2 + 6.0 * xg + 6.0);
             dE_[jj] = kPlanckNorm * em * x2 * x2;
-            eE[jj] = 0.0;
+            eE[jj] = dE_[jj] * (4.0 - xg);
             lowE[jj] = false;
             continue;
           }
         }
         edge_tab(tab.pc, e <= G ? tab.xe[e] * invT : 1.0, pqE[jj], dE_[jj], eE[jj], lowE[jj]);
+      }
+      // the same edge values in FP32 for the Jacobian (bit-pattern cut, no FP64 instruction)
+      float pqF[NE], dF_[NE], eF[NE];
+      bool lowF[NE];
+#pragma unroll
+      for (int jj = 0; jj < NE; ++jj) {
+        pqF[jj] = scaled_f(pqE[jj], 0);
+        dF_[jj] = scaled_f(dE_[jj], 0);
+        eF[jj] = scaled_f(eE[jj], 0);
+        lowF[jj] = lowE[jj];
       }
       const float be[3] = {scaled_f(m[0], shV) * imV, scaled_f(m[1], shV) * imV,
                            scaled_f(m[2], shV) * imV};
@@ -453,8 +463,11 @@ __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant
         C.rR[j] = scaled_f(FR, shE) * imE;
         for (int d = 0; d < 3; ++d) {
           const double vp = ca * v[d] + kf * C.F[j][d];
-          C.Fn[j][d] = (C.ft[j][d] + tdt * v[d] * srcg) * inv + kap * vp;
-          const double FF = C.F[j][d] - C.Fn[j][d];
+          // eq. numF1 at the iterate: the cell's flux if this evaluation finishes
+          // it (the state's array holds it meanwhile; F^t stays in C.ft)
+          const double Fn = (C.ft[j][d] + tdt * v[d] * srcg) * inv + kap * vp;
+          P.frad[d][(int64_t)g * P.gs + i] = Fn;
+          const double FF = C.F[j][d] - Fn;
           C.rF[j][d] = scaled_f(FF, shE) * imEc;
           sdf[d] += C.rF[j][d];
           sfl += fabsf(C.rF[j][d]);
@@ -472,8 +485,9 @@ __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant
       sabs = seg_sumf<L>(sabs, mask);
       for (int d = 0; d < 3; ++d) sdf[d] = seg_sumf<L>(sdf[d], mask);
       const float db[3] = {mu * sdf[0], mu * sdf[1], mu * sdf[2]};  // d(v/c)
-      const float mc[3] = {scaled_f(m[0] * c, shE) * imE, scaled_f(m[1] * c, shE) * imE,
-                           scaled_f(m[2] * c, shE) * imE};
+      const float cf = (float)c;
+      const float mc[3] = {scaled_f(m[0], shE) * imE * cf, scaled_f(m[1], shE) * imE * cf,
+                           scaled_f(m[2], shE) * imE * cf};  // m c / E_tot
       float cg = 0.0f;
       bool gok = true;
 #pragma unroll
@@ -500,21 +514,11 @@ __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant
       if (k == kMaxCorrections || !ok) break;
       // ---- FP32 Jacobian at the iterate, group blocks, sums, the step
       const float rG = scaled_f(FG, shE) * imE;
-      const float Tf = scaled_f(T, 0);
-      const float invTf = 1.0f / Tf;
       const float eint = scaled_f(Eint, shE) * imE;
       const float aT4s = scaled_f(aT4, shE) * imE;
       const float dTs = aT4s / eint;
-      float pqF[NE], dF_[NE], eF[NE];
-      bool lowF[NE];
-#pragma unroll
-      for (int jj = 0; jj < NE; ++jj) {
-        const int e = l + L * jj;
-        edge_tab32(pf, e <= G ? tab.xef[e] * invTf : 1.0f, pqF[jj], dF_[jj], eF[jj], lowF[jj]);
-      }
       float sums[20];
       for (int t = 0; t < 20; ++t) sums[t] = 0.0f;
-      GBlock blk[GPL];
 #pragma unroll
       for (int j = 0; j < GPL; ++j) {
         const float pa = __shfl_sync(mask, pqF[j], src_lane), pb = __shfl_sync(mask, pqF[j + 1], src_lane);
@@ -525,25 +529,30 @@ __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant
         const bool last = l == L - 1;
         const int g = l + L * j;
         if (g >= G) {
-          for (int t = 0; t < 4; ++t) blk[j].p[t] = blk[j].q[t] = 0.0f;
-          for (int t = 0; t < 12; ++t) blk[j].S[t] = 0.0f;
+          for (int t = 0; t < 20; ++t) gb[(j * 20 + t) * 32 + lane] = 0.0f;
           continue;
         }
         const float tau = mt * scaled_f(tab.kbar[g], -et);
         const float Eg = scaled_f(C.E0[j] + C.R[j], shE) * imE;
         const float fcur[3] = {scaled_f(C.F[j][0], shE) * imEc, scaled_f(C.F[j][1], shE) * imEc,
                                scaled_f(C.F[j][2], shE) * imEc};
+        GBlock blk;
         ok = group_jac32(P.closure, tau, tab.alphaf[g], tab.rmf[g], tab.rpf[g], pqF[j], lowF[j],
                          dF_[j], eF[j], last ? pb : pa, (last ? lb : la) != 0, last ? db_ : da,
-                         last ? eb : ea, aT4s, dTs, Eg, fcur, be, C.rR[j], C.rF[j], blk[j]) && ok;
-        sums[0] += blk[j].p[0];
-        sums[1] += blk[j].q[0];
+                         last ? eb : ea, aT4s, dTs, Eg, fcur, be, C.rR[j], C.rF[j], blk) && ok;
+        sums[0] += blk.p[0];
+        sums[1] += blk.q[0];
         for (int t = 0; t < 3; ++t) {
-          sums[2 + t] += blk[j].S[t];
-          sums[5 + t] += blk[j].p[1 + t];
-          sums[8 + t] += blk[j].q[1 + t];
-          for (int c2 = 0; c2 < 3; ++c2) sums[11 + 3 * t + c2] += blk[j].S[3 * (1 + t) + c2];
+          sums[2 + t] += blk.S[t];
+          sums[5 + t] += blk.p[1 + t];
+          sums[8 + t] += blk.q[1 + t];
+          for (int c2 = 0; c2 < 3; ++c2) sums[11 + 3 * t + c2] += blk.S[3 * (1 + t) + c2];
         }
+        for (int t = 0; t < 4; ++t) {
+          gb[(j * 20 + t) * 32 + lane] = blk.p[t];
+          gb[(j * 20 + 4 + t) * 32 + lane] = blk.q[t];
+        }
+        for (int t = 0; t < 12; ++t) gb[(j * 20 + 8 + t) * 32 + lane] = blk.S[t];
       }
 #pragma unroll
       for (int t = 0; t < 20; ++t) sums[t] = seg_sumf<L>(sums[t], mask);
@@ -554,8 +563,10 @@ __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant
 #pragma unroll
       for (int j = 0; j < GPL; ++j)
         for (int t = 0; t < 4; ++t) {
-          u[j][t] = blk[j].p[t] + blk[j].q[t] * x + blk[j].S[3 * t] * beta[0] +
-                    blk[j].S[3 * t + 1] * beta[1] + blk[j].S[3 * t + 2] * beta[2];
+          u[j][t] = gb[(j * 20 + t) * 32 + lane] + gb[(j * 20 + 4 + t) * 32 + lane] * x +
+                    gb[(j * 20 + 8 + 3 * t) * 32 + lane] * beta[0] +
+                    gb[(j * 20 + 9 + 3 * t) * 32 + lane] * beta[1] +
+                    gb[(j * 20 + 10 + 3 * t) * 32 + lane] * beta[2];
           ok = ok && fabsf(u[j][t]) < kMaxStep;
         }
       ok = __all_sync(mask, ok);
@@ -590,10 +601,7 @@ __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant
         const int64_t o = (int64_t)g * P.gs + i;
         P.erad[o] = C.E0[j] + R;
         sR += R;
-        for (int d = 0; d < 3; ++d) {
-          P.frad[d][o] = C.Fn[j][d];
-          sF[d] += C.Fn[j][d] - C.ft[j][d];
-        }
+        for (int d = 0; d < 3; ++d) sF[d] += P.frad[d][o] - C.ft[j][d];
       }
       sR = seg_sum<L>(sR, mask);
       for (int d = 0; d < 3; ++d) sF[d] = seg_sum<L>(sF[d], mask);
@@ -607,11 +615,12 @@ __global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant
       continue;
     }
     // ---- not finished: the FP64 passes start from W + U (the FP32 iterate
-    // and the steps taken here; none when no step was taken)
+    // and the steps taken here; none when no step was taken), from F^t
 #pragma unroll
     for (int j = 0; j < GPL; ++j) {
       const int g = l + L * j;
       if (g >= G) continue;
+      for (int d = 0; d < 3; ++d) P.frad[d][(int64_t)g * P.gs + i] = C.ft[j][d];
       const int64_t o = (int64_t)g * n + i;
       U.ur[o] = steps ? scaled_f(C.R[j] - f2d(C.rw[j]) * Et, shE) * imE : 0.0f;
       for (int d = 0; d < 3; ++d)

@@ -558,7 +558,7 @@ int launch_fused(rhd_surrogate *s, const KParams &kp, const WarmOut &W, bool ful
   N.full = full ? 1 : 0;
   N.err = s->err;
   const size_t smem = mlp::fused_bytes(N.k1, N.n4);
-  if (tc::allow_smem<mlp::infer_fused_kernel>(smem) != cudaSuccess) return RHD_ECUDA;
+  if (allow_smem<mlp::infer_fused_kernel>(smem) != cudaSuccess) return RHD_ECUDA;
   const int64_t tiles = (kp.n + tc::kTileM - 1) / tc::kTileM;
   const int64_t pairs = (tiles + mlp::kFusedGroups - 1) / mlp::kFusedGroups;
   const int blocks = (int)(pairs < sms ? pairs : sms);

@@ -14,7 +14,6 @@
 // raises an error flag and skips the rest (the context stays usable).
 #pragma once
 #include <cstdint>
-#include <mutex>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -274,26 +273,6 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
 }
 
 __host__ constexpr size_t gemm_smem_bytes(int NT) { return (size_t)kStageA + (size_t)NT * kChunkK * 2; }
-
-// Allow `kernel` smem bytes of dynamic shared memory on the current device.
-// The attribute belongs to the (kernel, device) pair, so the largest size set
-// so far is remembered per device (one table per kernel instance, under a
-// lock: launches may come from several host threads).
-constexpr int kAttrDevices = 64;
-template <auto kernel>
-cudaError_t allow_smem(size_t smem) {
-  static std::mutex mu;
-  static size_t done[kAttrDevices];
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kAttrDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(mu);
-  if (done[dev] >= smem) return cudaSuccess;
-  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e == cudaSuccess) done[dev] = smem;
-  return e;
-}
 
 template <int NT, int TCOLS>
 cudaError_t launch_nt(const GemmArgs &g, cudaStream_t st) {
