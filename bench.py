@@ -176,7 +176,7 @@ KERNEL_CELLS = {"correction": "cellsc", "fp64_passes": "cells64"}
 # DRAM bytes (read + write) per cell-group of one launch of the dominant kernel,
 # ncu on a 65536-cell sample of the same workload
 # (profiles/correct_warp_kernel_65536cells_ng64.md); None once the kernel changed
-DOMINANT_TRAFFIC_PER_CG = {("full_256cube_ng64", "correction"): None}
+DOMINANT_TRAFFIC_PER_CG = {("full_256cube_ng64", "correction"): 69.4}
 
 
 def op_slots(counts: dict, weights: dict) -> float:

@@ -287,6 +287,14 @@ int rhd_surrogate_train_step(rhd_surrogate_t *s, const float *x, const float *y,
 int rhd_surrogate_predict(rhd_surrogate_t *s, const float *x, int64_t n, float *y, void *stream);
 /* 1 if a tensor-core wait of this surrogate ever timed out (results then invalid). */
 int rhd_surrogate_error(rhd_surrogate_t *s, int32_t *flag);
+/* Test support for the bounded waits (no counterpart in the paper): with on != 0
+ * the surrogate's tensor-core GEMMs (training and rhd_surrogate_predict) issue no
+ * MMA, so each one's first barrier wait gives up after a few polls with nothing
+ * asynchronous in flight; the kernel sets the error flag that rhd_surrogate_error
+ * reads, releases its tensor memory and returns, and the device stays usable.
+ * Outputs of calls made meanwhile are meaningless; on = 0 restores the normal
+ * path (the flag stays set for this surrogate). */
+int rhd_surrogate_test_wait_timeout(rhd_surrogate_t *s, int32_t on);
 /* Save the network (parameters and standardisation, not the Adam moments) to a
  * file: a 32-byte header -- the 8 bytes "RHDMLP1\0", int32 n_groups,
  * n_features, n_outputs, int32 0 (padding), int64 n_params -- then n_params FP32

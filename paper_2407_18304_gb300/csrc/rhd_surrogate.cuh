@@ -328,6 +328,7 @@ struct rhd_surrogate {
   __nv_bfloat16 *wt[4] = {nullptr, nullptr, nullptr, nullptr};
   float *norm = nullptr;  // x_mean [kin], x_sd [kin], y_mean [nout], y_sd [nout]
   unsigned *err = nullptr;
+  int wait_test = 0;  // rhd_surrogate_test_wait_timeout
   // training buffers (capacity cap_b rows)
   int64_t cap_b = 0;
   void *tbuf = nullptr;
@@ -413,7 +414,7 @@ int ensure_train(rhd_surrogate *s, int64_t B) {
 
 tc::GemmArgs gemm_args(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *Bm, int64_t ldb,
                        int64_t M, int64_t N, int64_t K, float *D, int64_t ldd, int epi,
-                       const float *bias, __nv_bfloat16 *H, int64_t ldh, unsigned *err) {
+                       const float *bias, __nv_bfloat16 *H, int64_t ldh, const rhd_surrogate *s) {
   tc::GemmArgs g{};
   g.A = A;
   g.lda = lda;
@@ -428,7 +429,8 @@ tc::GemmArgs gemm_args(const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 
   g.bias = bias;
   g.H = H;
   g.ldh = ldh;
-  g.err = err;
+  g.err = s->err;
+  g.wait_test = s->wait_test;
   return g;
 }
 
@@ -443,12 +445,12 @@ int forward_backward(rhd_surrogate *s, const TrainBufs &t, int64_t B, float *los
   };
   // forward
   run(gemm_args(t.xb, s->kpad, s->w[0], s->kpad, B, H, s->kin, t.z[0], H, tc::kEpiBiasGelu,
-                s->params + s->off_b[0], t.h[0], H, s->err));
+                s->params + s->off_b[0], t.h[0], H, s));
   for (int l = 1; l < 3; ++l)
     run(gemm_args(t.h[l - 1], H, s->w[l], H, B, H, H, t.z[l], H, tc::kEpiBiasGelu,
-                  s->params + s->off_b[l], t.h[l], H, s->err));
+                  s->params + s->off_b[l], t.h[l], H, s));
   run(gemm_args(t.h[2], H, s->w[3], H, B, s->nout, H, t.pred, s->nout, tc::kEpiBias,
-                s->params + s->off_b[3], nullptr, 0, s->err));
+                s->params + s->off_b[3], nullptr, 0, s));
   if (e != cudaSuccess) return RHD_ECUDA;
   mlp::loss_kernel<<<blocks_for(B, 256), 256, 0, st>>>(t.pred, t.yb, B, s->nout, t.dy, t.dyb,
                                                        s->npad, t.dyt, loss);
@@ -456,9 +458,9 @@ int forward_backward(rhd_surrogate *s, const TrainBufs &t, int64_t B, float *los
   // layer 4: dW4 = dY^T H3, dH3 = dY W4
   e = tc::transpose(t.h[2], B, H, H, t.ht, B, st);
   run(gemm_args(t.dyt, B, t.ht, B, s->nout, H, B, s->grads + s->off_w[3], H, tc::kEpiStore,
-                nullptr, nullptr, 0, s->err));
+                nullptr, nullptr, 0, s));
   run(gemm_args(t.dyb, s->npad, s->wt[3], s->npad, B, H, s->nout, t.dh, H, tc::kEpiStore,
-                nullptr, nullptr, 0, s->err));
+                nullptr, nullptr, 0, s));
   for (int l = 2; l >= 0; --l) {
     if (e != cudaSuccess) return RHD_ECUDA;
     mlp::gelu_back_kernel<<<blocks_for(B * H, 256), 256, 0, st>>>(t.z[l], t.dh, t.dzb, B * H);
@@ -468,13 +470,13 @@ int forward_backward(rhd_surrogate *s, const TrainBufs &t, int64_t B, float *los
       // dW_l = dZ^T H_{l-1}; dH_{l-1} = dZ W_l
       if (e == cudaSuccess) e = tc::transpose(t.h[l - 1], B, H, H, t.ht, B, st);
       run(gemm_args(t.dzt, B, t.ht, B, H, H, B, s->grads + s->off_w[l], H, tc::kEpiStore,
-                    nullptr, nullptr, 0, s->err));
+                    nullptr, nullptr, 0, s));
       run(gemm_args(t.dzb, H, s->wt[l], H, B, H, H, t.dh, H, tc::kEpiStore, nullptr, nullptr, 0,
-                    s->err));
+                    s));
     } else {
       // dW_1 = dZ^T X
       run(gemm_args(t.dzt, B, t.xbt, B, H, s->kin, B, s->grads + s->off_w[0], s->kin,
-                    tc::kEpiStore, nullptr, nullptr, 0, s->err));
+                    tc::kEpiStore, nullptr, nullptr, 0, s));
     }
   }
   return (e == cudaSuccess && cudaGetLastError() == cudaSuccess) ? RHD_OK : RHD_ECUDA;
@@ -522,19 +524,19 @@ InferBufs infer_views(rhd_surrogate *s) {
 int infer_rows(rhd_surrogate *s, const InferBufs &b, int64_t m, float *y, cudaStream_t st) {
   const int64_t H = mlp::kH;
   cudaError_t e = tc::gemm(gemm_args(b.xb, s->kpad, s->w[0], s->kpad, m, H, s->kin, nullptr, H,
-                                     tc::kEpiBiasGelu, s->params + s->off_b[0], b.h0, H, s->err),
+                                     tc::kEpiBiasGelu, s->params + s->off_b[0], b.h0, H, s),
                            st);
   if (e == cudaSuccess)
     e = tc::gemm(gemm_args(b.h0, H, s->w[1], H, m, H, H, nullptr, H, tc::kEpiBiasGelu,
-                           s->params + s->off_b[1], b.h1, H, s->err),
+                           s->params + s->off_b[1], b.h1, H, s),
                  st);
   if (e == cudaSuccess)
     e = tc::gemm(gemm_args(b.h1, H, s->w[2], H, m, H, H, nullptr, H, tc::kEpiBiasGelu,
-                           s->params + s->off_b[2], b.h0, H, s->err),
+                           s->params + s->off_b[2], b.h0, H, s),
                  st);
   if (e == cudaSuccess)
     e = tc::gemm(gemm_args(b.h0, H, s->w[3], H, m, s->nout, H, y, s->nout, tc::kEpiBias,
-                           s->params + s->off_b[3], nullptr, 0, s->err),
+                           s->params + s->off_b[3], nullptr, 0, s),
                  st);
   return e == cudaSuccess ? RHD_OK : RHD_ECUDA;
 }
@@ -832,6 +834,13 @@ extern "C" int rhd_surrogate_predict(rhd_surrogate_t *s, const float *x, int64_t
   }
   if (rc == RHD_OK && cudaGetLastError() != cudaSuccess) rc = RHD_ECUDA;
   return rc;
+}
+
+extern "C" int rhd_surrogate_test_wait_timeout(rhd_surrogate_t *s, int32_t on) {
+  int rc = rhd::check_surrogate(s);
+  if (rc != RHD_OK) return rc;
+  s->wait_test = on ? 1 : 0;
+  return RHD_OK;
 }
 
 extern "C" int rhd_surrogate_error(rhd_surrogate_t *s, int32_t *flag) {

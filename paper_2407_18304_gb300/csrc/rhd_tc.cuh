@@ -56,10 +56,12 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
 }
 
-// Poll the barrier's phase `parity` until it completes; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity) {
+// Poll the barrier's phase `parity` until it completes, at most `limit`
+// times; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity,
+                                          long long limit = kWaitLimit) {
   const uint32_t a = smem_addr(bar);
-  for (long long k = 0; k < kWaitLimit; ++k) {
+  for (long long k = 0; k < limit; ++k) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -178,7 +180,10 @@ struct GemmArgs {
   int epi;
   int accumulate;          // D += result (kEpiStore only; split-K partial sums)
   unsigned *err;           // set to 1 on a wait timeout
+  int wait_test;           // test only (0 otherwise): issue no MMA, so the first barrier
+                           // wait runs out (after kTestWaitLimit polls) with nothing in flight
 };
+constexpr long long kTestWaitLimit = 64;
 
 // tanh form of GELU, 0.5 z (1 + tanh(u)) with u = k0 (z + k1 z^3), written as
 // z / (1 + e^-2u) (0.5 (1 + tanh u) is the logistic function of 2u): one fast
@@ -224,7 +229,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
     stage<NT>(sB, g.B, g.ldb, 0, g.N, k0, g.K);
     fence_async_smem();
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && !g.wait_test) {
       tc_fence_after();
 #pragma unroll
       for (int ks = 0; ks < kChunkK / 16; ++ks) {
@@ -235,7 +240,7 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
       }
       mma_commit(&bar);
     }
-    const bool ok = mbar_wait(&bar, phase);
+    const bool ok = mbar_wait(&bar, phase, g.wait_test ? kTestWaitLimit : kWaitLimit);
     phase ^= 1u;
     if (!ok) failed = 1;
     tc_fence_after();
@@ -263,8 +268,9 @@ __global__ void __launch_bounds__(128) gemm_bf16_kernel(const GemmArgs g) {
     }
   } else {
     // the MMAs of the abandoned chunk may still be in flight: give them one
-    // more bounded wait before the accumulator is released
-    mbar_wait(&bar, phase ^ 1u);
+    // more bounded wait before the accumulator is released (none were issued
+    // in the wait test)
+    mbar_wait(&bar, phase ^ 1u, g.wait_test ? kTestWaitLimit : kWaitLimit);
     if (threadIdx.x == 0 && g.err) atomicExch(g.err, 1u);
   }
   tc_fence_before();

@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
                                          ctypes.c_float, _F, _P],
             "rhd_surrogate_predict": [_P, _F, ctypes.c_int64, _F, _P],
             "rhd_surrogate_error": [_P, ctypes.POINTER(ctypes.c_int32)],
+            "rhd_surrogate_test_wait_timeout": [_P, ctypes.c_int32],
             "rhd_source_update_warm": [_P, ctypes.POINTER(State), ctypes.POINTER(Groups),
                                        ctypes.POINTER(OpacityLaw), _D, ctypes.c_int64, _P],
             "rhd_surrogate_save": [_P, ctypes.c_char_p],
@@ -605,6 +606,10 @@ class Surrogate:
         f = ctypes.c_int32()
         _raise(lib().rhd_surrogate_error(self._h, ctypes.byref(f)))
         return f.value
+
+    def test_wait_timeout(self, on: bool) -> None:
+        """Test support: make the tensor-core waits give up (see include/rhd.h)."""
+        _raise(lib().rhd_surrogate_test_wait_timeout(self._h, 1 if on else 0))
 
     def source_update(self, state: dict, edges, law, *, dt: float, c_v: float, consts: dict,
                       theta: float = 1.0, precision: int = MIXED, closure: int = M1,

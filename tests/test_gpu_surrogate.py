@@ -218,3 +218,33 @@ def test_a_useless_surrogate_falls_back_to_the_cold_start():
     for k, v in e.items():
         if not k.endswith("_plain"):
             assert v < FP64_TOL, (k, v)
+
+
+def test_a_tensor_core_wait_that_runs_out_is_reported_and_the_device_stays_usable():
+    """The bounded waits of the tensor-core GEMM: with the test switch on, no
+    MMA is issued, so the first barrier wait gives up after a few polls with
+    nothing in flight; the kernel sets the surrogate's error flag, frees its
+    tensor memory and returns.  Afterwards the same device trains and
+    predicts normally (a fresh surrogate: flag 0, forward as the reference)."""
+    G, n = 4, 257
+    sur, p, norm = _random_net(G, 5)
+    x = torch.tensor(np.random.default_rng(1).normal(0, 1, (n, sur.n_features)).astype(np.float32),
+                     device="cuda")
+    sur.test_wait_timeout(True)
+    sur.predict(x)
+    torch.cuda.synchronize()
+    assert sur.error_flag() == 1
+    sur.test_wait_timeout(False)
+    fresh, p2, norm2 = _random_net(G, 6)
+    y = fresh.predict(x).cpu().numpy().astype(np.float64)
+    ref = M.predict(p2, norm2, x.cpu().numpy().astype(np.float64), fresh.n_features,
+                    fresh.n_outputs, bf=True)
+    assert _rel(y, ref) < 1e-2
+    assert fresh.error_flag() == 0
+    # and a training step on the fresh network runs its backward GEMMs cleanly
+    yt = torch.tensor(np.random.default_rng(2).normal(0, 1, (n, fresh.n_outputs)).astype(np.float32),
+                      device="cuda")
+    fresh.fit_normalization(x, yt)
+    fresh.train_step(x, yt, 0, 256, 1, 0, 1e-3)  # a batch of 256 rows (a multiple of 8)
+    torch.cuda.synchronize()
+    assert fresh.error_flag() == 0
