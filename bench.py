@@ -456,6 +456,10 @@ def run_batched(args, ws, rank):
 
     restore()
     shape = ctx.autotune(specs, stream=stream)  # untimed; leaves the state unchanged
+    buckets = sorted({0 if g.n_groups <= 16 else 1 if g.n_groups <= 32 else 2 for g in grids})
+    # per step: the table kernel, then per bucket its FP32 passes, correction
+    # and FP64 passes (mixed form) or its FP64 passes
+    launches = 1 + len(buckets) * (3 if prec == rhd.MIXED else 1)
     ms, clk = timed(batched, args.steps, args.warmup, True)
     t_max = allmax(sum(ms) / 1e3, ws)
     total = allsum(units1 * args.steps, ws)
@@ -469,9 +473,12 @@ def run_batched(args, ws, rank):
                       "cells": int(sum(g.n_cells for g in grids)), "cell_groups": int(units1),
                       "precision": args.precision, "tol": 1e-11, "tol_outer": 1e-13,
                       "shape": {"threads": shape[0], "cells_per_item": shape[1]},
+                      "mappings": {f"bucket{b}": {"passes": ctx.mapping(b)[0],
+                                                  "correction": ctx.mapping(b)[1]}
+                                   for b in buckets},
                       "l2": "state restored from a pristine copy before each step (2x state > L2)",
                       "parallelism": f"weak x{ws}, no collective"},
-           "gpu_launches": args.steps * 2, "clocks": clk}
+           "gpu_launches": args.steps * launches, "clocks": clk}
     pg, _ = timed(per_grid, max(1, args.fp64_steps), 1)
     t_pg = allmax(sum(pg) / 1e3, ws)
     res["per_grid_form"] = {"value": allsum(units1 * len(pg), ws) / t_pg,

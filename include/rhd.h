@@ -180,25 +180,41 @@ int rhd_imex_step(rhd_state_t *state, const rhd_groups_t *groups,
 
 /* ---- Batched uneven grids --------------------------------------------------
  * Many independent grids (own cell count, N_g <= RHD_MAX_GROUPS_BATCHED, own
- * opacity law, dt and parameters) in one persistent launch: a device work queue
- * hands (grid, cell-tile) items to the CTAs, each CTA keeps the group table of
- * its current grid in shared memory, and every cell is solved by the same
- * per-cell algorithm as rhd_source_update (the mixed form runs its FP32 and
- * FP64 phases in the same thread).  The call is recorded once as a CUDA graph
- * (descriptor upload, queue reset, table setup, solve) and replayed while the
- * number of grids and work items is unchanged.  A context owns the workspace
- * (descriptors, tables, queue head), the graph and the tuned launch shape; it
- * is not thread-safe, and a call waits (host side) for the previous call of
- * the same context to finish reading its host staging buffer.  The operation
- * on each cell is the implicit source update of Sec. 3 (the same as
+ * opacity law, dt and parameters) in a few persistent launches: a device work
+ * queue hands (grid, cell-tile) items to the CTAs, each CTA keeps the group
+ * table of its current grid in shared memory, and every cell is solved by the
+ * same per-cell algorithm as rhd_source_update -- the FP64 form's passes, or
+ * the mixed form's three phases (FP32 passes, correction step, FP64 passes for
+ * the cells the correction leaves), each grid's phases handing over through
+ * its own part of the context's workspace.  The grids fall into
+ * RHD_BATCH_BUCKETS buckets by group count (bucket 0: 1..16, 1: 17..32, 2:
+ * 33..64 groups); the grids of a bucket share a mapping of cells to lanes and
+ * their own queues, and the buckets run side by side on separate streams.  A
+ * mapping is a number of lanes per cell: 1 (one cell per thread) or a segment
+ * of 8, 16 or 32 lanes of a warp, each lane holding (the bucket's largest
+ * group count / lanes) groups in registers; the passes and the correction step
+ * have a mapping each (rhd_context_set_mapping lists the choices).  The
+ * defaults are the one-grid call's mappings, so that a batched call gives
+ * every cell exactly as rhd_source_update gives it; rhd_context_autotune
+ * picks them by timing.  RHD_CELL_PER_THREAD has no effect here.  The call is
+ * recorded once as a CUDA graph (descriptor upload, queue reset, table setup,
+ * the phases) and replayed while the number of grids, the work items and the
+ * mappings are unchanged.  A context owns the workspace (descriptors, tables,
+ * queue heads; mixed form 32 bytes per cell-group + 34 per cell of every
+ * grid, grown on demand), the graph and the tuned mappings; it is not
+ * thread-safe, and a call waits (host side) for the previous call of the same
+ * context to finish reading its host staging buffers.  The operation on each
+ * cell is the implicit source update of Sec. 3 (the same as
  * rhd_source_update); batching several grids into one launch has no
  * counterpart in the paper, which updates one patch at a time.
  * Errors: RHD_EINVAL (null context or grids, n_grids < 1, grids of mixed
- * precision, or a per-grid check of rhd_source_update failing), RHD_ESIZE
- * (n_grids > RHD_MAX_GRIDS or a grid with more than RHD_MAX_GROUPS_BATCHED
- * groups), RHD_ENOMEM, RHD_ECUDA; on any error nothing was launched. */
+ * precision, or a per-grid check of rhd_source_update failing), RHD_ELAW (free
+ * slopes), RHD_ESIZE (n_grids > RHD_MAX_GRIDS or a grid with more than
+ * RHD_MAX_GROUPS_BATCHED groups), RHD_ENOMEM, RHD_ECUDA; on any error nothing
+ * was launched. */
 #define RHD_MAX_GROUPS_BATCHED 64
 #define RHD_MAX_GRIDS 4096
+#define RHD_BATCH_BUCKETS 3
 
 typedef struct rhd_context rhd_context_t;
 
@@ -219,15 +235,32 @@ int rhd_context_destroy(rhd_context_t *ctx);
 int rhd_source_update_batched(rhd_context_t *ctx, const rhd_grid_t *grids, int32_t n_grids,
                               void *stream);
 
-/* Time every candidate launch shape (CTA size x cells per work item) on these
- * grids and keep the fastest in the context.  The grids' state is saved to a
- * temporary device copy first and restored after each candidate, so it is
- * unchanged on return; the call synchronizes the stream. */
+/* Pick each bucket's mappings and the CTA shape by timing them on these
+ * grids: per bucket (on its own grids) every mapping of the passes, then
+ * (mixed form) every mapping of the correction step; then the CTA size x cells
+ * per work item of the one-cell-per-thread mapping (threads 64, 128, 256;
+ * items of 1, 4 or 16 CTAs' worth of cells).  Each candidate is timed as the
+ * best of two uncaptured calls.  The grids' state is saved to a temporary
+ * device copy first and restored after each candidate, so it is unchanged on
+ * return; the call synchronizes the stream.  On an error the mappings are
+ * left as they were. */
 int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids, int32_t n_grids,
                          void *stream);
 
-/* The launch shape the context uses (threads per CTA, cells per work item). */
+/* The CTA shape of the one-cell-per-thread mapping (threads per CTA, cells
+ * per work item). */
 int rhd_context_shape(const rhd_context_t *ctx, int32_t *threads, int32_t *cells_per_item);
+
+/* Read or set bucket `bucket`'s mappings, as lanes per cell: `passes` for the
+ * FP32 and FP64 passes (bucket 0: 1 or 8; bucket 1: 1, 8, 16 or 32; bucket
+ * 2: 1, 16 or 32), `correction` for the mixed form's correction step (bucket
+ * 0: 8; bucket 1: 8 or 16; bucket 2: 16 or 32).  Defaults: passes 1, 1, 32;
+ * correction 8, 16, 32.  RHD_EINVAL for another bucket or mapping (nothing
+ * changed). */
+int rhd_context_mapping(const rhd_context_t *ctx, int32_t bucket, int32_t *passes,
+                        int32_t *correction);
+int rhd_context_set_mapping(rhd_context_t *ctx, int32_t bucket, int32_t passes,
+                            int32_t correction);
 
 /* ---- Learned warm start ----------------------------------------------------
  * A small MLP (features 2 N_g + 4 -> 128 -> 128 -> 128 -> N_g + 1, GELU, BF16

@@ -600,26 +600,62 @@ extern "C" int rhd_imex_step(rhd_state_t *state, const rhd_groups_t *groups,
 // ---------------------------------------------------------------------------
 // Batched uneven grids
 // ---------------------------------------------------------------------------
-// Grids are split in two classes, each with its own work queue: one cell per
-// thread (up to 32 groups, or RHD_CELL_PER_THREAD) and one cell per warp
-// (33..64 groups).  Staging layout: offsets [2][cap + 1], selections [2][cap].
+// The grids fall into RHD_BATCH_BUCKETS buckets by group count, each with its
+// own mapping of cells to lanes and its own queues (rhd_batched.cuh).
+// Staging layout: offsets [2 * buckets][cap + 1] (bucket b's pass items at
+// 2b, its correction items at 2b + 1), selections [buckets][cap], queue heads
+// [3 * buckets] (FP32 passes, correction, FP64 passes of each bucket).
+namespace rhd {
+namespace {
+constexpr int kBuckets = RHD_BATCH_BUCKETS;
+constexpr int kCpiWarp = 64;  // cells per work item of a lane-segment mapping
+constexpr int kCpiCorr = 64;  // cells per work item of the correction step
+constexpr int kSigWords = 5 + 2 * kBuckets + 3 * kBuckets;
+
+int bucket_of(int G) { return G <= 16 ? 0 : G <= 32 ? 1 : 2; }
+
+// The mappings each bucket offers (lanes per cell; 1 = one cell per thread).
+// The groups per lane follow: the bucket's largest group count / lanes.
+bool pass_mapping_ok(int b, int m) {
+  switch (b) {
+    case 0: return m == 1 || m == 8;
+    case 1: return m == 1 || m == 8 || m == 16 || m == 32;
+    case 2: return m == 1 || m == 16 || m == 32;
+  }
+  return false;
+}
+bool corr_mapping_ok(int b, int m) {
+  switch (b) {
+    case 0: return m == 8;
+    case 1: return m == 8 || m == 16;
+    case 2: return m == 16 || m == 32;
+  }
+  return false;
+}
+}  // namespace
+}  // namespace rhd
+
 struct rhd_context {
   int device = -1;
-  int threads = 128, cpi = 512;  // thread-class launch shape (autotuned)
+  int threads = 128, cpi = 512;                // shape of the cell-per-thread mapping (autotuned)
+  int pass_map[RHD_BATCH_BUCKETS] = {1, 1, 32};  // lanes per cell of each bucket's passes
+  int corr_map[RHD_BATCH_BUCKETS] = {8, 16, 32}; // lanes per cell of its correction step
   int cap_grids = 0;
   rhd::KParams *h_grids = nullptr, *d_grids = nullptr;
+  rhd::WarmOut *h_warm = nullptr, *d_warm = nullptr;
   int64_t *h_off = nullptr, *d_off = nullptr;
   int *h_sel = nullptr, *d_sel = nullptr;
-  int n_sel[2] = {0, 0};
+  int n_sel[RHD_BATCH_BUCKETS] = {0, 0, 0};
   double *d_tables = nullptr;
-  unsigned long long *d_head = nullptr;  // one counter per class
+  unsigned long long *d_head = nullptr;
+  char *d_ws = nullptr;  // the mixed form's per-grid workspaces
+  size_t ws_bytes = 0;
   cudaStream_t cap = nullptr;
-  cudaStream_t side = nullptr;       // the warp class runs here, forked from the main stream
-  cudaEvent_t fork = nullptr, join = nullptr;
+  cudaStream_t side[RHD_BATCH_BUCKETS - 1] = {};  // buckets 1.. run here, forked from the main stream
+  cudaEvent_t fork = nullptr, join[RHD_BATCH_BUCKETS - 1] = {};
   cudaGraphExec_t exec = nullptr;
-  int sig_grids = -1, sig_threads = 0, sig_cpi = 0, sig_prec = -1;
-  int64_t sig_items[2] = {-1, -1};
-  int sig_sel[2] = {-1, -1};
+  int64_t sig[rhd::kSigWords] = {};
+  bool has_sig = false;
   cudaEvent_t done = nullptr;
   bool pending = false;
 };
@@ -627,22 +663,24 @@ struct rhd_context {
 namespace rhd {
 namespace {
 
-constexpr int kMaxGB = RHD_MAX_GROUPS_BATCHED;
 const int64_t kTableWords = group_table_words(kMaxGB) + 1;
-constexpr int kCpiWarp = 64;  // cells per work item of the warp class
 
 void ctx_free(rhd_context *c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
   if (c->h_grids) cudaFreeHost(c->h_grids);
+  if (c->h_warm) cudaFreeHost(c->h_warm);
   if (c->h_off) cudaFreeHost(c->h_off);
   if (c->h_sel) cudaFreeHost(c->h_sel);
   if (c->d_grids) cudaFree(c->d_grids);
+  if (c->d_warm) cudaFree(c->d_warm);
   if (c->d_off) cudaFree(c->d_off);
   if (c->d_sel) cudaFree(c->d_sel);
   if (c->d_tables) cudaFree(c->d_tables);
   if (c->d_head) cudaFree(c->d_head);
   c->exec = nullptr;
+  c->has_sig = false;
   c->h_grids = c->d_grids = nullptr;
+  c->h_warm = c->d_warm = nullptr;
   c->h_off = c->d_off = nullptr;
   c->h_sel = c->d_sel = nullptr;
   c->d_tables = nullptr;
@@ -653,17 +691,20 @@ void ctx_free(rhd_context *c) {
 int ctx_reserve(rhd_context *c, int n_grids) {
   if (n_grids <= c->cap_grids) return RHD_OK;
   if (c->pending) cudaEventSynchronize(c->done);
+  c->pending = false;
   ctx_free(c);
   int cap = 64;
   while (cap < n_grids) cap *= 2;
+  const size_t noff = sizeof(int64_t) * 2 * kBuckets * (cap + 1), nsel = sizeof(int) * kBuckets * cap;
   if (cudaHostAlloc(&c->h_grids, sizeof(KParams) * cap, cudaHostAllocDefault) != cudaSuccess ||
-      cudaHostAlloc(&c->h_off, sizeof(int64_t) * 2 * (cap + 1), cudaHostAllocDefault) != cudaSuccess ||
-      cudaHostAlloc(&c->h_sel, sizeof(int) * 2 * cap, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&c->h_warm, sizeof(WarmOut) * cap, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&c->h_off, noff, cudaHostAllocDefault) != cudaSuccess ||
+      cudaHostAlloc(&c->h_sel, nsel, cudaHostAllocDefault) != cudaSuccess ||
       cudaMalloc(&c->d_grids, sizeof(KParams) * cap) != cudaSuccess ||
-      cudaMalloc(&c->d_off, sizeof(int64_t) * 2 * (cap + 1)) != cudaSuccess ||
-      cudaMalloc(&c->d_sel, sizeof(int) * 2 * cap) != cudaSuccess ||
+      cudaMalloc(&c->d_warm, sizeof(WarmOut) * cap) != cudaSuccess ||
+      cudaMalloc(&c->d_off, noff) != cudaSuccess || cudaMalloc(&c->d_sel, nsel) != cudaSuccess ||
       cudaMalloc(&c->d_tables, sizeof(double) * kTableWords * cap) != cudaSuccess ||
-      cudaMalloc(&c->d_head, 2 * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&c->d_head, 3 * kBuckets * sizeof(unsigned long long)) != cudaSuccess) {
     ctx_free(c);
     return RHD_ENOMEM;
   }
@@ -671,15 +712,20 @@ int ctx_reserve(rhd_context *c, int n_grids) {
   return RHD_OK;
 }
 
-// Pack the grids into the pinned staging buffers and split them into the two
-// classes; work items per class out (items[0] thread class, items[1] warp class).
+int64_t *off_of(int64_t *base, const rhd_context *c, int set) {
+  return base + (int64_t)set * (c->cap_grids + 1);
+}
+
+// Pack the grids into the pinned staging buffers and split them into the
+// buckets; work items per set out (items[2b] bucket b's passes, items[2b+1]
+// its correction step).  Mixed form: each grid's workspace is carved out of
+// the context's (grown here, before anything is enqueued).
 int pack_batch(rhd_context *c, const rhd_grid_t *grids, int n_grids, int cpi, int *prec,
-               int64_t items[2]) {
-  int64_t acc[2] = {0, 0};
-  int ns[2] = {0, 0};
-  int64_t *off[2] = {c->h_off, c->h_off + c->cap_grids + 1};
-  int *sel[2] = {c->h_sel, c->h_sel + c->cap_grids};
+               int64_t items[2 * kBuckets]) {
+  int64_t acc[2 * kBuckets] = {};
+  int ns[kBuckets] = {};
   *prec = -1;
+  size_t ws = 0;
   for (int j = 0; j < n_grids; ++j) {
     const rhd_grid_t &g = grids[j];
     const int rc = pack(&g.state, &g.groups, &g.opacity_law, g.dt, g.n_cells, &c->h_grids[j]);
@@ -688,69 +734,174 @@ int pack_batch(rhd_context *c, const rhd_grid_t *grids, int n_grids, int cpi, in
     if (g.groups.n_groups > kMaxGB) return RHD_ESIZE;
     if (*prec < 0) *prec = g.state.precision;
     if (g.state.precision != *prec) return RHD_EINVAL;
-    const int cls = (g.groups.n_groups > 32 && !(g.state.flags & RHD_CELL_PER_THREAD)) ? 1 : 0;
-    const int per = cls ? kCpiWarp : cpi;
-    off[cls][ns[cls]] = acc[cls];
-    sel[cls][ns[cls]] = j;
-    ++ns[cls];
-    acc[cls] += (g.n_cells + per - 1) / per;
+    ws += (warm_bytes(g.n_cells, g.groups.n_groups) + 255) & ~(size_t)255;
   }
-  for (int k = 0; k < 2; ++k) {
-    off[k][ns[k]] = acc[k];
-    items[k] = acc[k];
-    c->n_sel[k] = ns[k];
+  if (*prec == RHD_MIXED && ws > c->ws_bytes) {
+    if (c->pending) cudaEventSynchronize(c->done);
+    c->pending = false;
+    if (c->d_ws) cudaFree(c->d_ws);
+    c->d_ws = nullptr;
+    c->ws_bytes = 0;
+    if (cudaMalloc(&c->d_ws, ws) != cudaSuccess) return RHD_ENOMEM;
+    c->ws_bytes = ws;
+  }
+  size_t at = 0;
+  for (int j = 0; j < n_grids; ++j) {
+    const rhd_grid_t &g = grids[j];
+    const int G = g.groups.n_groups, b = bucket_of(G);
+    if (*prec == RHD_MIXED) {
+      WarmStart unused;
+      carve(c->d_ws + at, g.n_cells, G, &c->h_warm[j], &unused);
+      at += (warm_bytes(g.n_cells, G) + 255) & ~(size_t)255;
+    }
+    const int per = c->pass_map[b] == 1 ? cpi : kCpiWarp;
+    off_of(c->h_off, c, 2 * b)[ns[b]] = acc[2 * b];
+    off_of(c->h_off, c, 2 * b + 1)[ns[b]] = acc[2 * b + 1];
+    c->h_sel[(int64_t)b * c->cap_grids + ns[b]] = j;
+    ++ns[b];
+    acc[2 * b] += (g.n_cells + per - 1) / per;
+    acc[2 * b + 1] += (g.n_cells + kCpiCorr - 1) / kCpiCorr;
+  }
+  for (int b = 0; b < kBuckets; ++b) {
+    for (int s = 2 * b; s <= 2 * b + 1; ++s) {
+      off_of(c->h_off, c, s)[ns[b]] = acc[s];
+      items[s] = acc[s];
+    }
+    c->n_sel[b] = ns[b];
   }
   return RHD_OK;
 }
 
-template <bool MIXED>
-cudaError_t enqueue_batch(rhd_context *c, int n_grids, int threads, int cpi, int sms,
-                          const int64_t items[2], cudaStream_t st) {
+// A persistent launch over a queue of `items` work items: the CTAs resident
+// at once, fewer when there are fewer items.
+template <typename K>
+void launch_queue(K kernel, int threads, size_t smem, int sms, int64_t items, const BatchArgs &A,
+                  cudaStream_t s) {
+  if (items <= 0) return;
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess ||
+      per_sm < 1)
+    per_sm = 1;
+  const int64_t full = (int64_t)sms * per_sm;
+  kernel<<<(int)(items < full ? items : full), threads, smem, s>>>(A);
+}
+
+template <int L, int GPL>
+void launch_segments(int phase, int sms, int64_t items, const BatchArgs &A, cudaStream_t s) {
+  if (phase == 0) launch_queue(batched_w32_kernel<L, GPL>, 128, kBatchTableBytes, sms, items, A, s);
+  else launch_queue(batched_w64_kernel<L, GPL>, 128, kBatchTableBytes, sms, items, A, s);
+}
+
+// Bucket b's FP32 (phase 0) or FP64 (phase 2) passes with mapping m.
+void launch_passes(int phase, int b, int m, int threads, int sms, int64_t items,
+                   const BatchArgs &A, cudaStream_t s) {
+  if (m == 1) {
+    if (phase == 0) launch_queue(batched_fp32_kernel<kMaxGB>, threads, kBatchTableBytes, sms, items, A, s);
+    else launch_queue(batched_fp64_kernel<kMaxGB>, threads, kBatchTableBytes, sms, items, A, s);
+    return;
+  }
+  switch (100 * b + m) {  // groups per lane = the bucket's largest group count / lanes
+    case 8: launch_segments<8, 2>(phase, sms, items, A, s); break;
+    case 108: launch_segments<8, 4>(phase, sms, items, A, s); break;
+    case 116: launch_segments<16, 2>(phase, sms, items, A, s); break;
+    case 132: launch_segments<32, 1>(phase, sms, items, A, s); break;
+    case 216: launch_segments<16, 4>(phase, sms, items, A, s); break;
+    case 232: launch_segments<32, 2>(phase, sms, items, A, s); break;
+  }
+}
+
+template <int L, int GPL>
+void launch_corr(int sms, int64_t items, const BatchArgs &A, cudaStream_t s) {
+  launch_queue(batched_correct_kernel<L, GPL>, 128, batch_correct_smem(GPL), sms, items, A, s);
+}
+
+void launch_correction(int b, int m, int sms, int64_t items, const BatchArgs &A, cudaStream_t s) {
+  switch (100 * b + m) {
+    case 8: launch_corr<8, 2>(sms, items, A, s); break;
+    case 108: launch_corr<8, 4>(sms, items, A, s); break;
+    case 116: launch_corr<16, 2>(sms, items, A, s); break;
+    case 216: launch_corr<16, 4>(sms, items, A, s); break;
+    case 232: launch_corr<32, 2>(sms, items, A, s); break;
+  }
+}
+
+// The shared-memory opt-in of the correction kernels above 48 KB; made once
+// per device, before any capture.
+cudaError_t batch_prepare() {
+  cudaError_t e = cudaSuccess;
+  if (batch_correct_smem(4) > 48 * 1024) {
+    if ((e = allow_smem<batched_correct_kernel<8, 4>>(batch_correct_smem(4))) != cudaSuccess) return e;
+    if ((e = allow_smem<batched_correct_kernel<16, 4>>(batch_correct_smem(4))) != cudaSuccess) return e;
+  }
+  if (batch_correct_smem(2) > 48 * 1024) {
+    if ((e = allow_smem<batched_correct_kernel<8, 2>>(batch_correct_smem(2))) != cudaSuccess) return e;
+    if ((e = allow_smem<batched_correct_kernel<16, 2>>(batch_correct_smem(2))) != cudaSuccess) return e;
+    if ((e = allow_smem<batched_correct_kernel<32, 2>>(batch_correct_smem(2))) != cudaSuccess) return e;
+  }
+  return e;
+}
+
+// Everything one batched call enqueues: descriptors, queue reset, tables,
+// then each bucket's phases on its own stream (bucket 0 on st).
+cudaError_t enqueue_batch(rhd_context *c, int prec, int n_grids, int threads, int cpi, int sms,
+                          const int64_t items[2 * kBuckets], cudaStream_t st) {
   const int cap = c->cap_grids;
+  const bool mixed = prec == RHD_MIXED;
   cudaMemcpyAsync(c->d_grids, c->h_grids, sizeof(KParams) * n_grids, cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(c->d_off, c->h_off, sizeof(int64_t) * 2 * (cap + 1), cudaMemcpyHostToDevice, st);
-  cudaMemcpyAsync(c->d_sel, c->h_sel, sizeof(int) * 2 * cap, cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(c->d_head, 0, 2 * sizeof(unsigned long long), st);
+  if (mixed)
+    cudaMemcpyAsync(c->d_warm, c->h_warm, sizeof(WarmOut) * n_grids, cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(c->d_off, c->h_off, sizeof(int64_t) * 2 * kBuckets * (cap + 1),
+                  cudaMemcpyHostToDevice, st);
+  cudaMemcpyAsync(c->d_sel, c->h_sel, sizeof(int) * kBuckets * cap, cudaMemcpyHostToDevice, st);
+  cudaMemsetAsync(c->d_head, 0, 3 * kBuckets * sizeof(unsigned long long), st);
   tables_kernel<<<n_grids, 128, table_bytes(kMaxGB) + 64, st>>>(c->d_grids, c->d_tables,
                                                                    kTableWords);
-  const size_t smem = table_bytes(kMaxGB) + 64;
-  const bool both = items[0] > 0 && items[1] > 0;
-  if (both) {
-    cudaEventRecord(c->fork, st);
-    cudaStreamWaitEvent(c->side, c->fork, 0);
-  }
-  if (items[0] > 0) {
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_kernel<kMaxGB, MIXED>,
-                                                      threads, smem) != cudaSuccess ||
-        per_sm < 1)
-      per_sm = 1;
-    batched_kernel<kMaxGB, MIXED><<<sms * per_sm, threads, smem, st>>>(
-        c->d_grids, c->d_tables, kTableWords, c->d_sel, c->d_off, c->n_sel[0], cpi, c->d_head);
-  }
-  if (items[1] > 0) {
-    // the two classes run side by side (each one's tail overlaps the other's work)
-    cudaStream_t ws = both ? c->side : st;
-    int per_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batched_warp_kernel<MIXED>, 128,
-                                                      smem) != cudaSuccess ||
-        per_sm < 1)
-      per_sm = 1;
-    batched_warp_kernel<MIXED><<<sms * per_sm, 128, smem, ws>>>(
-        c->d_grids, c->d_tables, kTableWords, c->d_sel + cap, c->d_off + cap + 1, c->n_sel[1],
-        kCpiWarp, c->d_head + 1);
-    if (ws != st) {
-      cudaEventRecord(c->join, ws);
-      cudaStreamWaitEvent(st, c->join, 0);
+  bool forked = false;
+  for (int b = 0; b < kBuckets; ++b) {
+    if (c->n_sel[b] == 0 || items[2 * b] == 0) continue;
+    cudaStream_t s = st;
+    if (b > 0) {
+      if (!forked) cudaEventRecord(c->fork, st);
+      forked = true;
+      s = c->side[b - 1];
+      cudaStreamWaitEvent(s, c->fork, 0);
+    }
+    const int pm = c->pass_map[b];
+    BatchArgs A{c->d_grids, c->d_tables, kTableWords, mixed ? c->d_warm : nullptr,
+                c->d_sel + (int64_t)b * cap, off_of(c->d_off, c, 2 * b), c->n_sel[b],
+                pm == 1 ? cpi : kCpiWarp, nullptr};
+    const int th = pm == 1 ? threads : 128;
+    if (mixed) {
+      A.head = c->d_head + 3 * b;
+      launch_passes(0, b, pm, th, sms, items[2 * b], A, s);
+      BatchArgs Ac = A;
+      Ac.item_off = off_of(c->d_off, c, 2 * b + 1);
+      Ac.cpi = kCpiCorr;
+      Ac.head = c->d_head + 3 * b + 1;
+      launch_correction(b, c->corr_map[b], sms, items[2 * b + 1], Ac, s);
+    }
+    A.head = c->d_head + 3 * b + 2;
+    launch_passes(2, b, pm, th, sms, items[2 * b], A, s);
+    if (s != st) {
+      cudaEventRecord(c->join[b - 1], s);
+      cudaStreamWaitEvent(st, c->join[b - 1], 0);
     }
   }
   return cudaGetLastError();
 }
 
-cudaError_t enqueue_any(rhd_context *c, int prec, int n_grids, int threads, int cpi, int sms,
-                        const int64_t items[2], cudaStream_t st) {
-  return prec == RHD_MIXED ? enqueue_batch<true>(c, n_grids, threads, cpi, sms, items, st)
-                           : enqueue_batch<false>(c, n_grids, threads, cpi, sms, items, st);
+void signature(const rhd_context *c, int prec, int n_grids, const int64_t items[2 * kBuckets],
+               int64_t out[kSigWords]) {
+  int k = 0;
+  out[k++] = n_grids;
+  out[k++] = prec;
+  out[k++] = c->threads;
+  out[k++] = c->cpi;
+  out[k++] = c->cap_grids;
+  for (int s = 0; s < 2 * kBuckets; ++s) out[k++] = items[s];
+  for (int b = 0; b < kBuckets; ++b) out[k++] = c->n_sel[b];
+  for (int b = 0; b < kBuckets; ++b) out[k++] = c->pass_map[b];
+  for (int b = 0; b < kBuckets; ++b) out[k++] = c->corr_map[b];
 }
 
 }  // namespace
@@ -760,17 +911,21 @@ extern "C" int rhd_context_create(rhd_context_t **ctx) {
   if (!ctx) return RHD_EINVAL;
   rhd_context *c = new (std::nothrow) rhd_context();
   if (!c) return RHD_ENOMEM;
-  if (cudaGetDevice(&c->device) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess) {
+  bool ok = cudaGetDevice(&c->device) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) == cudaSuccess;
+  for (int k = 0; ok && k < rhd::kBuckets - 1; ++k)
+    ok = cudaStreamCreateWithFlags(&c->side[k], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->join[k], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     if (c->cap) cudaStreamDestroy(c->cap);
-    if (c->side) cudaStreamDestroy(c->side);
     if (c->fork) cudaEventDestroy(c->fork);
-    if (c->join) cudaEventDestroy(c->join);
     if (c->done) cudaEventDestroy(c->done);
+    for (int k = 0; k < rhd::kBuckets - 1; ++k) {
+      if (c->side[k]) cudaStreamDestroy(c->side[k]);
+      if (c->join[k]) cudaEventDestroy(c->join[k]);
+    }
     delete c;
     return RHD_ECUDA;
   }
@@ -782,11 +937,14 @@ extern "C" int rhd_context_destroy(rhd_context_t *ctx) {
   if (!ctx) return RHD_EINVAL;
   if (ctx->pending) cudaEventSynchronize(ctx->done);
   rhd::ctx_free(ctx);
+  if (ctx->d_ws) cudaFree(ctx->d_ws);
   if (ctx->cap) cudaStreamDestroy(ctx->cap);
-  if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->fork) cudaEventDestroy(ctx->fork);
-  if (ctx->join) cudaEventDestroy(ctx->join);
   if (ctx->done) cudaEventDestroy(ctx->done);
+  for (int k = 0; k < rhd::kBuckets - 1; ++k) {
+    if (ctx->side[k]) cudaStreamDestroy(ctx->side[k]);
+    if (ctx->join[k]) cudaEventDestroy(ctx->join[k]);
+  }
   delete ctx;
   return RHD_OK;
 }
@@ -799,6 +957,24 @@ extern "C" int rhd_context_shape(const rhd_context_t *ctx, int32_t *threads,
   return RHD_OK;
 }
 
+extern "C" int rhd_context_mapping(const rhd_context_t *ctx, int32_t bucket, int32_t *passes,
+                                   int32_t *correction) {
+  if (!ctx || !passes || !correction || bucket < 0 || bucket >= rhd::kBuckets) return RHD_EINVAL;
+  *passes = ctx->pass_map[bucket];
+  *correction = ctx->corr_map[bucket];
+  return RHD_OK;
+}
+
+extern "C" int rhd_context_set_mapping(rhd_context_t *ctx, int32_t bucket, int32_t passes,
+                                       int32_t correction) {
+  if (!ctx || bucket < 0 || bucket >= rhd::kBuckets) return RHD_EINVAL;
+  if (!rhd::pass_mapping_ok(bucket, passes) || !rhd::corr_mapping_ok(bucket, correction))
+    return RHD_EINVAL;
+  ctx->pass_map[bucket] = passes;
+  ctx->corr_map[bucket] = correction;
+  return RHD_OK;
+}
+
 extern "C" int rhd_source_update_batched(rhd_context_t *ctx, const rhd_grid_t *grids,
                                          int32_t n_grids, void *stream) {
   if (!ctx || !grids || n_grids < 1) return RHD_EINVAL;
@@ -806,6 +982,7 @@ extern "C" int rhd_source_update_batched(rhd_context_t *ctx, const rhd_grid_t *g
   int sms = 0;
   int rc = rhd::ensure_device(&sms);
   if (rc != RHD_OK) return rc;
+  if (rhd::batch_prepare() != cudaSuccess) return RHD_ECUDA;
   // the previous call of this context may still read the staging buffers
   if (ctx->pending) {
     cudaEventSynchronize(ctx->done);
@@ -814,23 +991,25 @@ extern "C" int rhd_source_update_batched(rhd_context_t *ctx, const rhd_grid_t *g
   rc = rhd::ctx_reserve(ctx, n_grids);
   if (rc != RHD_OK) return rc;
   int prec = 0;
-  int64_t items[2] = {0, 0};
+  int64_t items[2 * rhd::kBuckets] = {};
   rc = rhd::pack_batch(ctx, grids, n_grids, ctx->cpi, &prec, items);
   if (rc != RHD_OK) return rc;
-  if (items[0] + items[1] == 0) return RHD_OK;
+  int64_t any = 0;
+  for (int b = 0; b < rhd::kBuckets; ++b) any += items[2 * b];
+  if (any == 0) return RHD_OK;
   cudaStream_t st = (cudaStream_t)stream;
-  const bool same = ctx->exec && ctx->sig_grids == n_grids && ctx->sig_items[0] == items[0] &&
-                    ctx->sig_items[1] == items[1] && ctx->sig_sel[0] == ctx->n_sel[0] &&
-                    ctx->sig_sel[1] == ctx->n_sel[1] && ctx->sig_threads == ctx->threads &&
-                    ctx->sig_cpi == ctx->cpi && ctx->sig_prec == prec;
+  int64_t sig[rhd::kSigWords];
+  rhd::signature(ctx, prec, n_grids, items, sig);
+  const bool same = ctx->exec && ctx->has_sig && std::memcmp(sig, ctx->sig, sizeof(sig)) == 0;
   if (!same) {
     if (ctx->exec) cudaGraphExecDestroy(ctx->exec);
     ctx->exec = nullptr;
+    ctx->has_sig = false;
     cudaGraph_t graph = nullptr;
     if (cudaStreamBeginCapture(ctx->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
       return RHD_ECUDA;
     const cudaError_t le =
-        rhd::enqueue_any(ctx, prec, n_grids, ctx->threads, ctx->cpi, sms, items, ctx->cap);
+        rhd::enqueue_batch(ctx, prec, n_grids, ctx->threads, ctx->cpi, sms, items, ctx->cap);
     const cudaError_t ce = cudaStreamEndCapture(ctx->cap, &graph);
     if (le != cudaSuccess || ce != cudaSuccess || !graph) {
       if (graph) cudaGraphDestroy(graph);
@@ -842,20 +1021,90 @@ extern "C" int rhd_source_update_batched(rhd_context_t *ctx, const rhd_grid_t *g
       ctx->exec = nullptr;
       return RHD_ECUDA;
     }
-    ctx->sig_grids = n_grids;
-    ctx->sig_items[0] = items[0];
-    ctx->sig_items[1] = items[1];
-    ctx->sig_sel[0] = ctx->n_sel[0];
-    ctx->sig_sel[1] = ctx->n_sel[1];
-    ctx->sig_threads = ctx->threads;
-    ctx->sig_cpi = ctx->cpi;
-    ctx->sig_prec = prec;
+    std::memcpy(ctx->sig, sig, sizeof(sig));
+    ctx->has_sig = true;
   }
   if (cudaGraphLaunch(ctx->exec, st) != cudaSuccess) return RHD_ECUDA;
   if (cudaEventRecord(ctx->done, st) != cudaSuccess) return RHD_ECUDA;
   ctx->pending = true;
   return RHD_OK;
 }
+
+namespace rhd {
+namespace {
+
+// The device copy of every grid's in/out arrays, restored after each
+// candidate the autotuner times.
+struct StateSave {
+  struct Buf {
+    void *dst;
+    const void *src;
+    size_t bytes;
+  };
+  std::vector<Buf> bufs;
+  char *save = nullptr;
+
+  int take(const rhd_grid_t *grids, int n_grids, cudaStream_t st) {
+    size_t total = 0;
+    for (int j = 0; j < n_grids; ++j) {
+      const rhd_grid_t &g = grids[j];
+      if (g.n_cells <= 0) continue;
+      const int64_t gs = g.state.group_stride ? g.state.group_stride : g.n_cells;
+      const size_t per = sizeof(double) * g.n_cells;
+      const size_t pg = sizeof(double) * ((int64_t)(g.groups.n_groups - 1) * gs + g.n_cells);
+      if (!g.state.egas || !g.state.erad) return RHD_EINVAL;
+      bufs.push_back({nullptr, g.state.egas, per});
+      for (int d = 0; d < 3; ++d) bufs.push_back({nullptr, g.state.mom[d], per});
+      bufs.push_back({nullptr, g.state.erad, pg});
+      for (int d = 0; d < 3; ++d) bufs.push_back({nullptr, g.state.frad[d], pg});
+    }
+    for (auto &b : bufs) total += (b.bytes + 255) & ~size_t(255);
+    if (total && cudaMalloc(&save, total) != cudaSuccess) return RHD_ENOMEM;
+    size_t off = 0;
+    for (auto &b : bufs) {
+      b.dst = save + off;
+      off += (b.bytes + 255) & ~size_t(255);
+      cudaMemcpyAsync(b.dst, b.src, b.bytes, cudaMemcpyDeviceToDevice, st);
+    }
+    return RHD_OK;
+  }
+  void restore(cudaStream_t st) const {
+    for (auto &b : bufs)
+      cudaMemcpyAsync(const_cast<void *>(b.src), b.dst, b.bytes, cudaMemcpyDeviceToDevice, st);
+  }
+  ~StateSave() {
+    if (save) cudaFree(save);
+  }
+};
+
+// Time one candidate: the batched call (not captured) on these grids with the
+// context's current mappings and the given shape, then the state restored.
+// The best of two runs (the first also loads the kernels).
+int time_candidate(rhd_context *c, const rhd_grid_t *grids, int n_grids, int threads, int cpi,
+                   int sms, const StateSave &sv, cudaEvent_t e0, cudaEvent_t e1, cudaStream_t st,
+                   float *ms_out) {
+  int prec = 0;
+  int64_t items[2 * kBuckets] = {};
+  int rc = pack_batch(c, grids, n_grids, cpi, &prec, items);
+  if (rc != RHD_OK) return rc;
+  float best = 1e30f;
+  for (int rep = 0; rep < 2; ++rep) {
+    cudaEventRecord(e0, st);
+    if (enqueue_batch(c, prec, n_grids, threads, cpi, sms, items, st) != cudaSuccess)
+      return RHD_ECUDA;
+    cudaEventRecord(e1, st);
+    sv.restore(st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return RHD_ECUDA;
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return RHD_ECUDA;
+    if (ms < best) best = ms;
+  }
+  *ms_out = best;
+  return RHD_OK;
+}
+
+}  // namespace
+}  // namespace rhd
 
 extern "C" int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids, int32_t n_grids,
                                     void *stream) {
@@ -865,80 +1114,90 @@ extern "C" int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids,
   int sms = 0;
   int rc = rhd::ensure_device(&sms);
   if (rc != RHD_OK) return rc;
+  if (rhd::batch_prepare() != cudaSuccess) return RHD_ECUDA;
   if (ctx->pending) {
     cudaEventSynchronize(ctx->done);
     ctx->pending = false;
   }
   rc = rhd::ctx_reserve(ctx, n_grids);
   if (rc != RHD_OK) return rc;
-  // save the in/out arrays of every grid
-  struct Buf {
-    void *dst;
-    const void *src;
-    size_t bytes;
-  };
-  std::vector<Buf> bufs;
-  size_t total_bytes = 0;
-  for (int j = 0; j < n_grids; ++j) {
-    const rhd_grid_t &g = grids[j];
-    if (g.n_cells <= 0) continue;
-    const int64_t gs = g.state.group_stride ? g.state.group_stride : g.n_cells;
-    const size_t per = sizeof(double) * g.n_cells;
-    const size_t pg = sizeof(double) * ((int64_t)(g.groups.n_groups - 1) * gs + g.n_cells);
-    if (!g.state.egas || !g.state.erad) return RHD_EINVAL;
-    bufs.push_back({nullptr, g.state.egas, per});
-    for (int d = 0; d < 3; ++d) bufs.push_back({nullptr, g.state.mom[d], per});
-    bufs.push_back({nullptr, g.state.erad, pg});
-    for (int d = 0; d < 3; ++d) bufs.push_back({nullptr, g.state.frad[d], pg});
+  {  // every grid checked (and the workspace sized) before anything runs
+    int prec = 0;
+    int64_t items[2 * rhd::kBuckets] = {};
+    rc = rhd::pack_batch(ctx, grids, n_grids, ctx->cpi, &prec, items);
+    if (rc != RHD_OK) return rc;
   }
-  for (auto &b : bufs) total_bytes += (b.bytes + 255) & ~size_t(255);
-  char *save = nullptr;
-  if (cudaMalloc(&save, total_bytes) != cudaSuccess) return RHD_ENOMEM;
-  size_t off = 0;
-  for (auto &b : bufs) {
-    b.dst = save + off;
-    off += (b.bytes + 255) & ~size_t(255);
-    cudaMemcpyAsync(b.dst, b.src, b.bytes, cudaMemcpyDeviceToDevice, st);
-  }
-  auto restore = [&]() {
-    for (auto &b : bufs) cudaMemcpyAsync(const_cast<void *>(b.src), b.dst, b.bytes,
-                                         cudaMemcpyDeviceToDevice, st);
-  };
-  const int cand_threads[3] = {64, 128, 256};
-  const int cand_mult[3] = {1, 4, 16};
-  float best = 1e30f;
-  int bt = ctx->threads, bc = ctx->cpi;
+  rhd::StateSave sv;
+  rc = sv.take(grids, n_grids, st);
+  if (rc != RHD_OK) return rc;
   cudaEvent_t e0, e1;
-  cudaEventCreate(&e0);
-  cudaEventCreate(&e1);
-  rc = RHD_OK;
-  for (int a = 0; a < 3 && rc == RHD_OK; ++a) {
-    for (int b = 0; b < 3 && rc == RHD_OK; ++b) {
-      const int th = cand_threads[a], cpi = th * cand_mult[b];
-      int prec = 0;
-      int64_t items[2] = {0, 0};
-      rc = rhd::pack_batch(ctx, grids, n_grids, cpi, &prec, items);
-      if (rc != RHD_OK || items[0] + items[1] == 0) break;
-      cudaEventRecord(e0, st);
-      if (rhd::enqueue_any(ctx, prec, n_grids, th, cpi, sms, items, st) != cudaSuccess)
-        rc = RHD_ECUDA;
-      cudaEventRecord(e1, st);
-      restore();
-      if (cudaStreamSynchronize(st) != cudaSuccess) rc = RHD_ECUDA;
-      float ms = 0.0f;
-      cudaEventElapsedTime(&ms, e0, e1);
-      if (rc == RHD_OK && ms < best) {
-        best = ms;
-        bt = th;
-        bc = cpi;
+  if (cudaEventCreate(&e0) != cudaSuccess) return RHD_ECUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return RHD_ECUDA;
+  }
+  const int saved_pass[rhd::kBuckets] = {ctx->pass_map[0], ctx->pass_map[1], ctx->pass_map[2]};
+  const int saved_corr[rhd::kBuckets] = {ctx->corr_map[0], ctx->corr_map[1], ctx->corr_map[2]};
+  // each bucket on its own grids: first the passes' mapping (cell per thread
+  // or L lanes per cell), then the correction step's lanes per cell
+  std::vector<rhd_grid_t> sub;
+  sub.reserve(n_grids);
+  for (int b = 0; b < rhd::kBuckets && rc == RHD_OK; ++b) {
+    sub.clear();
+    for (int j = 0; j < n_grids; ++j)
+      if (rhd::bucket_of(grids[j].groups.n_groups) == b && grids[j].n_cells > 0)
+        sub.push_back(grids[j]);
+    if (sub.empty()) continue;
+    const bool mixed = sub[0].state.precision == RHD_MIXED;
+    for (int stage = 0; stage < (mixed ? 2 : 1) && rc == RHD_OK; ++stage) {
+      const int cands[4] = {1, 8, 16, 32};
+      float best = 1e30f;
+      int pick = stage == 0 ? ctx->pass_map[b] : ctx->corr_map[b];
+      for (int m : cands) {
+        if (stage == 0 ? !rhd::pass_mapping_ok(b, m) : !rhd::corr_mapping_ok(b, m)) continue;
+        (stage == 0 ? ctx->pass_map : ctx->corr_map)[b] = m;
+        float ms = 0.0f;
+        rc = rhd::time_candidate(ctx, sub.data(), (int)sub.size(), ctx->threads, ctx->cpi, sms,
+                                 sv, e0, e1, st, &ms);
+        if (rc != RHD_OK) break;
+        if (ms < best) {
+          best = ms;
+          pick = m;
+        }
       }
+      (stage == 0 ? ctx->pass_map : ctx->corr_map)[b] = pick;
     }
   }
+  // then the CTA shape of the cell-per-thread mapping, on every grid
+  bool any_thread = false;
+  for (int b = 0; b < rhd::kBuckets; ++b) any_thread = any_thread || ctx->pass_map[b] == 1;
+  int bt = ctx->threads, bc = ctx->cpi;
+  if (any_thread && rc == RHD_OK) {
+    const int cand_threads[3] = {64, 128, 256};
+    const int cand_mult[3] = {1, 4, 16};
+    float best = 1e30f;
+    for (int a = 0; a < 3 && rc == RHD_OK; ++a)
+      for (int m = 0; m < 3 && rc == RHD_OK; ++m) {
+        const int th = cand_threads[a], cpi = th * cand_mult[m];
+        float ms = 0.0f;
+        rc = rhd::time_candidate(ctx, grids, n_grids, th, cpi, sms, sv, e0, e1, st, &ms);
+        if (rc == RHD_OK && ms < best) {
+          best = ms;
+          bt = th;
+          bc = cpi;
+        }
+      }
+  }
+  cudaStreamSynchronize(st);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  cudaStreamSynchronize(st);
-  cudaFree(save);
-  if (rc != RHD_OK) return rc;
+  if (rc != RHD_OK) {
+    for (int b = 0; b < rhd::kBuckets; ++b) {
+      ctx->pass_map[b] = saved_pass[b];
+      ctx->corr_map[b] = saved_corr[b];
+    }
+    return rc;
+  }
   ctx->threads = bt;
   ctx->cpi = bc;
   return RHD_OK;

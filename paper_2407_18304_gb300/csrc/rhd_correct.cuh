@@ -277,373 +277,389 @@ struct CCell {
 // eq. numF1, the conservative write-back of E_g, E_gas and the momentum in
 // FP64.  Any other cell is left to the FP64 passes with its iterate in
 // W + U.
+// The correction step of cell i with L lanes (lane = the thread's lane in
+// its warp; the cell's segment is lanes lane0 .. lane0 + L - 1), gb this
+// warp's slice of the group blocks in shared memory.
 template <int L, int GPL>
-__global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant__ KParams P,
-                                                           const WarmOut W, const CorrOut U) {
-  extern __shared__ double sm[];
-  const GroupTable tab = build_table(P, sm);
+__device__ __forceinline__ void correct_cell(const KParams &P, const GroupTable &tab,
+                                             const WarmOut &W, const CorrOut &U, float *gb,
+                                             int64_t i, int lane, CCell<GPL> &C) {
   constexpr int NE = GPL + 1;
-  const int lane = threadIdx.x & 31, seg = lane / L, l = lane % L, lane0 = seg * L;
-  // each lane's group blocks (p, q, S: 20 floats per group slot) between the
-  // elimination and the step, lane-fastest (no bank conflicts)
-  float *gb = correct_blocks(sm, P.G) + (threadIdx.x / 32) * (GPL * 20 * 32);
+  const int seg = lane / L, l = lane % L, lane0 = seg * L;
   const unsigned mask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << lane0);
-  constexpr int CPW = 32 / L;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
-  const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
   const int G = P.G;
   const int64_t n = P.n;
   const double c = P.c, tdt = P.c_hat * P.theta * P.dt;
   const int src_lane = lane0 + (l + 1) % L;
   const float tol = (float)P.tol, tol_o = (float)P.tol_outer, crf = (float)P.cr;
-  CCell<GPL> C;
-  for (int64_t i = warp * CPW + seg; i < n; i += nwarps * CPW) {
-    // ---- the cell, validated as the FP64 passes validate it; an invalid
-    // cell or one without an FP32 iterate is left to them
-    const double Eint0 = W.eint[i];
-    const double rho = P.rho[i];
-    const double k0 = P.kappa0 ? P.kappa0[i] : 1.0;
-    const double m0[3] = {P.mom[0][i], P.mom[1][i], P.mom[2][i]};
-    const double eg0 = P.egas[i];
-    bool valid = Eint0 > 0.0 && rho > 0.0 && isfinite(rho) && isfinite(eg0) && isfinite(k0) &&
-                 k0 >= 0.0 && isfinite(m0[0]) && isfinite(m0[1]) && isfinite(m0[2]);
-    valid = valid && eg0 - 0.5 * (m0[0] * m0[0] + m0[1] * m0[1] + m0[2] * m0[2]) / rho > 0.0;
-    double sumE0 = 0.0;
+  // ---- the cell, validated as the FP64 passes validate it; an invalid
+  // cell or one without an FP32 iterate is left to them
+  const double Eint0 = W.eint[i];
+  const double rho = P.rho[i];
+  const double k0 = P.kappa0 ? P.kappa0[i] : 1.0;
+  const double m0[3] = {P.mom[0][i], P.mom[1][i], P.mom[2][i]};
+  const double eg0 = P.egas[i];
+  bool valid = Eint0 > 0.0 && rho > 0.0 && isfinite(rho) && isfinite(eg0) && isfinite(k0) &&
+               k0 >= 0.0 && isfinite(m0[0]) && isfinite(m0[1]) && isfinite(m0[2]);
+  valid = valid && eg0 - 0.5 * (m0[0] * m0[0] + m0[1] * m0[1] + m0[2] * m0[2]) / rho > 0.0;
+  double sumE0 = 0.0;
 #pragma unroll
-    for (int j = 0; j < GPL; ++j) {
-      const int g = l + L * j;
-      C.E0[j] = 0.0;
-      C.rw[j] = 0.0f;
+  for (int j = 0; j < GPL; ++j) {
+    const int g = l + L * j;
+    C.E0[j] = 0.0;
+    C.rw[j] = 0.0f;
+    for (int d = 0; d < 3; ++d) {
+      C.fw[j][d] = 0.0f;
+      C.ft[j][d] = 0.0;
+    }
+    if (g < G && valid) {
+      const int64_t o = (int64_t)g * P.gs + i;
+      const double e = P.erad[o], sg = P.src ? P.src[o] : 0.0;
+      C.E0[j] = e + sg;
+      valid = valid && isfinite(e) && isfinite(sg);
+      sumE0 += C.E0[j];
+      const int64_t ow = (int64_t)g * n + i;
+      C.rw[j] = W.r[ow];
       for (int d = 0; d < 3; ++d) {
-        C.fw[j][d] = 0.0f;
-        C.ft[j][d] = 0.0;
-      }
-      if (g < G && valid) {
-        const int64_t o = (int64_t)g * P.gs + i;
-        const double e = P.erad[o], sg = P.src ? P.src[o] : 0.0;
-        C.E0[j] = e + sg;
-        valid = valid && isfinite(e) && isfinite(sg);
-        sumE0 += C.E0[j];
-        const int64_t ow = (int64_t)g * n + i;
-        C.rw[j] = W.r[ow];
-        for (int d = 0; d < 3; ++d) {
-          C.ft[j][d] = P.frad[d][o];
-          valid = valid && isfinite(C.ft[j][d]);
-          C.fw[j][d] = W.f[(int64_t)d * G * n + ow];
-        }
+        C.ft[j][d] = P.frad[d][o];
+        valid = valid && isfinite(C.ft[j][d]);
+        C.fw[j][d] = W.f[(int64_t)d * G * n + ow];
       }
     }
-    if (!__all_sync(mask, valid)) {
-      if (l == 0) U.done[i] = 0;
-      continue;
-    }
-    sumE0 = seg_sum<L>(sumE0, mask);
-    const double Et = eg0 + P.cr * sumE0;
-    int shE;
-    const float imE = 1.0f / frexp_f(Et, shE);
-    const float imEc = imE * (float)P.ic;
-    const double fs = c * Et;
-    // the iterate in FP64
+  }
+  if (!__all_sync(mask, valid)) {
+    if (l == 0) U.done[i] = 0;
+    return;
+  }
+  sumE0 = seg_sum<L>(sumE0, mask);
+  const double Et = eg0 + P.cr * sumE0;
+  int shE;
+  const float imE = 1.0f / frexp_f(Et, shE);
+  const float imEc = imE * (float)P.ic;
+  const double fs = c * Et;
+  // the iterate in FP64
+#pragma unroll
+  for (int j = 0; j < GPL; ++j) {
+    C.R[j] = f2d(C.rw[j]) * Et;
+    for (int d = 0; d < 3; ++d) C.F[j][d] = f2d(C.fw[j][d]) * fs;
+  }
+  double Eint = Eint0;
+  const double irho = 1.0 / rho;
+  const double rcv = rho * P.c_v, irc = 1.0 / rcv;
+  int shV;
+  const float imV = 1.0f / frexp_f(rho * c, shV);
+  const float mu = scaled_f(Et * irho * P.icc, 0);  // E_tot / (rho c c_hat)
+  double cs = rho * k0;  // rho kappa0 (T/T_ref)^p
+  double its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
+  int et = 0;
+  float mt = tdt * cs > 0.0 ? frexp_f(tdt * cs, et) : 0.0f;  // c_hat theta dt cs = mt 2^et
+  int nit = W.nit[i], steps = 0, nres = 0;
+  bool finished = false, ok = true;
+  for (int k = 0; k <= kMaxCorrections; ++k) {
+    ++nres;
+    // ---- FP64 residual at the iterate: its momentum (eq. vupdate) and the
+    // sum of R_g, summed exactly
+    double dF[3] = {0.0, 0.0, 0.0}, sumR = 0.0;
 #pragma unroll
     for (int j = 0; j < GPL; ++j) {
-      C.R[j] = f2d(C.rw[j]) * Et;
-      for (int d = 0; d < 3; ++d) C.F[j][d] = f2d(C.fw[j][d]) * fs;
+      if (l + L * j >= G) continue;
+      sumR += C.R[j];
+      for (int d = 0; d < 3; ++d) dF[d] += C.F[j][d] - C.ft[j][d];
     }
-    double Eint = Eint0;
-    const double irho = 1.0 / rho;
-    const double rcv = rho * P.c_v, irc = 1.0 / rcv;
-    int shV;
-    const float imV = 1.0f / frexp_f(rho * c, shV);
-    const float mu = scaled_f(Et * irho * P.icc, 0);  // E_tot / (rho c c_hat)
-    double cs = rho * k0;  // rho kappa0 (T/T_ref)^p
-    double its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
-    int et = 0;
-    float mt = tdt * cs > 0.0 ? frexp_f(tdt * cs, et) : 0.0f;  // c_hat theta dt cs = mt 2^et
-    int nit = W.nit[i], steps = 0, nres = 0;
-    bool finished = false, ok = true;
-    for (int k = 0; k <= kMaxCorrections; ++k) {
-      ++nres;
-      // ---- FP64 residual at the iterate: its momentum (eq. vupdate) and the
-      // sum of R_g, summed exactly
-      double dF[3] = {0.0, 0.0, 0.0}, sumR = 0.0;
+    for (int d = 0; d < 3; ++d) dF[d] = seg_sum<L>(dF[d], mask);
+    sumR = seg_sum<L>(sumR, mask);
+    const double m[3] = {m0[0] - dF[0] * P.icc, m0[1] - dF[1] * P.icc, m0[2] - dF[2] * P.icc};
+    const double v[3] = {m[0] * irho, m[1] * irho, m[2] * irho};
+    const double KE = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) * irho;
+    const double T = Eint * irc;
+    if (P.temp_exp != 0.0) {  // the opacity scale follows T (otherwise set once per cell)
+      cs = rho * k0 * pow(T / P.T_ref, P.temp_exp);
+      its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
+      mt = tdt * cs > 0.0 ? frexp_f(tdt * cs, et) : 0.0f;
+    }
+    const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
+    const double invT = 1.0 / T;
+    double pqE[NE], dE_[NE], eE[NE];
+    bool lowE[NE];
 #pragma unroll
-      for (int j = 0; j < GPL; ++j) {
-        if (l + L * j >= G) continue;
-        sumR += C.R[j];
-        for (int d = 0; d < 3; ++d) dF[d] += C.F[j][d] - C.ft[j][d];
-      }
-      for (int d = 0; d < 3; ++d) dF[d] = seg_sum<L>(dF[d], mask);
-      sumR = seg_sum<L>(sumR, mask);
-      const double m[3] = {m0[0] - dF[0] * P.icc, m0[1] - dF[1] * P.icc, m0[2] - dF[2] * P.icc};
-      const double v[3] = {m[0] * irho, m[1] * irho, m[2] * irho};
-      const double KE = 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) * irho;
-      const double T = Eint * irc;
-      if (P.temp_exp != 0.0) {  // the opacity scale follows T (otherwise set once per cell)
-        cs = rho * k0 * pow(T / P.T_ref, P.temp_exp);
-        its = (tdt * cs > 0.0) ? 1.0 / (tdt * cs) : 0.0;
-        mt = tdt * cs > 0.0 ? frexp_f(tdt * cs, et) : 0.0f;
-      }
-      const double aT3 = P.a_rad * T * T * T, aT4 = aT3 * T;
-      const double invT = 1.0 / T;
-      double pqE[NE], dE_[NE], eE[NE];
-      bool lowE[NE];
-#pragma unroll
-      for (int jj = 0; jj < NE; ++jj) {
-        const int e = l + L * jj;
-        if (jj == NE - 1 && G == L * GPL) {  // the top edge alone (see winner_step)
-          const double xg = tab.xe[G] * invT;
-          if (xg >= 40.0 && xg < HUGE_VAL) {
-            const double em = exp(-xg);
-            const double x2 = xg * xg;
-            pqE[jj] = kPlanckNorm * em * (x2 * xg + 3.0 * x2 + 6.0 * xg + 6.0);
-            dE_[jj] = kPlanckNorm * em * x2 * x2;
-            eE[jj] = dE_[jj] * (4.0 - xg);
-            lowE[jj] = false;
-            continue;
-          }
-        }
-        edge_tab(tab.pc, e <= G ? tab.xe[e] * invT : 1.0, pqE[jj], dE_[jj], eE[jj], lowE[jj]);
-      }
-      // the same edge values in FP32 for the Jacobian (bit-pattern cut, no FP64 instruction)
-      float pqF[NE], dF_[NE], eF[NE];
-      bool lowF[NE];
-#pragma unroll
-      for (int jj = 0; jj < NE; ++jj) {
-        pqF[jj] = scaled_f(pqE[jj], 0);
-        dF_[jj] = scaled_f(dE_[jj], 0);
-        eF[jj] = scaled_f(eE[jj], 0);
-        lowF[jj] = lowE[jj];
-      }
-      const float be[3] = {scaled_f(m[0], shV) * imV, scaled_f(m[1], shV) * imV,
-                           scaled_f(m[2], shV) * imV};
-      float sabs = 0.0f, sdf[3] = {0.0f, 0.0f, 0.0f}, sfl = 0.0f;
-#pragma unroll
-      for (int j = 0; j < GPL; ++j) {
-        const double pa = __shfl_sync(mask, pqE[j], src_lane), pb = __shfl_sync(mask, pqE[j + 1], src_lane);
-        const double da = __shfl_sync(mask, dE_[j], src_lane), db_ = __shfl_sync(mask, dE_[j + 1], src_lane);
-        const int la = __shfl_sync(mask, (int)lowE[j], src_lane),
-                  lb = __shfl_sync(mask, (int)lowE[j + 1], src_lane);
-        const bool last = l == L - 1;
-        const double pqU = last ? pb : pa, dU = last ? db_ : da;
-        const bool lowU = (last ? lb : la) != 0;
-        const int g = l + L * j;
-        C.rR[j] = 0.0f;
-        C.rF[j][0] = C.rF[j][1] = C.rF[j][2] = 0.0f;
-        C.q[j] = 0.0f;
-        C.qe[j] = 0.0f;
-        if (g >= G) continue;
-        const double dP = band_fp64(pqE[j], lowE[j], pqU, lowU);
-        const double dD = dU - dE_[j];
-        const double b = aT4 * dP;
-        const double a = tab.alpha[g], rm = tab.rm[g], rp = tab.rp[g];
-        const double q = chiF_q<double>(b, aT4, dD, a, rm, rp, dE_[j], dU);
-        const double dnx = aT4 * (rp * dU - rm * dE_[j]);
-        const double chiB = cs * tab.kbar[g];
-        const double Enew = C.E0[j] + C.R[j];
-        const double w = (v[0] * C.F[j][0] + v[1] * C.F[j][1] + v[2] * C.F[j][2]) * P.inv_c2;
-        const double FR = chiB > 0.0 ? b + (1.0 + a) * q * w - C.R[j] * its * tab.ikbar[g] - Enew
-                                     : -C.R[j];
-        // the flux residual F - (eq. numF1 at this iterate), as wouter_end forms it
-        double ca, kn, kd;
-        closure_vP_parts<double>(P.closure, c, P.ic, Enew, C.F[j][0], C.F[j][1], C.F[j][2], v[0],
-                                 v[1], v[2], ca, kn, kd);
-        const double srcg = chiB * (b - dnx * (1.0 / 3.0));
-        const double den = 1.0 + tdt * chiB * q;
-        const double dk = den * kd;
-        double inv, kf;
-        if (dk > 1e-290) {
-          const double rr = 1.0 / dk;
-          inv = kd * rr;
-          kf = kn * den * rr;
-        } else {
-          inv = 1.0 / den;
-          kf = kn / kd;
-        }
-        const double kap = tdt * (1.0 + a) * chiB * inv;
-        C.rR[j] = scaled_f(FR, shE) * imE;
-        for (int d = 0; d < 3; ++d) {
-          const double vp = ca * v[d] + kf * C.F[j][d];
-          // eq. numF1 at the iterate: the cell's flux if this evaluation finishes
-          // it (the state's array holds it meanwhile; F^t stays in C.ft)
-          const double Fn = (C.ft[j][d] + tdt * v[d] * srcg) * inv + kap * vp;
-          P.frad[d][(int64_t)g * P.gs + i] = Fn;
-          const double FF = C.F[j][d] - Fn;
-          C.rF[j][d] = scaled_f(FF, shE) * imEc;
-          sdf[d] += C.rF[j][d];
-          sfl += fabsf(C.rF[j][d]);
-        }
-        const float tau = mt * scaled_f(tab.kbar[g], -et);
-        C.q[j] = scaled_f(q, 0);
-        C.qe[j] = tau > 0.0f ? tau / (1.0f + tau) : 0.0f;
-        sabs += fabsf(C.rR[j]);
-      }
-      // ---- the paper's tests on this residual: the inner test, and the
-      // outer test on the change one more outer pass would make (fluxes
-      // F - F_F, momentum and kinetic energy from them, the v.F terms of R_g
-      // after the implicit solve), taken to first order in the change
-      const double FG = Eint + KE - eg0 + P.cr * sumR;
-      sabs = seg_sumf<L>(sabs, mask);
-      for (int d = 0; d < 3; ++d) sdf[d] = seg_sumf<L>(sdf[d], mask);
-      const float db[3] = {mu * sdf[0], mu * sdf[1], mu * sdf[2]};  // d(v/c)
-      const float cf = (float)c;
-      const float mc[3] = {scaled_f(m[0], shE) * imE * cf, scaled_f(m[1], shE) * imE * cf,
-                           scaled_f(m[2], shE) * imE * cf};  // m c / E_tot
-      float cg = 0.0f;
-      bool gok = true;
-#pragma unroll
-      for (int j = 0; j < GPL; ++j) {
-        const int g = l + L * j;
-        if (g >= G) continue;
-        float dw = 0.0f;
-        for (int d = 0; d < 3; ++d)
-          dw += db[d] * (C.fw[j][d] - C.rF[j][d]) - be[d] * C.rF[j][d];
-        const float cgg = fabsf((1.0f + tab.alphaf[g]) * C.q[j] * dw) * C.qe[j];
-        cg += cgg;
-        if (P.flags & RHD_GROUP_TEST) {
-          const float e0 = scaled_f(C.E0[j], shE) * imE;
-          gok = gok && cgg <= tol_o * (fabsf(e0) + fabsf(e0 + C.rw[j]));
-        }
-      }
-      float chg = fabsf(mc[0] * db[0] + mc[1] * db[1] + mc[2] * db[2]) + seg_sumf<L>(cg, mask);
-      if (P.flags & RHD_FLUX_TEST) chg += seg_sumf<L>(sfl, mask);
-      gok = __all_sync(mask, gok);
-      if (fabs(FG) < P.tol * Et && crf * sabs < tol && chg <= tol_o && gok) {
-        finished = true;
-        break;
-      }
-      if (k == kMaxCorrections || !ok) break;
-      // ---- FP32 Jacobian at the iterate, group blocks, sums, the step
-      const float rG = scaled_f(FG, shE) * imE;
-      const float eint = scaled_f(Eint, shE) * imE;
-      const float aT4s = scaled_f(aT4, shE) * imE;
-      const float dTs = aT4s / eint;
-      float sums[20];
-      for (int t = 0; t < 20; ++t) sums[t] = 0.0f;
-#pragma unroll
-      for (int j = 0; j < GPL; ++j) {
-        const float pa = __shfl_sync(mask, pqF[j], src_lane), pb = __shfl_sync(mask, pqF[j + 1], src_lane);
-        const float da = __shfl_sync(mask, dF_[j], src_lane), db_ = __shfl_sync(mask, dF_[j + 1], src_lane);
-        const float ea = __shfl_sync(mask, eF[j], src_lane), eb = __shfl_sync(mask, eF[j + 1], src_lane);
-        const int la = __shfl_sync(mask, (int)lowF[j], src_lane),
-                  lb = __shfl_sync(mask, (int)lowF[j + 1], src_lane);
-        const bool last = l == L - 1;
-        const int g = l + L * j;
-        if (g >= G) {
-          for (int t = 0; t < 20; ++t) gb[(j * 20 + t) * 32 + lane] = 0.0f;
+    for (int jj = 0; jj < NE; ++jj) {
+      const int e = l + L * jj;
+      if (jj == NE - 1 && G == L * GPL) {  // the top edge alone (see winner_step)
+        const double xg = tab.xe[G] * invT;
+        if (xg >= 40.0 && xg < HUGE_VAL) {
+          const double em = exp(-xg);
+          const double x2 = xg * xg;
+          pqE[jj] = kPlanckNorm * em * (x2 * xg + 3.0 * x2 + 6.0 * xg + 6.0);
+          dE_[jj] = kPlanckNorm * em * x2 * x2;
+          eE[jj] = dE_[jj] * (4.0 - xg);
+          lowE[jj] = false;
           continue;
         }
-        const float tau = mt * scaled_f(tab.kbar[g], -et);
-        const float Eg = scaled_f(C.E0[j] + C.R[j], shE) * imE;
-        const float fcur[3] = {scaled_f(C.F[j][0], shE) * imEc, scaled_f(C.F[j][1], shE) * imEc,
-                               scaled_f(C.F[j][2], shE) * imEc};
-        GBlock blk;
-        ok = group_jac32(P.closure, tau, tab.alphaf[g], tab.rmf[g], tab.rpf[g], pqF[j], lowF[j],
-                         dF_[j], eF[j], last ? pb : pa, (last ? lb : la) != 0, last ? db_ : da,
-                         last ? eb : ea, aT4s, dTs, Eg, fcur, be, C.rR[j], C.rF[j], blk) && ok;
-        sums[0] += blk.p[0];
-        sums[1] += blk.q[0];
-        for (int t = 0; t < 3; ++t) {
-          sums[2 + t] += blk.S[t];
-          sums[5 + t] += blk.p[1 + t];
-          sums[8 + t] += blk.q[1 + t];
-          for (int c2 = 0; c2 < 3; ++c2) sums[11 + 3 * t + c2] += blk.S[3 * (1 + t) + c2];
-        }
-        for (int t = 0; t < 4; ++t) {
-          gb[(j * 20 + t) * 32 + lane] = blk.p[t];
-          gb[(j * 20 + 4 + t) * 32 + lane] = blk.q[t];
-        }
-        for (int t = 0; t < 12; ++t) gb[(j * 20 + 8 + t) * 32 + lane] = blk.S[t];
       }
-#pragma unroll
-      for (int t = 0; t < 20; ++t) sums[t] = seg_sumf<L>(sums[t], mask);
-      float x = 0.0f, beta[3] = {0.0f, 0.0f, 0.0f};
-      ok = global_solve(sums, rG, crf, mc, mu, x, beta) && ok;
-      ok = ok && fabsf(x) < kMaxStep;
-      float u[GPL][4];
-#pragma unroll
-      for (int j = 0; j < GPL; ++j)
-        for (int t = 0; t < 4; ++t) {
-          u[j][t] = gb[(j * 20 + t) * 32 + lane] + gb[(j * 20 + 4 + t) * 32 + lane] * x +
-                    gb[(j * 20 + 8 + 3 * t) * 32 + lane] * beta[0] +
-                    gb[(j * 20 + 9 + 3 * t) * 32 + lane] * beta[1] +
-                    gb[(j * 20 + 10 + 3 * t) * 32 + lane] * beta[2];
-          ok = ok && fabsf(u[j][t]) < kMaxStep;
-        }
-      ok = __all_sync(mask, ok);
-      if (!ok) break;  // the iterate stays the last good one
-      // ---- take the step (FP64)
-      Eint += f2d(x) * Et;
-#pragma unroll
-      for (int j = 0; j < GPL; ++j) {
-        if (l + L * j >= G) continue;
-        C.R[j] += f2d(u[j][0]) * Et;
-        for (int d = 0; d < 3; ++d) C.F[j][d] += f2d(u[j][1 + d]) * fs;
-      }
-      ++nit;
-      ++steps;
+      edge_tab(tab.pc, e <= G ? tab.xe[e] * invT : 1.0, pqE[jj], dE_[jj], eE[jj], lowE[jj]);
     }
-    if (l == 0) {
-      count_event(P, RHD_EV_CELLSC, 1);
-      count_event(P, RHD_EV_RESID64, nres);
-      count_event(P, RHD_EV_STEP32, steps);
-      count_event(P, RHD_EV_FINISH64, finished ? 1 : 0);
-    }
-    if (finished) {
-      // ---- the end of a converged pass, as the FP64 passes end it: each
-      // R_g from its own row, the flux update (F - F_F), the conservative
-      // write-back of E_g, E_gas and the momentum in FP64
-      double sR = 0.0, sF[3] = {0.0, 0.0, 0.0};
+    // the same edge values in FP32 for the Jacobian (bit-pattern cut, no FP64 instruction)
+    float pqF[NE], dF_[NE], eF[NE];
+    bool lowF[NE];
 #pragma unroll
-      for (int j = 0; j < GPL; ++j) {
-        const int g = l + L * j;
-        if (g >= G) continue;
-        const double R = C.R[j] + f2d(C.rR[j] * C.qe[j]) * Et;
-        const int64_t o = (int64_t)g * P.gs + i;
-        P.erad[o] = C.E0[j] + R;
-        sR += R;
-        for (int d = 0; d < 3; ++d) sF[d] += P.frad[d][o] - C.ft[j][d];
-      }
-      sR = seg_sum<L>(sR, mask);
-      for (int d = 0; d < 3; ++d) sF[d] = seg_sum<L>(sF[d], mask);
-      if (l == 0) {
-        P.egas[i] = eg0 - P.cr * sR;
-        for (int d = 0; d < 3; ++d) P.mom[d][i] = m0[d] - sF[d] * P.icc;
-        if (P.status) P.status[i] = RHD_STATUS_OK;
-        if (P.iters) P.iters[i] = (uint8_t)(nit > 255 ? 255 : nit);
-        U.done[i] = 1;
-      }
-      continue;
+    for (int jj = 0; jj < NE; ++jj) {
+      pqF[jj] = scaled_f(pqE[jj], 0);
+      dF_[jj] = scaled_f(dE_[jj], 0);
+      eF[jj] = scaled_f(eE[jj], 0);
+      lowF[jj] = lowE[jj];
     }
-    // ---- not finished: the FP64 passes start from W + U (the FP32 iterate
-    // and the steps taken here; none when no step was taken), from F^t
+    const float be[3] = {scaled_f(m[0], shV) * imV, scaled_f(m[1], shV) * imV,
+                         scaled_f(m[2], shV) * imV};
+    float sabs = 0.0f, sdf[3] = {0.0f, 0.0f, 0.0f}, sfl = 0.0f;
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      const double pa = __shfl_sync(mask, pqE[j], src_lane), pb = __shfl_sync(mask, pqE[j + 1], src_lane);
+      const double da = __shfl_sync(mask, dE_[j], src_lane), db_ = __shfl_sync(mask, dE_[j + 1], src_lane);
+      const int la = __shfl_sync(mask, (int)lowE[j], src_lane),
+                lb = __shfl_sync(mask, (int)lowE[j + 1], src_lane);
+      const bool last = l == L - 1;
+      const double pqU = last ? pb : pa, dU = last ? db_ : da;
+      const bool lowU = (last ? lb : la) != 0;
+      const int g = l + L * j;
+      C.rR[j] = 0.0f;
+      C.rF[j][0] = C.rF[j][1] = C.rF[j][2] = 0.0f;
+      C.q[j] = 0.0f;
+      C.qe[j] = 0.0f;
+      if (g >= G) continue;
+      const double dP = band_fp64(pqE[j], lowE[j], pqU, lowU);
+      const double dD = dU - dE_[j];
+      const double b = aT4 * dP;
+      const double a = tab.alpha[g], rm = tab.rm[g], rp = tab.rp[g];
+      const double q = chiF_q<double>(b, aT4, dD, a, rm, rp, dE_[j], dU);
+      const double dnx = aT4 * (rp * dU - rm * dE_[j]);
+      const double chiB = cs * tab.kbar[g];
+      const double Enew = C.E0[j] + C.R[j];
+      const double w = (v[0] * C.F[j][0] + v[1] * C.F[j][1] + v[2] * C.F[j][2]) * P.inv_c2;
+      const double FR = chiB > 0.0 ? b + (1.0 + a) * q * w - C.R[j] * its * tab.ikbar[g] - Enew
+                                   : -C.R[j];
+      // the flux residual F - (eq. numF1 at this iterate), as wouter_end forms it
+      double ca, kn, kd;
+      closure_vP_parts<double>(P.closure, c, P.ic, Enew, C.F[j][0], C.F[j][1], C.F[j][2], v[0],
+                               v[1], v[2], ca, kn, kd);
+      const double srcg = chiB * (b - dnx * (1.0 / 3.0));
+      const double den = 1.0 + tdt * chiB * q;
+      const double dk = den * kd;
+      double inv, kf;
+      if (dk > 1e-290) {
+        const double rr = 1.0 / dk;
+        inv = kd * rr;
+        kf = kn * den * rr;
+      } else {
+        inv = 1.0 / den;
+        kf = kn / kd;
+      }
+      const double kap = tdt * (1.0 + a) * chiB * inv;
+      C.rR[j] = scaled_f(FR, shE) * imE;
+      for (int d = 0; d < 3; ++d) {
+        const double vp = ca * v[d] + kf * C.F[j][d];
+        // eq. numF1 at the iterate: the cell's flux if this evaluation finishes
+        // it (the state's array holds it meanwhile; F^t stays in C.ft)
+        const double Fn = (C.ft[j][d] + tdt * v[d] * srcg) * inv + kap * vp;
+        P.frad[d][(int64_t)g * P.gs + i] = Fn;
+        const double FF = C.F[j][d] - Fn;
+        C.rF[j][d] = scaled_f(FF, shE) * imEc;
+        sdf[d] += C.rF[j][d];
+        sfl += fabsf(C.rF[j][d]);
+      }
+      const float tau = mt * scaled_f(tab.kbar[g], -et);
+      C.q[j] = scaled_f(q, 0);
+      C.qe[j] = tau > 0.0f ? tau / (1.0f + tau) : 0.0f;
+      sabs += fabsf(C.rR[j]);
+    }
+    // ---- the paper's tests on this residual: the inner test, and the
+    // outer test on the change one more outer pass would make (fluxes
+    // F - F_F, momentum and kinetic energy from them, the v.F terms of R_g
+    // after the implicit solve), taken to first order in the change
+    const double FG = Eint + KE - eg0 + P.cr * sumR;
+    sabs = seg_sumf<L>(sabs, mask);
+    for (int d = 0; d < 3; ++d) sdf[d] = seg_sumf<L>(sdf[d], mask);
+    const float db[3] = {mu * sdf[0], mu * sdf[1], mu * sdf[2]};  // d(v/c)
+    const float cf = (float)c;
+    const float mc[3] = {scaled_f(m[0], shE) * imE * cf, scaled_f(m[1], shE) * imE * cf,
+                         scaled_f(m[2], shE) * imE * cf};  // m c / E_tot
+    float cg = 0.0f;
+    bool gok = true;
 #pragma unroll
     for (int j = 0; j < GPL; ++j) {
       const int g = l + L * j;
       if (g >= G) continue;
-      for (int d = 0; d < 3; ++d) P.frad[d][(int64_t)g * P.gs + i] = C.ft[j][d];
-      const int64_t o = (int64_t)g * n + i;
-      U.ur[o] = steps ? scaled_f(C.R[j] - f2d(C.rw[j]) * Et, shE) * imE : 0.0f;
+      float dw = 0.0f;
       for (int d = 0; d < 3; ++d)
-        U.uf[(int64_t)d * G * n + o] =
-            steps ? scaled_f(C.F[j][d] - f2d(C.fw[j][d]) * fs, shE) * imEc : 0.0f;
-    }
-    double dF[3] = {0.0, 0.0, 0.0};
-    if (steps) {
-#pragma unroll
-      for (int j = 0; j < GPL; ++j)
-        if (l + L * j < G)
-          for (int d = 0; d < 3; ++d) dF[d] += C.F[j][d] - C.ft[j][d];
-      for (int d = 0; d < 3; ++d) dF[d] = seg_sum<L>(dF[d], mask);
-    }
-    if (l == 0) {
-      if (steps) {
-        W.eint[i] = Eint;
-        for (int d = 0; d < 3; ++d) W.mom[(int64_t)d * n + i] = m0[d] - dF[d] * P.icc;
-        W.nit[i] = (uint8_t)(nit > 255 ? 255 : nit);
+        dw += db[d] * (C.fw[j][d] - C.rF[j][d]) - be[d] * C.rF[j][d];
+      const float cgg = fabsf((1.0f + tab.alphaf[g]) * C.q[j] * dw) * C.qe[j];
+      cg += cgg;
+      if (P.flags & RHD_GROUP_TEST) {
+        const float e0 = scaled_f(C.E0[j], shE) * imE;
+        gok = gok && cgg <= tol_o * (fabsf(e0) + fabsf(e0 + C.rw[j]));
       }
-      U.done[i] = 0;
     }
+    float chg = fabsf(mc[0] * db[0] + mc[1] * db[1] + mc[2] * db[2]) + seg_sumf<L>(cg, mask);
+    if (P.flags & RHD_FLUX_TEST) chg += seg_sumf<L>(sfl, mask);
+    gok = __all_sync(mask, gok);
+    if (fabs(FG) < P.tol * Et && crf * sabs < tol && chg <= tol_o && gok) {
+      finished = true;
+      break;
+    }
+    if (k == kMaxCorrections || !ok) break;
+    // ---- FP32 Jacobian at the iterate, group blocks, sums, the step
+    const float rG = scaled_f(FG, shE) * imE;
+    const float eint = scaled_f(Eint, shE) * imE;
+    const float aT4s = scaled_f(aT4, shE) * imE;
+    const float dTs = aT4s / eint;
+    float sums[20];
+    for (int t = 0; t < 20; ++t) sums[t] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      const float pa = __shfl_sync(mask, pqF[j], src_lane), pb = __shfl_sync(mask, pqF[j + 1], src_lane);
+      const float da = __shfl_sync(mask, dF_[j], src_lane), db_ = __shfl_sync(mask, dF_[j + 1], src_lane);
+      const float ea = __shfl_sync(mask, eF[j], src_lane), eb = __shfl_sync(mask, eF[j + 1], src_lane);
+      const int la = __shfl_sync(mask, (int)lowF[j], src_lane),
+                lb = __shfl_sync(mask, (int)lowF[j + 1], src_lane);
+      const bool last = l == L - 1;
+      const int g = l + L * j;
+      if (g >= G) {
+        for (int t = 0; t < 20; ++t) gb[(j * 20 + t) * 32 + lane] = 0.0f;
+        continue;
+      }
+      const float tau = mt * scaled_f(tab.kbar[g], -et);
+      const float Eg = scaled_f(C.E0[j] + C.R[j], shE) * imE;
+      const float fcur[3] = {scaled_f(C.F[j][0], shE) * imEc, scaled_f(C.F[j][1], shE) * imEc,
+                             scaled_f(C.F[j][2], shE) * imEc};
+      GBlock blk;
+      ok = group_jac32(P.closure, tau, tab.alphaf[g], tab.rmf[g], tab.rpf[g], pqF[j], lowF[j],
+                       dF_[j], eF[j], last ? pb : pa, (last ? lb : la) != 0, last ? db_ : da,
+                       last ? eb : ea, aT4s, dTs, Eg, fcur, be, C.rR[j], C.rF[j], blk) && ok;
+      sums[0] += blk.p[0];
+      sums[1] += blk.q[0];
+      for (int t = 0; t < 3; ++t) {
+        sums[2 + t] += blk.S[t];
+        sums[5 + t] += blk.p[1 + t];
+        sums[8 + t] += blk.q[1 + t];
+        for (int c2 = 0; c2 < 3; ++c2) sums[11 + 3 * t + c2] += blk.S[3 * (1 + t) + c2];
+      }
+      for (int t = 0; t < 4; ++t) {
+        gb[(j * 20 + t) * 32 + lane] = blk.p[t];
+        gb[(j * 20 + 4 + t) * 32 + lane] = blk.q[t];
+      }
+      for (int t = 0; t < 12; ++t) gb[(j * 20 + 8 + t) * 32 + lane] = blk.S[t];
+    }
+#pragma unroll
+    for (int t = 0; t < 20; ++t) sums[t] = seg_sumf<L>(sums[t], mask);
+    float x = 0.0f, beta[3] = {0.0f, 0.0f, 0.0f};
+    ok = global_solve(sums, rG, crf, mc, mu, x, beta) && ok;
+    ok = ok && fabsf(x) < kMaxStep;
+    float u[GPL][4];
+#pragma unroll
+    for (int j = 0; j < GPL; ++j)
+      for (int t = 0; t < 4; ++t) {
+        u[j][t] = gb[(j * 20 + t) * 32 + lane] + gb[(j * 20 + 4 + t) * 32 + lane] * x +
+                  gb[(j * 20 + 8 + 3 * t) * 32 + lane] * beta[0] +
+                  gb[(j * 20 + 9 + 3 * t) * 32 + lane] * beta[1] +
+                  gb[(j * 20 + 10 + 3 * t) * 32 + lane] * beta[2];
+        ok = ok && fabsf(u[j][t]) < kMaxStep;
+      }
+    ok = __all_sync(mask, ok);
+    if (!ok) break;  // the iterate stays the last good one
+    // ---- take the step (FP64)
+    Eint += f2d(x) * Et;
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      if (l + L * j >= G) continue;
+      C.R[j] += f2d(u[j][0]) * Et;
+      for (int d = 0; d < 3; ++d) C.F[j][d] += f2d(u[j][1 + d]) * fs;
+    }
+    ++nit;
+    ++steps;
   }
+  if (l == 0) {
+    count_event(P, RHD_EV_CELLSC, 1);
+    count_event(P, RHD_EV_RESID64, nres);
+    count_event(P, RHD_EV_STEP32, steps);
+    count_event(P, RHD_EV_FINISH64, finished ? 1 : 0);
+  }
+  if (finished) {
+    // ---- the end of a converged pass, as the FP64 passes end it: each
+    // R_g from its own row, the flux update (F - F_F), the conservative
+    // write-back of E_g, E_gas and the momentum in FP64
+    double sR = 0.0, sF[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      const int g = l + L * j;
+      if (g >= G) continue;
+      const double R = C.R[j] + f2d(C.rR[j] * C.qe[j]) * Et;
+      const int64_t o = (int64_t)g * P.gs + i;
+      P.erad[o] = C.E0[j] + R;
+      sR += R;
+      for (int d = 0; d < 3; ++d) sF[d] += P.frad[d][o] - C.ft[j][d];
+    }
+    sR = seg_sum<L>(sR, mask);
+    for (int d = 0; d < 3; ++d) sF[d] = seg_sum<L>(sF[d], mask);
+    if (l == 0) {
+      P.egas[i] = eg0 - P.cr * sR;
+      for (int d = 0; d < 3; ++d) P.mom[d][i] = m0[d] - sF[d] * P.icc;
+      if (P.status) P.status[i] = RHD_STATUS_OK;
+      if (P.iters) P.iters[i] = (uint8_t)(nit > 255 ? 255 : nit);
+      U.done[i] = 1;
+    }
+    return;
+  }
+  // ---- not finished: the FP64 passes start from W + U (the FP32 iterate
+  // and the steps taken here; none when no step was taken), from F^t
+#pragma unroll
+  for (int j = 0; j < GPL; ++j) {
+    const int g = l + L * j;
+    if (g >= G) continue;
+    for (int d = 0; d < 3; ++d) P.frad[d][(int64_t)g * P.gs + i] = C.ft[j][d];
+    const int64_t o = (int64_t)g * n + i;
+    U.ur[o] = steps ? scaled_f(C.R[j] - f2d(C.rw[j]) * Et, shE) * imE : 0.0f;
+    for (int d = 0; d < 3; ++d)
+      U.uf[(int64_t)d * G * n + o] =
+          steps ? scaled_f(C.F[j][d] - f2d(C.fw[j][d]) * fs, shE) * imEc : 0.0f;
+  }
+  double dF[3] = {0.0, 0.0, 0.0};
+  if (steps) {
+#pragma unroll
+    for (int j = 0; j < GPL; ++j)
+      if (l + L * j < G)
+        for (int d = 0; d < 3; ++d) dF[d] += C.F[j][d] - C.ft[j][d];
+    for (int d = 0; d < 3; ++d) dF[d] = seg_sum<L>(dF[d], mask);
+  }
+  if (l == 0) {
+    if (steps) {
+      W.eint[i] = Eint;
+      for (int d = 0; d < 3; ++d) W.mom[(int64_t)d * n + i] = m0[d] - dF[d] * P.icc;
+      W.nit[i] = (uint8_t)(nit > 255 ? 255 : nit);
+    }
+    U.done[i] = 0;
+  }
+}
+
+// Warp w's slice of the group blocks (p, q, S: 20 floats per group slot,
+// lane-fastest: no bank conflicts) that a cell keeps in shared memory between
+// the elimination and the step; blocks is the CTA's first slice.
+template <int GPL>
+__device__ __forceinline__ float *warp_blocks(float *blocks, int w) {
+  return blocks + w * (GPL * 20 * 32);
+}
+
+template <int L, int GPL>
+__global__ void __launch_bounds__(128) correct_warp_kernel(const __grid_constant__ KParams P,
+                                                           const WarmOut W, const CorrOut U) {
+  extern __shared__ double sm[];
+  const GroupTable tab = build_table(P, sm);
+  const int lane = threadIdx.x & 31, seg = lane / L;
+  float *gb = warp_blocks<GPL>(correct_blocks(sm, P.G), threadIdx.x / 32);
+  constexpr int CPW = 32 / L;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
+  CCell<GPL> C;
+  for (int64_t i = warp * CPW + seg; i < P.n; i += nwarps * CPW)
+    correct_cell<L, GPL>(P, tab, W, U, gb, i, lane, C);
 }
 
 }  // namespace rhd

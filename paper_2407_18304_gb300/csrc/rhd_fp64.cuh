@@ -530,16 +530,61 @@ __device__ __forceinline__ void apply_warm(const KParams &P, const WarmStart &W,
   }
 }
 
+// The FP64 passes of cell i, one cell per thread.  With a warm start (W.r)
+// the first attempt starts from it; if that attempt does not converge and
+// W.fallback is set, the cell is solved again from the cold start (status
+// FALLBACK if that converges).  A cell the correction step finished (W.done)
+// is skipped.  CACHE: take the cached first iteration of each outer pass.
+template <int MAXG, bool CACHE = false>
+__device__ __forceinline__ void fp64_cell(const KParams &P, const GroupTable &tab,
+                                          const WarmStart &W, int64_t i, Cell &C,
+                                          Arr64<MAXG> &A) {
+  const bool warm = W.r != nullptr;
+  if (W.done && W.done[i]) return;
+  if (!load_cell(P, i, C, A)) return;
+  C.use_cache = CACHE;
+  C.nfn = 0;
+  unsigned ne = 0, nc = 0, no = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    int nit0 = 0;
+    if (attempt == 1) {
+      if (!(warm && W.fallback && C.stat != RHD_STATUS_OK)) break;
+      nit0 = C.nit;
+      load_cell(P, i, C, A);
+      C.use_cache = CACHE;
+    }
+    set_tau(P, tab, C, A, C.chi0s);
+    if (warm && attempt == 0) apply_warm(P, W, C, A);
+    outer_begin(P, C, A);
+    for (;;) {
+      if (CACHE && C.cached) ++nc;
+      else ++ne;
+      const int r = inner_step<MAXG, CACHE>(P, tab, C, A);
+      if (r == 0) continue;
+      if (r == 2) C.stat = RHD_STATUS_MAXITER;
+      ++no;
+      if (outer_end(P, tab, C, A)) break;
+    }
+    if (attempt == 1) {
+      C.nit += nit0;
+      if (C.stat == RHD_STATUS_OK) C.stat = RHD_STATUS_FALLBACK;
+    }
+  }
+  store_cell(P, C, A);
+  count_event(P, RHD_EV_CELLS64, 1);
+  count_event(P, RHD_EV_EVAL64, ne);
+  count_event(P, RHD_EV_CACHED64, nc);
+  count_event(P, RHD_EV_OUTER64, no);
+  count_event(P, RHD_EV_FLUXNEWTON, C.nfn);
+}
+
 // FP64 solve, one cell per thread: each thread walks the cells i, i + stride,
-// ..., finishing each before the next.  With a warm start (W.r) the first
-// attempt starts from it; if that attempt does not converge and W.fallback is
-// set, the cell is solved again from the cold start (status FALLBACK if that
-// converges).  CACHE: take the cached first iteration of each outer pass.  The
-// lanes of a warp hold different cells here, so a cached iteration on some
-// lanes runs beside full evaluations on others and saves nothing (measured:
-// +50 % time at 16 and 32 groups, and the extra path costs registers); it is
-// instantiated for RHD_CELL_PER_THREAD, which runs the warp mapping's
-// algorithm to count its operations.
+// ..., finishing each before the next.  The lanes of a warp hold different
+// cells here, so a cached iteration on some lanes runs beside full
+// evaluations on others and saves nothing (measured: +50 % time at 16 and 32
+// groups, and the extra path costs registers); CACHE is instantiated for
+// RHD_CELL_PER_THREAD, which runs the warp mapping's algorithm to count its
+// operations.
 template <int MAXG, bool CACHE = false>
 __global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__ KParams P,
                                                          const WarmStart W) {
@@ -548,45 +593,8 @@ __global__ void __launch_bounds__(128) solve_fp64_kernel(const __grid_constant__
   Arr64<MAXG> A;
   Cell C;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  const bool warm = W.r != nullptr;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride) {
-    if (W.done && W.done[i]) continue;
-    if (!load_cell(P, i, C, A)) continue;
-    C.use_cache = CACHE;
-    C.nfn = 0;
-    unsigned ne = 0, nc = 0, no = 0;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      int nit0 = 0;
-      if (attempt == 1) {
-        if (!(warm && W.fallback && C.stat != RHD_STATUS_OK)) break;
-        nit0 = C.nit;
-        load_cell(P, i, C, A);
-        C.use_cache = CACHE;
-      }
-      set_tau(P, tab, C, A, C.chi0s);
-      if (warm && attempt == 0) apply_warm(P, W, C, A);
-      outer_begin(P, C, A);
-      for (;;) {
-        if (CACHE && C.cached) ++nc;
-        else ++ne;
-        const int r = inner_step<MAXG, CACHE>(P, tab, C, A);
-        if (r == 0) continue;
-        if (r == 2) C.stat = RHD_STATUS_MAXITER;
-        ++no;
-        if (outer_end(P, tab, C, A)) break;
-      }
-      if (attempt == 1) {
-        C.nit += nit0;
-        if (C.stat == RHD_STATUS_OK) C.stat = RHD_STATUS_FALLBACK;
-      }
-    }
-    store_cell(P, C, A);
-    count_event(P, RHD_EV_CELLS64, 1);
-    count_event(P, RHD_EV_EVAL64, ne);
-    count_event(P, RHD_EV_CACHED64, nc);
-    count_event(P, RHD_EV_OUTER64, no);
-    count_event(P, RHD_EV_FLUXNEWTON, C.nfn);
-  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < P.n; i += stride)
+    fp64_cell<MAXG, CACHE>(P, tab, W, i, C, A);
 }
 
 }  // namespace rhd

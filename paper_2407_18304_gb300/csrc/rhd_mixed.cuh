@@ -330,24 +330,24 @@ __device__ __forceinline__ void store_warm(const KParams &P, const WarmOut &W, c
   }
 }
 
-// Phase A launch: lane-persistent FP32 iteration; writes the warm start.
-// S.r non-null: each cell starts from S (E_int and R_g / E_tot; a surrogate's
-// guess) instead of the cold start.  S may alias W (each thread reads its
-// cell's start before it writes that cell's result).
+// The FP32 passes of cells i, i + stride, ... < end, one cell per thread,
+// lane-persistent: a thread takes its next cell as soon as its current one is
+// stored, so the lanes of a warp stay busy while their cells take different
+// iteration counts (every lane of the warp must call this).  S.r non-null:
+// each cell starts from S (E_int and R_g / E_tot; a surrogate's guess)
+// instead of the cold start.  S may alias W (each thread reads its cell's
+// start before it writes that cell's result).
 template <int MAXG>
-__global__ void __launch_bounds__(128) warm_fp32_kernel(const __grid_constant__ KParams P,
-                                                        const WarmOut W, const WarmStart S) {
-  extern __shared__ double sm[];
-  const GroupTable tab = build_table(P, sm);
+__device__ __forceinline__ void fp32_cells(const KParams &P, const GroupTable &tab,
+                                           const WarmOut &W, const WarmStart &S, int64_t i,
+                                           int64_t end, int64_t stride) {
   Arr32<MAXG> B;
   Cell C;
   Cell32 D;
-  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   unsigned ne = 0, no = 0;
   auto next = [&]() -> bool {
     ne = no = 0;
-    while (i < P.n) {
+    while (i < end) {
       if (load_cell32(P, tab, i, C, D, B)) {
         if (S.r && S.eint[i] > 0.0) {
           C.Eint = S.eint[i];
@@ -376,6 +376,16 @@ __global__ void __launch_bounds__(128) warm_fp32_kernel(const __grid_constant__ 
       }
     }
   }
+}
+
+// Phase A launch: the FP32 passes over the whole grid; writes the warm start.
+template <int MAXG>
+__global__ void __launch_bounds__(128) warm_fp32_kernel(const __grid_constant__ KParams P,
+                                                        const WarmOut W, const WarmStart S) {
+  extern __shared__ double sm[];
+  const GroupTable tab = build_table(P, sm);
+  fp32_cells<MAXG>(P, tab, W, S, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, P.n,
+                   (int64_t)gridDim.x * blockDim.x);
 }
 
 }  // namespace rhd

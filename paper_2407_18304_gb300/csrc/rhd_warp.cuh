@@ -475,6 +475,55 @@ __device__ __forceinline__ void wstore(const KParams &P, int l, const WCell<L, G
   }
 }
 
+// The FP64 passes of one cell with L lanes (lane l of the cell's segment,
+// mask its lanes): from the warm start in W where W.r is set (skipping a cell
+// the correction step finished), with the cold restart on failure.
+template <int L, int GPL>
+__device__ __forceinline__ void warp_cell(const KParams &P, const GroupTable &tab,
+                                          const WarmStart &W, int64_t i, int l, int lane0,
+                                          unsigned mask, WCell<L, GPL> &C) {
+  const bool warm = W.r != nullptr;
+  if (W.done && W.done[i]) return;
+  if (!wload(P, i, l, mask, C)) return;
+  unsigned ne = 0, nc = 0, no = 0;
+  C.nfn = 0;
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    int nit0 = 0;
+    if (attempt == 1) {
+      if (!(warm && W.fallback && C.stat != RHD_STATUS_OK)) break;
+      nit0 = C.nit;
+      wload(P, i, l, mask, C);
+    }
+    wset_tau(P, tab, l, C, C.chi0s);
+    if (warm && attempt == 0) wapply_warm(P, W, l, C);
+    wouter_begin(P, C);
+    for (;;) {
+      if (C.cached) ++nc;
+      else ++ne;
+      const int r = winner_step(P, tab, l, lane0, mask, C);
+      if (r == 0) continue;
+      if (r == 2) C.stat = RHD_STATUS_MAXITER;
+      ++no;
+      if (wouter_end(P, tab, l, mask, C)) break;
+    }
+    if (attempt == 1) {
+      C.nit += nit0;
+      if (C.stat == RHD_STATUS_OK) C.stat = RHD_STATUS_FALLBACK;
+    }
+  }
+  wstore(P, l, C);
+  if (P.count) {
+    const unsigned nfn = __reduce_add_sync(mask, C.nfn);
+    if (l == 0) {
+      count_event(P, RHD_EV_CELLS64, 1);
+      count_event(P, RHD_EV_EVAL64, ne);
+      count_event(P, RHD_EV_CACHED64, nc);
+      count_event(P, RHD_EV_OUTER64, no);
+      count_event(P, RHD_EV_FLUXNEWTON, nfn);
+    }
+  }
+}
+
 // FP64 solve with L lanes per cell (32 / L cells per warp); warm start and
 // cold restart as solve_fp64_kernel.
 template <int L, int GPL>
@@ -488,49 +537,9 @@ __global__ void __launch_bounds__(128) solve_warp_kernel(const __grid_constant__
   constexpr int CPW = 32 / L;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
-  const bool warm = W.r != nullptr;
   WCell<L, GPL> C;
-  for (int64_t i = warp * CPW + seg; i < P.n; i += nwarps * CPW) {
-    if (W.done && W.done[i]) continue;
-    if (!wload(P, i, l, mask, C)) continue;
-    unsigned ne = 0, nc = 0, no = 0;
-    C.nfn = 0;
-    for (int attempt = 0; attempt < 2; ++attempt) {
-      int nit0 = 0;
-      if (attempt == 1) {
-        if (!(warm && W.fallback && C.stat != RHD_STATUS_OK)) break;
-        nit0 = C.nit;
-        wload(P, i, l, mask, C);
-      }
-      wset_tau(P, tab, l, C, C.chi0s);
-      if (warm && attempt == 0) wapply_warm(P, W, l, C);
-      wouter_begin(P, C);
-      for (;;) {
-        if (C.cached) ++nc;
-        else ++ne;
-        const int r = winner_step(P, tab, l, lane0, mask, C);
-        if (r == 0) continue;
-        if (r == 2) C.stat = RHD_STATUS_MAXITER;
-        ++no;
-        if (wouter_end(P, tab, l, mask, C)) break;
-      }
-      if (attempt == 1) {
-        C.nit += nit0;
-        if (C.stat == RHD_STATUS_OK) C.stat = RHD_STATUS_FALLBACK;
-      }
-    }
-    wstore(P, l, C);
-    if (P.count) {
-      const unsigned nfn = __reduce_add_sync(mask, C.nfn);
-      if (l == 0) {
-        count_event(P, RHD_EV_CELLS64, 1);
-        count_event(P, RHD_EV_EVAL64, ne);
-        count_event(P, RHD_EV_CACHED64, nc);
-        count_event(P, RHD_EV_OUTER64, no);
-        count_event(P, RHD_EV_FLUXNEWTON, nfn);
-      }
-    }
-  }
+  for (int64_t i = warp * CPW + seg; i < P.n; i += nwarps * CPW)
+    warp_cell<L, GPL>(P, tab, W, i, l, lane0, mask, C);
 }
 
 }  // namespace rhd

@@ -372,6 +372,51 @@ __device__ __forceinline__ void w32_store(const KParams &P, const WarmOut &W, in
   }
 }
 
+// The FP32 passes of one cell with L lanes (lane l of the cell's segment,
+// mask its lanes); writes the cell's warm start to W.  S.r non-null starts the
+// cell from S (may alias W).
+template <int L, int GPL>
+__device__ __forceinline__ void w32_cell(const KParams &P, const GroupTable &tab, const float *pf,
+                                         const WarmOut &W, const WarmStart &S, int64_t i, int l,
+                                         int lane0, unsigned mask, WCell32<L, GPL> &C) {
+  if (!w32_load(P, tab, i, l, mask, C)) return;
+  if (S.r && S.eint[i] > 0.0) {
+    C.Eint = S.eint[i];
+#pragma unroll
+    for (int j = 0; j < GPL; ++j) {
+      const int g = l + L * j;
+      if (g < P.G) C.R[j] = S.r[(int64_t)g * P.n + i];
+    }
+  }
+  w32_outer_begin(P, C);
+  unsigned ne = 0, no = 0;
+  for (;;) {
+    const int r = w32_inner_step(P, tab, pf, l, lane0, mask, C);
+    ++ne;
+    if (r == 0) continue;
+    ++no;
+    if (w32_outer_end(P, tab, l, mask, C)) break;
+  }
+  w32_store(P, W, l, C);
+  if (l == 0) {
+    count_event(P, RHD_EV_CELLS32, 1);
+    count_event(P, RHD_EV_EVAL32, ne);
+    count_event(P, RHD_EV_OUTER32, no);
+  }
+}
+
+// The FP32 copy of the Planck polynomials the FP32 warp passes use (the
+// coefficients up to kDeg32, then the segment centres and 1/half-widths),
+// from the FP64 table at pc.
+__device__ __forceinline__ void load_planck32(const double *pc, float *pf) {
+  using namespace planck_table;
+  for (int t = threadIdx.x; t < kPlanckF; t += blockDim.x) {
+    const int k = t / kSeg, s = t % kSeg;
+    const int src = k <= kDeg32 ? k * kSeg + s : (kDeg + 1 + (k - kDeg32 - 1)) * kSeg + s;
+    pf[t] = (float)pc[src];
+  }
+}
+
 // Phase A of the mixed form with L lanes per cell (warm_fp32_kernel's job):
 // writes the warm start W; S.r non-null starts each cell from S (may alias W).
 template <int L, int GPL>
@@ -380,15 +425,7 @@ __global__ void __launch_bounds__(128) warm_warp32_kernel(const __grid_constant_
   extern __shared__ double sm[];
   __shared__ float pf[kPlanckF];
   const GroupTable tab = build_table(P, sm);
-  {
-    using namespace planck_table;
-    for (int t = threadIdx.x; t < kPlanckF; t += blockDim.x) {
-      const int k = t / kSeg, s = t % kSeg;
-      // coefficients 0..kDeg32, then centres and 1/half-widths
-      const int src = k <= kDeg32 ? k * kSeg + s : (kDeg + 1 + (k - kDeg32 - 1)) * kSeg + s;
-      pf[t] = (float)tab.pc[src];
-    }
-  }
+  load_planck32(tab.pc, pf);
   __syncthreads();
   const int lane = threadIdx.x & 31, seg = lane / L, l = lane % L, lane0 = seg * L;
   const unsigned mask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << lane0);
@@ -396,32 +433,8 @@ __global__ void __launch_bounds__(128) warm_warp32_kernel(const __grid_constant_
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
   WCell32<L, GPL> C;
-  for (int64_t i = warp * CPW + seg; i < P.n; i += nwarps * CPW) {
-    if (!w32_load(P, tab, i, l, mask, C)) continue;
-    if (S.r && S.eint[i] > 0.0) {
-      C.Eint = S.eint[i];
-#pragma unroll
-      for (int j = 0; j < GPL; ++j) {
-        const int g = l + L * j;
-        if (g < P.G) C.R[j] = S.r[(int64_t)g * P.n + i];
-      }
-    }
-    w32_outer_begin(P, C);
-    unsigned ne = 0, no = 0;
-    for (;;) {
-      const int r = w32_inner_step(P, tab, pf, l, lane0, mask, C);
-      ++ne;
-      if (r == 0) continue;
-      ++no;
-      if (w32_outer_end(P, tab, l, mask, C)) break;
-    }
-    w32_store(P, W, l, C);
-    if (l == 0) {
-      count_event(P, RHD_EV_CELLS32, 1);
-      count_event(P, RHD_EV_EVAL32, ne);
-      count_event(P, RHD_EV_OUTER32, no);
-    }
-  }
+  for (int64_t i = warp * CPW + seg; i < P.n; i += nwarps * CPW)
+    w32_cell<L, GPL>(P, tab, pf, W, S, i, l, lane0, mask, C);
 }
 
 }  // namespace rhd

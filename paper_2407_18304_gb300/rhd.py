@@ -95,6 +95,12 @@ def lib() -> ctypes.CDLL:
         _lib.rhd_context_shape.restype = ctypes.c_int
         _lib.rhd_context_shape.argtypes = [_P, ctypes.POINTER(ctypes.c_int32),
                                            ctypes.POINTER(ctypes.c_int32)]
+        _lib.rhd_context_mapping.restype = ctypes.c_int
+        _lib.rhd_context_mapping.argtypes = [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32)]
+        _lib.rhd_context_set_mapping.restype = ctypes.c_int
+        _lib.rhd_context_set_mapping.argtypes = [_P, ctypes.c_int32, ctypes.c_int32,
+                                                 ctypes.c_int32]
         _F = ctypes.c_void_p
         sig = {
             "rhd_surrogate_create": [ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(_P)],
@@ -414,9 +420,16 @@ class GridSpec:
         self.c = Grid(st, Groups(G, _dp(e)), lw, float(dt), int(n))
 
 
+BATCH_BUCKETS = 3  # RHD_BATCH_BUCKETS: group counts 1..16, 17..32, 33..64
+# the mappings each bucket offers, as lanes per cell (1: one cell per thread)
+PASS_MAPPINGS = ((1, 8), (1, 8, 16, 32), (1, 16, 32))
+CORRECTION_MAPPINGS = ((8,), (8, 16), (16, 32))
+
+
 class Context:
     """A batched-update context (``rhd_context_t``): staging buffers, the
-    captured CUDA graph and the tuned launch shape, reused across calls."""
+    captured CUDA graph, the per-bucket mappings and the tuned launch shape,
+    reused across calls."""
 
     def __init__(self):
         h = _P()
@@ -449,8 +462,9 @@ class Context:
                                                ctypes.c_void_p(s.cuda_stream)))
 
     def autotune(self, grids: list, stream: torch.cuda.Stream | None = None) -> tuple[int, int]:
-        """Time the launch shapes on these grids (their state is left as it
-        was) and keep the fastest; returns (threads, cells_per_item)."""
+        """Time each bucket's mappings and the CTA shape on these grids (their
+        state is left as it was) and keep the fastest; returns (threads,
+        cells_per_item); ``mappings`` has the picked mappings."""
         s = stream if stream is not None else torch.cuda.current_stream()
         arr = self._array(grids)
         _raise(lib().rhd_context_autotune(self._h, arr, len(grids),
@@ -462,6 +476,19 @@ class Context:
         t, c = ctypes.c_int32(), ctypes.c_int32()
         _raise(lib().rhd_context_shape(self._h, ctypes.byref(t), ctypes.byref(c)))
         return t.value, c.value
+
+    def mapping(self, bucket: int) -> tuple[int, int]:
+        """(passes, correction) lanes per cell of bucket ``bucket``."""
+        p, c = ctypes.c_int32(), ctypes.c_int32()
+        _raise(lib().rhd_context_mapping(self._h, bucket, ctypes.byref(p), ctypes.byref(c)))
+        return p.value, c.value
+
+    def set_mapping(self, bucket: int, passes: int, correction: int) -> None:
+        _raise(lib().rhd_context_set_mapping(self._h, bucket, passes, correction))
+
+    @property
+    def mappings(self) -> list[tuple[int, int]]:
+        return [self.mapping(b) for b in range(BATCH_BUCKETS)]
 
 
 class Surrogate:

@@ -126,6 +126,20 @@ def test_batched_entry_points_reject_null_arguments_without_a_device(lib):
     assert lib.rhd_context_create(None) == -1
     t, c = ctypes.c_int32(), ctypes.c_int32()
     assert lib.rhd_context_shape(None, ctypes.byref(t), ctypes.byref(c)) == -1
+    assert lib.rhd_context_mapping(None, 0, ctypes.byref(t), ctypes.byref(c)) == -1
+    assert lib.rhd_context_set_mapping(None, 0, 1, 8) == -1
+
+
+def test_the_binding_lists_the_mappings_the_header_documents():
+    txt = open(os.path.join(ROOT, "include", "rhd.h")).read()
+    assert f"#define RHD_BATCH_BUCKETS {rhd.BATCH_BUCKETS}" in txt
+    doc = re.sub(r"\s+", " ", re.sub(r"\n\s*\*", " ", txt[txt.index("Read or set bucket"):]))
+    for b, (p, c) in enumerate(zip(rhd.PASS_MAPPINGS, rhd.CORRECTION_MAPPINGS)):
+        p_txt = ", ".join(map(str, p[:-1])) + (" or " if len(p) > 1 else "") + str(p[-1])
+        c_txt = ", ".join(map(str, c[:-1])) + (" or " if len(c) > 1 else "") + str(c[-1])
+        passes, corr = doc.split("`correction`")[:2]
+        assert f"bucket {b}: {p_txt}" in passes, (b, p_txt)
+        assert f"bucket {b}: {c_txt}" in corr, (b, c_txt)
 
 
 def test_grid_struct_matches_the_c_layout():

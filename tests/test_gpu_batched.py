@@ -111,6 +111,63 @@ def test_batched_mixed_matches_oracle_and_single_grid():
     one = [run_gpu(w, precision=rhd.MIXED, theta=x["theta"], c_hat=x["c_hat"])
            for w, x in zip(ws, extra)]
     _check_parity(ws, extra, got, one, MIXED_BOUND, DEFAULT_FLOOR, "batched-mixed vs one-grid")
+    same = np.mean([np.array_equal(g[k], o[k]) for g, o in zip(got, one)
+                    for k in ("egas", "erad", "frad", "mom")])
+    print("bit-identical arrays (batched vs one-grid):", same)
+    # at the default mappings (the one-grid call's) the same device functions
+    # take every cell through the same phases
+    assert same == 1.0
+
+
+def _bucket_grids(seed=36):
+    """Two small grids in each bucket (4 and 16, 24 and 32, 40 and 64 groups),
+    moving cells, breakpoints on the group edges, own law and cell count each."""
+    rng = np.random.default_rng(seed)
+    ws = [synth.preset("mixed_128cube_ng16", n_cells=int(rng.integers(60, 200)), seed=seed + G,
+                       n_groups=G) for G in (4, 16, 24, 32, 40, 64)]
+    extra = [dict(theta=1.0, c_hat=w.consts["c_hat"]) for w in ws]
+    return ws, extra
+
+
+def _configs(precision):
+    """Mapping configurations that together take every mapping each bucket
+    offers (the passes', and in the mixed form the correction step's)."""
+    per_bucket = []
+    for b in range(rhd.BATCH_BUCKETS):
+        cs = rhd.CORRECTION_MAPPINGS[b] if precision == rhd.MIXED else rhd.CORRECTION_MAPPINGS[b][:1]
+        per_bucket.append([(p, c) for p in rhd.PASS_MAPPINGS[b] for c in cs])
+    n = max(len(x) for x in per_bucket)
+    return [[x[k % len(x)] for x in per_bucket] for k in range(n)]
+
+
+@pytest.mark.parametrize("precision", [rhd.MIXED, rhd.FP64], ids=["mixed", "fp64"])
+def test_every_mapping_of_every_bucket_matches_the_oracle(precision):
+    ws, extra = _bucket_grids()
+    orc = [run_oracle(w) for w in ws]
+    fp64 = precision == rhd.FP64
+    for cfg in _configs(precision):
+        ctx = rhd.Context()
+        for b, (p, c) in enumerate(cfg):
+            ctx.set_mapping(b, p, c)
+        assert ctx.mappings == cfg
+        got = run_batched(ws, extra, precision, tight=fp64, ctx=ctx,
+                          flags=rhd.FLUX_TEST if fp64 else 0)
+        _check_parity(ws, extra, got, orc, FP64_TOL if fp64 else MIXED_BOUND,
+                      FLOOR if fp64 else DEFAULT_FLOOR, f"mapping {cfg}")
+
+
+def test_set_mapping_rejects_what_a_bucket_does_not_offer():
+    ctx = rhd.Context()
+    default = [(1, 8), (1, 16), (32, 32)]
+    assert ctx.mappings == default
+    for b, p, c in [(0, 16, 8), (0, 1, 16), (1, 2, 8), (1, 1, 32), (2, 8, 32), (2, 1, 8),
+                    (3, 1, 8), (-1, 1, 8)]:
+        with pytest.raises(rhd.RhdError) as e:
+            ctx.set_mapping(b, p, c)
+        assert e.value.code == -1
+    with pytest.raises(rhd.RhdError):
+        ctx.mapping(3)
+    assert ctx.mappings == default
 
 
 def test_graph_replay_is_bit_exact_and_recaptures_on_a_new_batch():
@@ -127,8 +184,10 @@ def test_graph_replay_is_bit_exact_and_recaptures_on_a_new_batch():
             np.testing.assert_array_equal(a[k], b[k])
 
 
-def test_autotune_leaves_the_state_unchanged_and_keeps_a_candidate():
+def test_autotune_leaves_the_state_unchanged_and_keeps_valid_choices():
     ws, extra = _grids(n_grids=4, seed=34, max_side=12)
+    bws, bex = _bucket_grids(seed=37)
+    ws, extra = ws + bws, extra + bex  # every bucket has grids
     ctx = rhd.Context()
     assert ctx.shape == (128, 512)
     states = _to_dev(ws)
@@ -137,15 +196,25 @@ def test_autotune_leaves_the_state_unchanged_and_keeps_a_candidate():
     threads, cpi = ctx.autotune(specs)
     torch.cuda.synchronize()
     assert threads in (64, 128, 256) and cpi in (threads, 4 * threads, 16 * threads)
+    picked = ctx.mappings
+    print("autotuned mappings", picked, "shape", (threads, cpi))
+    for b, (p, c) in enumerate(picked):
+        assert p in rhd.PASS_MAPPINGS[b] and c in rhd.CORRECTION_MAPPINGS[b]
     for b, s in zip(before, states):
         a = synth.to_numpy(s)
         for k in ("egas", "erad", "frad", "mom"):
             np.testing.assert_array_equal(a[k], b[k])
     tuned = run_batched(ws, extra, rhd.MIXED, ctx=ctx)
-    plain = run_batched(ws, extra, rhd.MIXED)
+    # the CTA shape moves cells between threads, never the arithmetic of a cell
+    same = rhd.Context()
+    for b, (p, c) in enumerate(picked):
+        same.set_mapping(b, p, c)
+    plain = run_batched(ws, extra, rhd.MIXED, ctx=same)
     for a, b in zip(tuned, plain):
         for k in ("egas", "erad", "frad", "mom", "status"):
             np.testing.assert_array_equal(a[k], b[k])
+    orc = [run_oracle(w, theta=x["theta"], c_hat=x["c_hat"]) for w, x in zip(ws, extra)]
+    _check_parity(ws, extra, tuned, orc, MIXED_BOUND, DEFAULT_FLOOR, "autotuned vs oracle")
 
 
 def test_empty_grids_invalid_cells_and_errors():
