@@ -401,7 +401,8 @@ int rhd_profile_stop(int32_t *launches, double *total_ms);
 #define RHD_KERNEL_CORRECTION 1 /* its correction step (FP64 residual, FP32 Newton step) */
 #define RHD_KERNEL_FP64 2       /* the FP64 passes (the FP64 form; the mixed form's fallback) */
 #define RHD_KERNEL_INFERENCE 3  /* the learned warm start's fused inference */
-#define RHD_KERNELS 4
+#define RHD_KERNEL_REFINE 4     /* the correction's first step (float-float residual) */
+#define RHD_KERNELS 5
 int rhd_profile_kernel(int32_t kind, int32_t *launches, double *total_ms);
 
 /* ---- Event counts ------------------------------------------------------------
@@ -427,7 +428,9 @@ int rhd_profile_kernel(int32_t kind, int32_t *launches, double *total_ms);
 #define RHD_EV_OUTER64 10    /* FP64 outer passes */
 #define RHD_EV_FLUXNEWTON 11 /* group flux updates solved by Newton steps (slow cells) */
 #define RHD_EV_INFER 12      /* cells through the warm start's inference */
-#define RHD_EVENTS 13
+#define RHD_EV_RESIDDF 13    /* float-float evaluations of the coupled residual */
+#define RHD_EV_STEPDF 14     /* Newton steps taken from them */
+#define RHD_EVENTS 15
 int rhd_events_start(void);
 int rhd_events_stop(uint64_t *counts);
 

@@ -18,6 +18,7 @@
 #include "rhd_warp.cuh"
 #include "rhd_warp32.cuh"
 #include "rhd_correct.cuh"
+#include "rhd_refine.cuh"
 
 namespace rhd {
 namespace {
@@ -381,7 +382,17 @@ void launch_correct_k(const KParams &kp, const WarmOut &wo, int sms, cudaStream_
   const size_t smem = correct_smem_bytes(kp.G, GPL, threads);
   if (smem > 48 * 1024) allow_smem<correct_warp_kernel<L, GPL>>(smem);
   const int b = persistent_blocks(correct_warp_kernel<L, GPL>, smem, sms, kp.n * L, threads);
-  correct_warp_kernel<L, GPL><<<b, threads, smem, st>>>(kp, wo, CorrOut{wo.ur, wo.uf, wo.done});
+  correct_warp_kernel<L, GPL><<<b, threads, smem, st>>>(kp, wo,
+                                                        CorrOut{wo.ur, wo.uf, wo.done, 1});
+}
+
+template <int L, int GPL>
+void launch_refine_k(const KParams &kp, const WarmOut &wo, int sms, cudaStream_t st) {
+  const int threads = 128;
+  const size_t smem = refine_smem_bytes(kp.G, GPL, threads);
+  if (smem > 48 * 1024) allow_smem<refine_warp_kernel<L, GPL>>(smem);
+  const int b = persistent_blocks(refine_warp_kernel<L, GPL>, smem, sms, kp.n * L, threads);
+  refine_warp_kernel<L, GPL><<<b, threads, smem, st>>>(kp, wo, CorrOut{wo.ur, wo.uf, wo.done, 1});
 }
 
 // The correction step after the FP32 passes (rhd_correct.cuh): L lanes per
@@ -391,6 +402,12 @@ WarmStart launch_correct(const KParams &kp, const WarmOut &wo, const WarmStart &
                          cudaStream_t st) {
   WarmStart w = wi;
   if (kp.G > 128) return w;
+  timed_launch(RHD_KERNEL_REFINE, st, [&] {
+    if (kp.G <= 16) launch_refine_k<8, 2>(kp, wo, sms, st);
+    else if (kp.G <= 32) launch_refine_k<16, 2>(kp, wo, sms, st);
+    else if (kp.G <= 64) launch_refine_k<32, 2>(kp, wo, sms, st);
+    else launch_refine_k<32, 4>(kp, wo, sms, st);
+  });
   timed_launch(RHD_KERNEL_CORRECTION, st, [&] {
     if (kp.G <= 16) launch_correct_k<8, 2>(kp, wo, sms, st);
     else if (kp.G <= 32) launch_correct_k<16, 2>(kp, wo, sms, st);
@@ -704,7 +721,7 @@ int ctx_reserve(rhd_context *c, int n_grids) {
       cudaMalloc(&c->d_warm, sizeof(WarmOut) * cap) != cudaSuccess ||
       cudaMalloc(&c->d_off, noff) != cudaSuccess || cudaMalloc(&c->d_sel, nsel) != cudaSuccess ||
       cudaMalloc(&c->d_tables, sizeof(double) * kTableWords * cap) != cudaSuccess ||
-      cudaMalloc(&c->d_head, 3 * kBuckets * sizeof(unsigned long long)) != cudaSuccess) {
+      cudaMalloc(&c->d_head, 4 * kBuckets * sizeof(unsigned long long)) != cudaSuccess) {
     ctx_free(c);
     return RHD_ENOMEM;
   }
@@ -811,17 +828,23 @@ void launch_passes(int phase, int b, int m, int threads, int sms, int64_t items,
 }
 
 template <int L, int GPL>
-void launch_corr(int sms, int64_t items, const BatchArgs &A, cudaStream_t s) {
-  launch_queue(batched_correct_kernel<L, GPL>, 128, batch_correct_smem(GPL), sms, items, A, s);
+void launch_corr(bool refine, int sms, int64_t items, const BatchArgs &A, cudaStream_t s) {
+  if (refine)
+    launch_queue(batched_refine_kernel<L, GPL>, 128, batch_refine_smem(GPL), sms, items, A, s);
+  else
+    launch_queue(batched_correct_kernel<L, GPL>, 128, batch_correct_smem(GPL), sms, items, A, s);
 }
 
-void launch_correction(int b, int m, int sms, int64_t items, const BatchArgs &A, cudaStream_t s) {
+// Bucket b's correction with mapping m: its float-float first step (refine)
+// or its FP64 steps.
+void launch_correction(int b, int m, bool refine, int sms, int64_t items, const BatchArgs &A,
+                       cudaStream_t s) {
   switch (100 * b + m) {
-    case 8: launch_corr<8, 2>(sms, items, A, s); break;
-    case 108: launch_corr<8, 4>(sms, items, A, s); break;
-    case 116: launch_corr<16, 2>(sms, items, A, s); break;
-    case 216: launch_corr<16, 4>(sms, items, A, s); break;
-    case 232: launch_corr<32, 2>(sms, items, A, s); break;
+    case 8: launch_corr<8, 2>(refine, sms, items, A, s); break;
+    case 108: launch_corr<8, 4>(refine, sms, items, A, s); break;
+    case 116: launch_corr<16, 2>(refine, sms, items, A, s); break;
+    case 216: launch_corr<16, 4>(refine, sms, items, A, s); break;
+    case 232: launch_corr<32, 2>(refine, sms, items, A, s); break;
   }
 }
 
@@ -838,6 +861,15 @@ cudaError_t batch_prepare() {
     if ((e = allow_smem<batched_correct_kernel<16, 2>>(batch_correct_smem(2))) != cudaSuccess) return e;
     if ((e = allow_smem<batched_correct_kernel<32, 2>>(batch_correct_smem(2))) != cudaSuccess) return e;
   }
+  if (batch_refine_smem(4) > 48 * 1024) {
+    if ((e = allow_smem<batched_refine_kernel<8, 4>>(batch_refine_smem(4))) != cudaSuccess) return e;
+    if ((e = allow_smem<batched_refine_kernel<16, 4>>(batch_refine_smem(4))) != cudaSuccess) return e;
+  }
+  if (batch_refine_smem(2) > 48 * 1024) {
+    if ((e = allow_smem<batched_refine_kernel<8, 2>>(batch_refine_smem(2))) != cudaSuccess) return e;
+    if ((e = allow_smem<batched_refine_kernel<16, 2>>(batch_refine_smem(2))) != cudaSuccess) return e;
+    if ((e = allow_smem<batched_refine_kernel<32, 2>>(batch_refine_smem(2))) != cudaSuccess) return e;
+  }
   return e;
 }
 
@@ -853,7 +885,7 @@ cudaError_t enqueue_batch(rhd_context *c, int prec, int n_grids, int threads, in
   cudaMemcpyAsync(c->d_off, c->h_off, sizeof(int64_t) * 2 * kBuckets * (cap + 1),
                   cudaMemcpyHostToDevice, st);
   cudaMemcpyAsync(c->d_sel, c->h_sel, sizeof(int) * kBuckets * cap, cudaMemcpyHostToDevice, st);
-  cudaMemsetAsync(c->d_head, 0, 3 * kBuckets * sizeof(unsigned long long), st);
+  cudaMemsetAsync(c->d_head, 0, 4 * kBuckets * sizeof(unsigned long long), st);
   tables_kernel<<<n_grids, 128, table_bytes(kMaxGB) + 64, st>>>(c->d_grids, c->d_tables,
                                                                    kTableWords);
   bool forked = false;
@@ -872,15 +904,17 @@ cudaError_t enqueue_batch(rhd_context *c, int prec, int n_grids, int threads, in
                 pm == 1 ? cpi : kCpiWarp, nullptr};
     const int th = pm == 1 ? threads : 128;
     if (mixed) {
-      A.head = c->d_head + 3 * b;
+      A.head = c->d_head + 4 * b;
       launch_passes(0, b, pm, th, sms, items[2 * b], A, s);
       BatchArgs Ac = A;
       Ac.item_off = off_of(c->d_off, c, 2 * b + 1);
       Ac.cpi = kCpiCorr;
-      Ac.head = c->d_head + 3 * b + 1;
-      launch_correction(b, c->corr_map[b], sms, items[2 * b + 1], Ac, s);
+      Ac.head = c->d_head + 4 * b + 1;
+      launch_correction(b, c->corr_map[b], true, sms, items[2 * b + 1], Ac, s);
+      Ac.head = c->d_head + 4 * b + 2;
+      launch_correction(b, c->corr_map[b], false, sms, items[2 * b + 1], Ac, s);
     }
-    A.head = c->d_head + 3 * b + 2;
+    A.head = c->d_head + 4 * b + 3;
     launch_passes(2, b, pm, th, sms, items[2 * b], A, s);
     if (s != st) {
       cudaEventRecord(c->join[b - 1], s);

@@ -13,14 +13,16 @@
 // lanes per cell with GPL groups each -- for the passes and for the
 // correction step, chosen per bucket (rhd_context_autotune times them).  The
 // FP64 form is one launch of FP64 passes per bucket; the mixed form runs a
-// grid's three phases as the one-grid call runs them (FP32 passes, the
-// correction step, FP64 passes for the cells it did not finish), each phase
-// one launch per bucket, handing over through the grid's own workspace.
+// grid's phases as the one-grid call runs them (FP32 passes, the correction
+// step's float-float first step and its FP64 steps, FP64 passes for the cells
+// it did not finish), each phase one launch per bucket, handing over through
+// the grid's own workspace.
 // Per cell the algorithm is the one-grid call's (the same device functions).
 #pragma once
 #include "rhd_correct.cuh"
 #include "rhd_fp64.cuh"
 #include "rhd_mixed.cuh"
+#include "rhd_refine.cuh"
 #include "rhd_warp.cuh"
 #include "rhd_warp32.cuh"
 
@@ -178,9 +180,40 @@ __global__ void __launch_bounds__(128) batched_correct_kernel(const BatchArgs A)
   CCell<GPL> C;
   for_items(A, sm, [&](const KParams &P, const GroupTable &tab, int j, int64_t c0, int64_t c1) {
     const WarmOut &w = A.warm[j];
-    const CorrOut U{w.ur, w.uf, w.done};
+    const CorrOut U{w.ur, w.uf, w.done, 1};
     for (int64_t i = c0 + wid * CPW + seg; i < c1; i += nw * CPW)
       correct_cell<L, GPL>(P, tab, w, U, gb, i, lane, C);
+  });
+}
+
+// The correction's first step with a float-float residual (rhd_refine.cuh),
+// on the correction's mapping and items; the float-float group table after
+// the FP64 one, rebuilt when the CTA's grid changes.
+__host__ __device__ __forceinline__ size_t batch_refine_smem(int GPL) {
+  return kBatchTableBytes + refine_df_bytes(kMaxGB) + sizeof(float) * 20 * GPL * 128;
+}
+
+template <int L, int GPL>
+__global__ void __launch_bounds__(128) batched_refine_kernel(const BatchArgs A) {
+  extern __shared__ double sm[];
+  load_planck(sm);
+  const int lane = threadIdx.x & 31, seg = lane / L;
+  constexpr int CPW = 32 / L;
+  const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  float2 *dfs = reinterpret_cast<float2 *>(batch_blocks(sm));
+  float *gb = warp_blocks<GPL>(reinterpret_cast<float *>(dfs + 5 * kMaxGB), wid);
+  int cur = -1;
+  DfTable dt;
+  for_items(A, sm, [&](const KParams &P, const GroupTable &tab, int j, int64_t c0, int64_t c1) {
+    if (j != cur) {  // every thread of the CTA takes the same branch
+      __syncthreads();
+      dt = build_df_table(tab, dfs, P.G);
+      cur = j;
+    }
+    const WarmOut &w = A.warm[j];
+    const CorrOut U{w.ur, w.uf, w.done, 1};
+    for (int64_t i = c0 + wid * CPW + seg; i < c1; i += nw * CPW)
+      refine_cell<L, GPL>(P, tab, dt, w, U, gb, i, lane);
   });
 }
 

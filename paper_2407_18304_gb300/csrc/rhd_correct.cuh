@@ -40,6 +40,8 @@ struct CorrOut {
   float *ur;      // [G][n]
   float *uf;      // [3][G][n]
   uint8_t *done;  // [n]
+  int from_step;  // 1: ur, uf already hold a step from the FP32 iterate (rhd_refine.cuh),
+                  // and the correction starts from the FP32 iterate plus that step
 };
 
 // The closure in units with c = 1 (E, F / c, v / c): v.P, M = d(v.P)/dF at
@@ -337,11 +339,18 @@ __device__ __forceinline__ void correct_cell(const KParams &P, const GroupTable 
   const float imE = 1.0f / frexp_f(Et, shE);
   const float imEc = imE * (float)P.ic;
   const double fs = c * Et;
-  // the iterate in FP64
+  // the iterate in FP64 (the FP32 iterate, plus the refinement step when it ran)
 #pragma unroll
   for (int j = 0; j < GPL; ++j) {
-    C.R[j] = f2d(C.rw[j]) * Et;
-    for (int d = 0; d < 3; ++d) C.F[j][d] = f2d(C.fw[j][d]) * fs;
+    if (U.from_step && l + L * j < G) {
+      const int64_t ow = (int64_t)(l + L * j) * n + i;
+      C.R[j] = fma(f2d(C.rw[j]), Et, f2d(U.ur[ow]) * Et);
+      for (int d = 0; d < 3; ++d)
+        C.F[j][d] = fma(f2d(C.fw[j][d]), fs, f2d(U.uf[(int64_t)d * G * n + ow]) * fs);
+    } else {
+      C.R[j] = f2d(C.rw[j]) * Et;
+      for (int d = 0; d < 3; ++d) C.F[j][d] = f2d(C.fw[j][d]) * fs;
+    }
   }
   double Eint = Eint0;
   const double irho = 1.0 / rho;
@@ -609,12 +618,15 @@ __device__ __forceinline__ void correct_cell(const KParams &P, const GroupTable 
     return;
   }
   // ---- not finished: the FP64 passes start from W + U (the FP32 iterate
-  // and the steps taken here; none when no step was taken), from F^t
+  // and the steps taken here and by the refinement; none when no step was
+  // taken), from F^t
+  const bool moved = steps || U.from_step;
 #pragma unroll
   for (int j = 0; j < GPL; ++j) {
     const int g = l + L * j;
     if (g >= G) continue;
     for (int d = 0; d < 3; ++d) P.frad[d][(int64_t)g * P.gs + i] = C.ft[j][d];
+    if (!steps && U.from_step) continue;  // U holds the refinement's step already
     const int64_t o = (int64_t)g * n + i;
     U.ur[o] = steps ? scaled_f(C.R[j] - f2d(C.rw[j]) * Et, shE) * imE : 0.0f;
     for (int d = 0; d < 3; ++d)
@@ -622,7 +634,7 @@ __device__ __forceinline__ void correct_cell(const KParams &P, const GroupTable 
           steps ? scaled_f(C.F[j][d] - f2d(C.fw[j][d]) * fs, shE) * imEc : 0.0f;
   }
   double dF[3] = {0.0, 0.0, 0.0};
-  if (steps) {
+  if (moved) {
 #pragma unroll
     for (int j = 0; j < GPL; ++j)
       if (l + L * j < G)
@@ -630,7 +642,7 @@ __device__ __forceinline__ void correct_cell(const KParams &P, const GroupTable 
     for (int d = 0; d < 3; ++d) dF[d] = seg_sum<L>(dF[d], mask);
   }
   if (l == 0) {
-    if (steps) {
+    if (moved) {
       W.eint[i] = Eint;
       for (int d = 0; d < 3; ++d) W.mom[(int64_t)d * n + i] = m0[d] - dF[d] * P.icc;
       W.nit[i] = (uint8_t)(nit > 255 ? 255 : nit);

@@ -659,10 +659,11 @@ class Surrogate:
         del keep
 
 
-KERNEL_FP32, KERNEL_CORRECTION, KERNEL_FP64, KERNEL_INFERENCE = 0, 1, 2, 3
-KERNEL_NAMES = ("fp32_passes", "correction", "fp64_passes", "inference")
+KERNEL_FP32, KERNEL_CORRECTION, KERNEL_FP64, KERNEL_INFERENCE, KERNEL_REFINE = 0, 1, 2, 3, 4
+KERNEL_NAMES = ("fp32_passes", "correction", "fp64_passes", "inference", "refine")
 EVENT_NAMES = ("cells32", "eval32", "outer32", "cellsc", "resid64", "step32", "finish64",
-               "cells64", "eval64", "cached64", "outer64", "fluxnewton", "infer")
+               "cells64", "eval64", "cached64", "outer64", "fluxnewton", "infer", "residdf",
+               "stepdf")
 
 
 def profile_start() -> None:
