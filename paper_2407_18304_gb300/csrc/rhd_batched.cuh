@@ -190,18 +190,23 @@ __global__ void __launch_bounds__(128) batched_correct_kernel(const BatchArgs A)
 // on the correction's mapping and items; the float-float group table after
 // the FP64 one, rebuilt when the CTA's grid changes.
 __host__ __device__ __forceinline__ size_t batch_refine_smem(int GPL) {
-  return kBatchTableBytes + refine_df_bytes(kMaxGB) + sizeof(float) * 20 * GPL * 128;
+  return kBatchTableBytes + refine_planck_bytes() + refine_df_bytes(kMaxGB) +
+         sizeof(float) * 20 * GPL * 128;
 }
 
 template <int L, int GPL>
 __global__ void __launch_bounds__(128) batched_refine_kernel(const BatchArgs A) {
   extern __shared__ double sm[];
   load_planck(sm);
+  __syncthreads();
   const int lane = threadIdx.x & 31, seg = lane / L;
   constexpr int CPW = 32 / L;
   const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  float2 *dfs = reinterpret_cast<float2 *>(batch_blocks(sm));
-  float *gb = warp_blocks<GPL>(reinterpret_cast<float *>(dfs + 5 * kMaxGB), wid);
+  char *base = reinterpret_cast<char *>(batch_blocks(sm));
+  // visible after the first barrier of for_items
+  const DfPlanck pl = build_df_planck(sm, reinterpret_cast<float *>(base));
+  float2 *dfs = reinterpret_cast<float2 *>(base + refine_planck_bytes());
+  float *gb = warp_blocks<GPL>(reinterpret_cast<float *>(dfs + 6 * kMaxGB + 1), wid);
   int cur = -1;
   DfTable dt;
   for_items(A, sm, [&](const KParams &P, const GroupTable &tab, int j, int64_t c0, int64_t c1) {
@@ -213,7 +218,7 @@ __global__ void __launch_bounds__(128) batched_refine_kernel(const BatchArgs A) 
     const WarmOut &w = A.warm[j];
     const CorrOut U{w.ur, w.uf, w.done, 1};
     for (int64_t i = c0 + wid * CPW + seg; i < c1; i += nw * CPW)
-      refine_cell<L, GPL>(P, tab, dt, w, U, gb, i, lane);
+      refine_cell<L, GPL>(P, tab, dt, pl, w, U, gb, i, lane);
   });
 }
 

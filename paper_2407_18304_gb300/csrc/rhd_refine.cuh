@@ -32,11 +32,21 @@ constexpr dflt kThirdDF = {0x1.555556p-2f, -0x1.555556p-27f};  // 1/3
 // hi/lo pairs), built in shared memory after the FP64 table.
 struct DfTable {
   const float2 *kbar, *ikbar, *alpha, *rm, *rp;
+  const float2 *xe;  // [G + 1] h nu_e / k_B (x_e = xe / T)
 };
 
-__host__ __device__ __forceinline__ size_t refine_df_bytes(int G) { return sizeof(float2) * 5 * G; }
+__host__ __device__ __forceinline__ size_t refine_df_bytes(int G) {
+  return sizeof(float2) * (6 * G + 1);
+}
+// Shared memory of the refine kernel: the FP64 tables (build_table), the
+// float-float Planck polynomials, the float-float group table, then the group
+// blocks (20 floats per group slot per thread).
+__host__ __device__ __forceinline__ size_t refine_planck_bytes() {
+  return ((sizeof(float) * 2 * (8 + 1) * planck_table::kSeg +
+           sizeof(float) * (planck_table::kDeg - 8 + 2) * planck_table::kSeg) + 15) & ~(size_t)15;
+}
 __host__ __device__ __forceinline__ size_t refine_smem_bytes(int G, int GPL, int threads) {
-  return ((table_bytes(G) + 15) & ~(size_t)15) + refine_df_bytes(G) +
+  return ((table_bytes(G) + 15) & ~(size_t)15) + refine_planck_bytes() + refine_df_bytes(G) +
          sizeof(float) * 20 * GPL * threads;
 }
 
@@ -45,7 +55,11 @@ __device__ __forceinline__ dflt df_of(float2 v) { return dflt{v.x, v.y}; }
 // Build the float-float table of G groups at d (all threads of the CTA; ends
 // with __syncthreads()).
 __device__ __forceinline__ DfTable build_df_table(const GroupTable &tab, float2 *d, int G) {
-  for (int t = threadIdx.x; t < G; t += blockDim.x) {
+  for (int t = threadIdx.x; t <= G; t += blockDim.x) {
+    const dflt xe = isinf(tab.xe[t]) ? dflt{__int_as_float(0x7F800000), 0.0f}
+                                     : df_from_double(tab.xe[t], 0);
+    d[5 * G + t] = make_float2(xe.hi, xe.lo);
+    if (t == G) continue;
     const double v[5] = {tab.kbar[t], tab.ikbar[t], tab.alpha[t], tab.rm[t], tab.rp[t]};
     for (int k = 0; k < 5; ++k) {
       const dflt x = df_from_double(v[k], 0);
@@ -53,7 +67,110 @@ __device__ __forceinline__ DfTable build_df_table(const GroupTable &tab, float2 
     }
   }
   __syncthreads();
-  return DfTable{d, d + G, d + 2 * G, d + 3 * G, d + 4 * G};
+  return DfTable{d, d + G, d + 2 * G, d + 3 * G, d + 4 * G, d + 5 * G};
+}
+
+// ---- Planck edge terms in float-float ---------------------------------------
+//
+// The same functions as edge_tab (P(x) below x = 2, else Q(x) = 1 - P(x);
+// D(x) = (15/pi^4) x^4/(e^x - 1); x dD/dx), from the same planck_table.h
+// polynomials: coefficients 0..8 of each segment in float-float, 9..13 (below
+// 3e-7 of the leading one) in FP32, centres and inverse half-widths exact in
+// FP32.  e^x enters through one exponential of s = x (x < 2: x/(e^x - 1) from
+// expm1(x)) or s = -x (x >= 2: e^-x and x e^-x/(1 - e^-x)): s = k ln 2 + r with
+// ln 2 split in three (Cody & Waite: k ln2_a and k ln2_b exact), expm1(r) from
+// its Taylor series to r^13/13! (|r| <= ln2/2: the next term is below 4e-18).
+// Beyond x = 80, e^-x is below FP32's normal range and every edge term is
+// taken as 0 (Q(80) ~ 1e-30).
+constexpr int kDfDeg = 8;  // float-float coefficients 0..kDfDeg
+constexpr int kDfPlanckFloats =
+    2 * (kDfDeg + 1) * planck_table::kSeg + (planck_table::kDeg - kDfDeg + 2) * planck_table::kSeg;
+constexpr dflt kPlanckNormDF = {0x1.3b5ef8p-3f, 0x1.ab60cep-30f};  // 15/pi^4
+constexpr float kLn2a = 0x1.62ep-1f, kLn2b = 0x1.0bep-15f, kLn2c = 0x1.be8e7cp-27f;
+constexpr float kLog2e = 0x1.715476p+0f;
+struct DfPlanck {
+  const float2 *c;  // [kDfDeg + 1][kSeg]
+  const float *ct;  // [kDeg - kDfDeg][kSeg], coefficients kDfDeg + 1 .. kDeg
+  const float *cen, *ih;
+};
+
+// Convert the CTA's FP64 polynomial table (pc, planck_table.h layout) to dst
+// (all threads; the caller synchronises).
+__device__ __forceinline__ DfPlanck build_df_planck(const double *pc, float *dst) {
+  using namespace planck_table;
+  float2 *c = reinterpret_cast<float2 *>(dst);
+  float *ct = dst + 2 * (kDfDeg + 1) * kSeg, *cen = ct + (kDeg - kDfDeg) * kSeg, *ih = cen + kSeg;
+  for (int t = threadIdx.x; t < (kDeg + 1) * kSeg; t += blockDim.x) {
+    const int k = t / kSeg;
+    if (k <= kDfDeg) {
+      const dflt v = df_from_double(pc[t], 0);
+      c[t] = make_float2(v.hi, v.lo);
+    } else {
+      ct[t - (kDfDeg + 1) * kSeg] = (float)pc[t];
+    }
+  }
+  for (int t = threadIdx.x; t < kSeg; t += blockDim.x) {
+    cen[t] = (float)pc[(kDeg + 1) * kSeg + t];  // exact: a few significant bits
+    ih[t] = (float)pc[(kDeg + 2) * kSeg + t];   // powers of two
+  }
+  return DfPlanck{c, ct, cen, ih};
+}
+
+// expm1(r) for |r| <= ln2/2: r + r^2 S(r), S = sum_k r^(k-2)/k!, the terms
+// k >= 8 (below 5e-8 of S) in FP32, k = 2..7 with float-float coefficients.
+__device__ __forceinline__ dflt expm1_small_df(dflt r) {
+  float t = 0x1.612462p-33f;             // 1/13!
+  t = fmaf(t, r.hi, 0x1.1eed8ep-29f);    // 1/12!
+  t = fmaf(t, r.hi, 0x1.ae6456p-26f);    // 1/11!
+  t = fmaf(t, r.hi, 0x1.27e4fcp-22f);    // 1/10!
+  t = fmaf(t, r.hi, 0x1.71de3ap-19f);    // 1/9!
+  t = fmaf(t, r.hi, 0x1.a01a02p-16f);    // 1/8!
+  dflt S = {t, 0.0f};
+  S = S * r + dflt{0x1.a01a02p-13f, -0x1.7f97fap-39f};   // 1/7!
+  S = S * r + dflt{0x1.6c16c2p-10f, -0x1.27d27ep-35f};   // 1/6!
+  S = S * r + dflt{0x1.111112p-7f, -0x1.dddddep-32f};    // 1/5!
+  S = S * r + dflt{0x1.555556p-5f, -0x1.555556p-30f};    // 1/4!
+  S = S * r + dflt{0x1.555556p-3f, -0x1.555556p-28f};    // 1/3!
+  S = S * r + dflt{0x1p-1f, 0.0f};                       // 1/2!
+  return r + (r * r) * S;
+}
+
+// Edge values at x (float-float): pq = P(x) (low, x < 2) or Q(x), d = D(x),
+// ed = x dD/dx (FP32, for the Jacobian).
+__device__ __forceinline__ void edge_df(const DfPlanck &T, dflt x, dflt &pq, dflt &d, float &ed,
+                                        bool &low) {
+  using namespace planck_table;
+  low = !(x.hi > 0.0f);
+  if (low || !(x.hi < 80.0f)) {
+    pq = d = dflt{0.0f, 0.0f};
+    ed = 0.0f;
+    return;
+  }
+  low = x.hi < 2.0f;
+  const dflt s = low ? x : -x;
+  const float k = rintf(s.hi * kLog2e);
+  const dflt r = ((s - k * kLn2a) - k * kLn2b) - two_prod(k, kLn2c);
+  const dflt em = expm1_small_df(r);
+  const float p2 = __int_as_float((127 + (int)k) << 23);  // 2^k, k in [-116, 3]
+  const dflt ex = df_scale(em + 1.0f, p2);                  // e^s (e^-x on the Wien side)
+  const dflt e1 = df_scale(em, p2) + (p2 - 1.0f);           // expm1(s)
+  // x/(e^x - 1): x / expm1(x) below 2, x e^-x / (1 - e^-x) above
+  const dflt B = (low ? x : x * ex) / (low ? e1 : 1.0f - ex);
+  const int bits = __float_as_int(x.hi);
+  const int e = ((bits >> 23) & 0xFF) - 127;
+  int sg = 1 + (e - kEMin) * kSub + ((bits >> 21) & 3);
+  sg = e < kEMin ? 0 : (e > kEMax ? kSeg - 1 : sg);
+  const dflt u = df_scale(x - T.cen[sg], T.ih[sg]);
+  float pt = T.ct[(kDeg - kDfDeg - 1) * kSeg + sg];
+#pragma unroll
+  for (int c = kDeg - 1; c > kDfDeg; --c) pt = fmaf(pt, u.hi, T.ct[(c - kDfDeg - 1) * kSeg + sg]);
+  dflt p = {pt, 0.0f};
+#pragma unroll
+  for (int c = kDfDeg; c >= 0; --c) p = p * u + df_of(T.c[c * kSeg + sg]);
+  const dflt kx3 = kPlanckNormDF * (x * x * x);
+  pq = kx3 * (low ? p : p * ex);
+  d = kx3 * B;
+  ed = d.hi * (4.0f - B.hi - x.hi);
 }
 
 template <int L>
@@ -76,8 +193,9 @@ __device__ __forceinline__ dflt band_df(dflt pqL, bool lowL, dflt pqU, bool lowU
 // The refinement step of cell i with L lanes (the layout of correct_cell).
 template <int L, int GPL>
 __device__ __forceinline__ void refine_cell(const KParams &P, const GroupTable &tab,
-                                            const DfTable &dt, const WarmOut &W, const CorrOut &U,
-                                            float *gb, int64_t i, int lane) {
+                                            const DfTable &dt, const DfPlanck &pl,
+                                            const WarmOut &W, const CorrOut &U, float *gb,
+                                            int64_t i, int lane) {
   constexpr int NE = GPL + 1;
   const int seg = lane / L, l = lane % L, lane0 = seg * L;
   const unsigned mask = L == 32 ? 0xffffffffu : (((1u << L) - 1u) << lane0);
@@ -137,7 +255,8 @@ __device__ __forceinline__ void refine_cell(const KParams &P, const GroupTable &
     frexp_f(c * Et, shF);
     frexp_f(rho * c, shV);
     // 1 / mantissa of each, in float-float
-    const dflt imE = df_rcp(df_from_double(Et, shE)), imF = df_rcp(df_from_double(c * Et, shF)),
+    const dflt mEd = df_from_double(Et, shE);
+    const dflt imE = df_rcp(mEd), imF = df_rcp(df_from_double(c * Et, shF)),
                imV = df_rcp(df_from_double(rho * c, shV));
     // the iterate's momentum (eq. vupdate) from its fluxes, in units of rho c
     dflt e0[GPL], ftd[GPL][3], sdf[3] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
@@ -153,56 +272,41 @@ __device__ __forceinline__ void refine_cell(const KParams &P, const GroupTable &
     }
     sr = seg_sum_df<L>(sr, mask);
     for (int d = 0; d < 3; ++d) sdf[d] = seg_sum_df<L>(sdf[d], mask);
-    const dflt mu = df_from_double(Et / rho * P.icc, 0);  // E_tot / (rho c c_hat)
+    const dflt mu = mEd / df_from_double(rho * c * P.c_hat, shE);  // E_tot / (rho c c_hat)
     dflt be[3], dbe[3], b0[3];
     for (int d = 0; d < 3; ++d) {
       b0[d] = df_from_double(m0[d], shV) * imV;
       dbe[d] = -(mu * sdf[d]);
       be[d] = b0[d] + dbe[d];
     }
-    const dflt kE = df_from_double(rho * c * c / Et, 0);  // rho c^2 / E_tot
+    const dflt kE = df_from_double(rho * c * c, shE) * imE;  // rho c^2 / E_tot
     // F_G = E_int - E_int^t + (E_kin - E_kin^t) + (c/c_hat) sum_g R_g: the
     // kinetic energy enters through its change, (1/2) rho c^2 dbeta.(beta + beta^t),
     // so a cell whose gas energy is mostly kinetic loses nothing to cancellation
     const dflt dke = dbe[0] * (be[0] + b0[0]) + dbe[1] * (be[1] + b0[1]) + dbe[2] * (be[2] + b0[2]);
     const dflt FG = df_from_double(Eint - eint0, shE) * imE + df_scale(kE * dke, 0.5f) +
                     df_from_double(P.cr, 0) * sr;
-    // T, the opacity scale and the edges (FP64 Planck terms)
-    const double irc = 1.0 / (rho * P.c_v);
-    const double T = Eint * irc;
+    // T, the opacity scale and the edge terms, all in float-float
     double cs = rho * k0;
-    if (P.temp_exp != 0.0) cs *= pow(T / P.T_ref, P.temp_exp);
+    if (P.temp_exp != 0.0) cs *= pow(Eint / (rho * P.c_v * P.T_ref), P.temp_exp);
     const dflt tcs = df_from_double(tdt * cs, 0), its = df_rcp(tcs);
     int et = 0;
     const float mt = tdt * cs > 0.0 ? frexp_f(tdt * cs, et) : 0.0f;
-    const double invT = 1.0 / T;
-    const dflt aT4 = df_from_double(P.a_rad * T * T * T * T, shE) * imE;
-    double pqE[NE], dE_[NE], eE[NE];
+    const dflt T = df_from_double(Eint, 0) / df_from_double(rho * P.c_v, 0);
+    const dflt invT = df_rcp(T);
+    // a_R T^4 / E_tot as (T 2^-eT)^4 (a_R 2^(4 eT - shE)) / mE: both factors of
+    // order one, so neither part of a_R's float-float leaves FP32's range
+    const int eT = df_exponent(T.hi);
+    const dflt Tm = df_scale(T, __int_as_float((127 - eT) << 23)), T2 = Tm * Tm;
+    const dflt aT4 = (T2 * T2) * (df_from_double(P.a_rad, shE - 4 * eT) * imE);
+    dflt pqD[NE], dD_[NE];
+    float eF[NE];
     bool lowE[NE];
 #pragma unroll
     for (int jj = 0; jj < NE; ++jj) {
       const int e = l + L * jj;
-      if (jj == NE - 1 && G == L * GPL) {  // the top edge alone (see winner_step)
-        const double xg = tab.xe[G] * invT;
-        if (xg >= 40.0 && xg < HUGE_VAL) {
-          const double em = exp(-xg);
-          const double x2 = xg * xg;
-          pqE[jj] = kPlanckNorm * em * (x2 * xg + 3.0 * x2 + 6.0 * xg + 6.0);
-          dE_[jj] = kPlanckNorm * em * x2 * x2;
-          eE[jj] = dE_[jj] * (4.0 - xg);
-          lowE[jj] = false;
-          continue;
-        }
-      }
-      edge_tab(tab.pc, e <= G ? tab.xe[e] * invT : 1.0, pqE[jj], dE_[jj], eE[jj], lowE[jj]);
-    }
-    dflt pqD[NE], dD_[NE];
-    float eF[NE];
-#pragma unroll
-    for (int jj = 0; jj < NE; ++jj) {
-      pqD[jj] = df_from_double(pqE[jj], 0);
-      dD_[jj] = df_from_double(dE_[jj], 0);
-      eF[jj] = scaled_f(eE[jj], 0);
+      const dflt x = e <= G ? df_of(dt.xe[e]) * invT : dflt{1.0f, 0.0f};
+      edge_df(pl, x, pqD[jj], dD_[jj], eF[jj], lowE[jj]);
     }
     // ---- the residual, group by group (rhd_correct.cuh's rows in float-float)
     float rR[GPL], rF[GPL][3], Eg[GPL];
@@ -372,17 +476,18 @@ __global__ void __launch_bounds__(128) refine_warp_kernel(const __grid_constant_
                                                           const WarmOut W, const CorrOut U) {
   extern __shared__ double sm[];
   const GroupTable tab = build_table(P, sm);
-  float2 *dfs = reinterpret_cast<float2 *>(reinterpret_cast<char *>(sm) +
-                                           ((table_bytes(P.G) + 15) & ~(size_t)15));
-  const DfTable dt = build_df_table(tab, dfs, P.G);
-  float *blocks = reinterpret_cast<float *>(dfs + 5 * P.G);
+  char *base = reinterpret_cast<char *>(sm) + ((table_bytes(P.G) + 15) & ~(size_t)15);
+  const DfPlanck pl = build_df_planck(tab.pc, reinterpret_cast<float *>(base));
+  float2 *dfs = reinterpret_cast<float2 *>(base + refine_planck_bytes());
+  const DfTable dt = build_df_table(tab, dfs, P.G);  // synchronises (both tables)
+  float *blocks = reinterpret_cast<float *>(dfs + 6 * P.G + 1);
   const int lane = threadIdx.x & 31, seg = lane / L;
   float *gb = warp_blocks<GPL>(blocks, threadIdx.x / 32);
   constexpr int CPW = 32 / L;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
   const int64_t nwarps = (int64_t)gridDim.x * blockDim.x / 32;
   for (int64_t i = warp * CPW + seg; i < P.n; i += nwarps * CPW)
-    refine_cell<L, GPL>(P, tab, dt, W, U, gb, i, lane);
+    refine_cell<L, GPL>(P, tab, dt, pl, W, U, gb, i, lane);
 }
 
 }  // namespace rhd
