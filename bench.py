@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--cell-per-thread", action="store_true",
                     help="one cell per thread in every pass (the mapping whose operation "
                          "counts define the algorithmic flops; slower at 33-128 groups)")
+    ap.add_argument("--lanes16", action="store_true",
+                    help="33..64 groups: 16 lanes per cell in the mixed form's warp kernels "
+                         "(RHD_LANES_16) instead of 32")
     ap.add_argument("--no-surrogate", action="store_true",
                     help="time the solver from the cold start (no learned warm start)")
     ap.add_argument("--sur-train-cells", type=int, default=1 << 21)
@@ -169,6 +172,7 @@ def fp_peaks() -> dict:
 OPCOUNTS = os.path.join(ROOT, "tests", "golden", "opcounts.json")
 # events of each kind of launch (the names of rhd.EVENT_NAMES and of the table)
 KERNEL_EVENTS = {"fp32_passes": ("eval32", "outer32"),
+                 "refine": ("residdf", "stepdf"),
                  "correction": ("resid64", "step32", "finish64"),
                  "fp64_passes": ("eval64", "cached64", "outer64")}
 # the per-update setup (tau_g and its reciprocals) once per cell of these counters
@@ -176,7 +180,7 @@ KERNEL_CELLS = {"correction": "cellsc", "fp64_passes": "cells64"}
 # DRAM bytes (read + write) per cell-group of one launch of the dominant kernel,
 # ncu on a 65536-cell sample of the same workload
 # (profiles/correct_warp_kernel_65536cells_ng64.md); None once the kernel changed
-DOMINANT_TRAFFIC_PER_CG = {("full_256cube_ng64", "correction"): 69.4}
+DOMINANT_TRAFFIC_PER_CG = {("full_256cube_ng64", "correction"): 87.9}
 
 
 def op_slots(counts: dict, weights: dict) -> float:
@@ -187,19 +191,31 @@ def op_slots(counts: dict, weights: dict) -> float:
 
 
 def algorithmic_ops(workload: str, events: dict, G: int, peaks: dict) -> dict:
-    """{kernel: {"f64": slots, "f32": slots}} of the algorithm for the events counted."""
+    """{kernel: {"f64": slots, "f32": slots}} of the algorithm for the events counted
+    (float-float operations as the FP32 operations they are made of)."""
     with open(OPCOUNTS) as f:
-        table = json.load(f)["events"].get(workload)
+        full = json.load(f)
+    table = full["events"].get(workload)
     if table is None:
         return {}
     w64 = peaks.get("fp64_op_slots", {})
     w32 = peaks.get("fp32_op_slots", {})
+    dfc = full.get("df_fp32_ops", {})
+
+    def df_as_f32(counts: dict) -> dict:
+        out = {}
+        for kind, n in counts.items():
+            for k, v in dfc.get(kind, {}).items():
+                out[k] = out.get(k, 0.0) + n * v
+        return out
+
     out = {}
     for kern, evs in KERNEL_EVENTS.items():
         f64 = f32 = 0.0
         for e in evs:
             f64 += events.get(e, 0) * G * op_slots(table[e]["f64"], w64)
             f32 += events.get(e, 0) * G * op_slots(table[e]["f32"], w32)
+            f32 += events.get(e, 0) * G * op_slots(df_as_f32(table[e].get("df", {})), w32)
         if kern in KERNEL_CELLS:
             f64 += events.get(KERNEL_CELLS[kern], 0) * G * op_slots(table["setup64"]["f64"], w64)
         out[kern] = {"f64": f64, "f32": f32}
@@ -246,7 +262,8 @@ def run_ours(args, ws, rank):
         for k in ("mom", "egas", "erad", "frad"):
             st[k].copy_(pristine[k])
 
-    flags = rhd.CELL_PER_THREAD if args.cell_per_thread else 0
+    flags = (rhd.CELL_PER_THREAD if args.cell_per_thread else 0) | (
+        rhd.LANES_16 if args.lanes16 else 0)
 
     def call(p, warm):
         args_ = dict(dt=w.dt, c_v=w.c_v, consts=w.consts, precision=p, status=status,
@@ -319,7 +336,8 @@ def run_ours(args, ws, rank):
            "dtype": "f64" if prec == rhd.FP64 else ("f32+f64+bf16" if use_sur else "f32+f64"),
            "data": "synthetic (seeded generators of paper_2407_18304_gb300.synth)",
            "config": {"workload": name, "cells": n, "n_groups": G, "form": form,
-                      "mapping": "cell per thread" if args.cell_per_thread else "warp per cell",
+                      "mapping": ("cell per thread" if args.cell_per_thread else
+                                  "16 lanes per cell" if args.lanes16 else "warp per cell"),
                       "precision": args.precision, "tol": 1e-11, "tol_outer": 1e-13,
                       "l2": "state restored from a pristine copy before each step (2x state > L2)",
                       "parallelism": f"weak x{ws}, no collective"},

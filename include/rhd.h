@@ -83,6 +83,12 @@ extern "C" {
                                  without the lane-replicated per-cell work: under this flag
                                  the thread mapping also takes the warp mapping's cached first
                                  iteration of each outer pass, which it otherwise skips) */
+#define RHD_LANES_16 8 /* 33..64 groups: the mixed form's FP32 passes, first correction step
+                          and correction spread a cell over 16 lanes with 4 groups each (two
+                          cells per warp) instead of 32 lanes with 2 groups each; same
+                          equations and results to rounding, a different balance of
+                          registers, shuffles and cells in flight; no effect on other group
+                          counts, on the FP64 form or with RHD_CELL_PER_THREAD */
 #define RHD_FLUX_TEST 2  /* the outer iteration also stops only when the change of the
                             group fluxes, sum_g |F_g,new - F_g,old|_1 / c, is below
                             tol_outer E_tot (the paper's test sees F_g only through the
@@ -121,7 +127,8 @@ typedef struct {
   int32_t max_outer;    /* outer-iteration cap; <= 0 selects 16 */
   int32_t precision;    /* RHD_FP64 | RHD_MIXED */
   int32_t closure;      /* RHD_M1 | RHD_EDDINGTON */
-  int32_t flags;        /* 0, or RHD_GROUP_TEST | RHD_FLUX_TEST | RHD_CELL_PER_THREAD */
+  int32_t flags;        /* 0, or RHD_GROUP_TEST | RHD_FLUX_TEST | RHD_CELL_PER_THREAD |
+                           RHD_LANES_16 */
 } rhd_state_t;
 
 /* Lab-frame group edges (Sec. 2.1, eq. Qg: contiguous groups).  HOST array of

@@ -28,7 +28,15 @@ min, max) and of its precision.  The events are
   of every group's four rows, the elimination of each group's block, the
   4 x 4 system of the cell, the step;
 * ``finish64``: the end of a converged cell -- each R_g from its own row, the
-  flux update, the conservative write-back of E_g, E_gas and the momentum.
+  flux update, the conservative write-back of E_g, E_gas and the momentum;
+* ``residdf`` / ``stepdf``: the first Newton step of the correction with the
+  coupled residual evaluated in float-float arithmetic (no tests: that step
+  decides nothing) and the same FP32 step as ``step32``.  Its operations are
+  the FP64 residual's, tallied under the precision ``df``; ``DF_FP32_OPS``
+  gives the FP32 operations each float-float operation takes with the
+  error-free transformations it is built from (Knuth's two-sum: 6 additions;
+  Dekker's fast two-sum: 3; a product's error by one FMA) in the "sloppy"
+  double-double forms of Hida, Li & Bailey (2001).
 
 Each event is counted as a part per group plus a part per cell, so a count
 per cell-group follows for any N_g: ``per_cell_group(event, G)``.  Special
@@ -57,6 +65,49 @@ import numpy as np
 from . import planck_P, planck_Q
 
 KINDS = ("add", "mul", "fma", "div", "sqrt", "exp", "cmp")
+PRECS = ("f64", "f32", "df")
+
+# FP32 operations of one float-float operation (hi + lo, ~48 bits):
+#   add  a + b: two-sum of the high words (6), the low words added to its
+#        error (2), fast two-sum renormalisation (3);
+#   mul  a b: the high product and its error by FMA (1 mul, 1 fma), the cross
+#        terms (2 fma), fast two-sum (3 add);
+#   fma  a b + c: a mul then an add;
+#   div  a / b: FP32 reciprocal of b's high word (1 div), first quotient
+#        (1 mul), its exact product with b (1 mul, 1 fma), the remainder
+#        (3 add, 1 fma), the correction (1 mul), fast two-sum (3 add);
+#   sqrt FP32 square root (1 sqrt), its exact square (1 mul, 1 fma), the
+#        remainder (3 add), one Newton correction over 2 s (1 div, 1 mul),
+#        fast two-sum (3 add);
+#   exp  expm1 with Cody & Waite's reduction s = k ln 2 + r (ln 2 in three
+#        parts: 4 mul, 1 fma, 32 add), the Taylor series of expm1(r) to r^13
+#        (six terms in FP32: 6 fma; six in float-float: 6 mul + 6 add), its
+#        assembly r + r^2 S (2 mul, 1 add) and the scaling by 2^k with
+#        e^s = 2^k (expm1(r) + 1) beside it (4 mul, 2 add);
+#   cmp  high words, then low words on a tie: 2 compares.
+_DF_ADD = {"add": 11}
+_DF_MUL = {"mul": 1, "fma": 3, "add": 3}
+
+
+def _df_sum(*parts):
+    out = {k: 0 for k in KINDS}
+    for n, p in parts:
+        for k, v in p.items():
+            out[k] += n * v
+    return out
+
+
+DF_FP32_OPS = {
+    "add": _df_sum((1, _DF_ADD)),
+    "mul": _df_sum((1, _DF_MUL)),
+    "fma": _df_sum((1, _DF_MUL), (1, _DF_ADD)),
+    "div": _df_sum((1, {"div": 1, "mul": 3, "fma": 2, "add": 6})),
+    "sqrt": _df_sum((1, {"sqrt": 1, "div": 1, "mul": 2, "fma": 1, "add": 6})),
+    "exp": _df_sum((1, {"mul": 4, "fma": 1, "add": 32}), (6, {"fma": 1}),
+                   (6, _DF_MUL), (6, _DF_ADD), (2, _DF_MUL), (1, _DF_ADD),
+                   (4, {"mul": 1}), (2, _DF_ADD)),
+    "cmp": _df_sum((1, {"cmp": 2})),
+}
 K15 = 15.0 / math.pi ** 4
 PLANCK_DEGREE = 13
 
@@ -65,10 +116,11 @@ class Tally:
     """Counts of operations by (precision, kind)."""
 
     def __init__(self):
-        self.c = {p: {k: 0 for k in KINDS} for p in ("f64", "f32")}
+        self.c = {p: {k: 0 for k in KINDS} for p in PRECS}
+        self.remap = {}  # precision -> precision it is tallied under
 
     def add(self, prec: str, kind: str, n: int = 1):
-        self.c[prec][kind] += n
+        self.c[self.remap.get(prec, prec)][kind] += n
 
     def snapshot(self) -> dict:
         return {p: dict(v) for p, v in self.c.items()}
@@ -808,7 +860,7 @@ def finish(cell: Cell, res: dict):
 # the table the benchmark reads
 # ---------------------------------------------------------------------------
 EVENTS = ("setup64", "eval64", "cached64", "outer64", "eval32", "outer32", "resid64", "step32",
-          "finish64")
+          "finish64", "residdf", "stepdf")
 
 
 def _event_counts(state, i, params, groups):
@@ -850,6 +902,18 @@ def _event_counts(state, i, params, groups):
     t0 = TALLY.snapshot()
     finish(cell, res)
     out["finish64"] = Tally.diff(t0, TALLY.snapshot())
+    # the first step with the residual in float-float: the FP64 residual's
+    # operations under "df"; its tests (FP32) are not part of that step
+    cell = make_cell(state, i, params, groups)
+    setup(cell)
+    TALLY.remap = {"f64": "df"}
+    t0 = TALLY.snapshot()
+    coupled_residual(cell, 0.0, 0.0)
+    d = Tally.diff(t0, TALLY.snapshot())
+    TALLY.remap = {}
+    d["f32"] = {k: 0 for k in KINDS}
+    out["residdf"] = d
+    out["stepdf"] = {p: dict(v) for p, v in out["step32"].items()}
     return out
 
 
@@ -869,15 +933,16 @@ def table(presets=("full_256cube_ng64", "surrogate_256cube_ng32", "mixed_128cube
         km, al = group_table(w.edges, PPL_FIXED, w.law.nu_break, w.law.seg_logk,
                              w.law.seg_beta, w.law.nu_ref)
         g = Groups(w.edges, km, al)
-        acc = {e: {pr: {k: 0.0 for k in KINDS} for pr in ("f64", "f32")} for e in EVENTS}
+        acc = {e: {pr: {k: 0.0 for k in KINDS} for pr in PRECS} for e in EVENTS}
         for i in range(n_cells):
             ev = _event_counts(st, i, p, g)
             for e in EVENTS:
-                for pr in ("f64", "f32"):
+                for pr in PRECS:
                     for k in KINDS:
                         acc[e][pr][k] += ev[e][pr][k] / (n_cells * w.n_groups)
         out["events"][name] = {e: {pr: {k: round(v, 4) for k, v in acc[e][pr].items()}
-                                   for pr in ("f64", "f32")} for e in EVENTS}
+                                   for pr in PRECS} for e in EVENTS}
+    out["df_fp32_ops"] = DF_FP32_OPS
     return out
 
 

@@ -202,7 +202,8 @@ int pack(const rhd_state_t *s, const rhd_groups_t *gr, const rhd_opacity_law_t *
   if (!std::isfinite(dt) || dt < 0.0) return RHD_EINVAL;
   if (s->precision != RHD_FP64 && s->precision != RHD_MIXED) return RHD_EINVAL;
   if (s->closure != RHD_M1 && s->closure != RHD_EDDINGTON) return RHD_EINVAL;
-  if (s->flags & ~(RHD_GROUP_TEST | RHD_FLUX_TEST | RHD_CELL_PER_THREAD)) return RHD_EINVAL;
+  if (s->flags & ~(RHD_GROUP_TEST | RHD_FLUX_TEST | RHD_CELL_PER_THREAD | RHD_LANES_16))
+    return RHD_EINVAL;
   if (law->mode != RHD_PPL_FIXED && law->mode != RHD_PC && law->mode != RHD_PPL_FREE)
     return RHD_ELAW;
   // edges: strictly increasing; PPL needs finite positive edges
@@ -362,6 +363,11 @@ void launch_fp32_passes_impl(const KParams &kp, const WarmOut &wo, const WarmSta
   const int threads = 128;
   const size_t smem = table_bytes(kp.G);
   if (kp.G > 32 && kp.G <= 64 && !(kp.flags & RHD_CELL_PER_THREAD)) {
+    if (kp.flags & RHD_LANES_16) {  // two cells per warp
+      const int b = persistent_blocks(warm_warp32_kernel<16, 4>, smem, sms, kp.n * 16, threads);
+      warm_warp32_kernel<16, 4><<<b, threads, smem, st>>>(kp, wo, S);
+      return;
+    }
     const int b = persistent_blocks(warm_warp32_kernel<32, 2>, smem, sms, kp.n * 32, threads);
     warm_warp32_kernel<32, 2><<<b, threads, smem, st>>>(kp, wo, S);
     return;
@@ -402,15 +408,18 @@ WarmStart launch_correct(const KParams &kp, const WarmOut &wo, const WarmStart &
                          cudaStream_t st) {
   WarmStart w = wi;
   if (kp.G > 128) return w;
+  const bool l16 = (kp.flags & RHD_LANES_16) != 0;
   timed_launch(RHD_KERNEL_REFINE, st, [&] {
     if (kp.G <= 16) launch_refine_k<8, 2>(kp, wo, sms, st);
     else if (kp.G <= 32) launch_refine_k<16, 2>(kp, wo, sms, st);
+    else if (kp.G <= 64 && l16) launch_refine_k<16, 4>(kp, wo, sms, st);
     else if (kp.G <= 64) launch_refine_k<32, 2>(kp, wo, sms, st);
     else launch_refine_k<32, 4>(kp, wo, sms, st);
   });
   timed_launch(RHD_KERNEL_CORRECTION, st, [&] {
     if (kp.G <= 16) launch_correct_k<8, 2>(kp, wo, sms, st);
     else if (kp.G <= 32) launch_correct_k<16, 2>(kp, wo, sms, st);
+    else if (kp.G <= 64 && l16) launch_correct_k<16, 4>(kp, wo, sms, st);
     else if (kp.G <= 64) launch_correct_k<32, 2>(kp, wo, sms, st);
     else launch_correct_k<32, 4>(kp, wo, sms, st);
   });

@@ -21,6 +21,7 @@ STATUS_OK, STATUS_FALLBACK, STATUS_MAXITER, STATUS_INVALID = 0, 1, 2, 3
 GROUP_TEST = 1
 FLUX_TEST = 2
 CELL_PER_THREAD = 4
+LANES_16 = 8
 MAX_GROUPS = 256
 NOALLOC_BYTES = 64 << 20
 

@@ -64,7 +64,8 @@ def test_argument_checks_without_a_device(lib):
     assert _call(lib, synth.log_edges(300)) == -6
     assert _call(lib, edges, c_v=-1.0) == -1
     assert _call(lib, edges, precision=7) == -1
-    assert _call(lib, edges, flags=8) == -1
+    assert _call(lib, edges, flags=rhd.LANES_16) == 0
+    assert _call(lib, edges, flags=16) == -1
     law = synth.OpacityLaw(np.array([2.0, 1.0]), np.zeros(3), np.zeros(3), synth.NU0)
     assert _call(lib, edges, law=law) == -3  # breakpoints must increase
     # pointers missing with cells to do

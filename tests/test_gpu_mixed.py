@@ -134,3 +134,25 @@ def test_float_float_first_step_leaves_one_fp64_residual_per_cell(preset, n):
     assert e["T"] < MIXED_BOUND and e["erad"] < MIXED_BOUND
     ce, cm = conservation(g, st0, w.consts["c"], w.consts["c_hat"])
     assert ce < 64 * 2.0 ** -52 and cm < 64 * 2.0 ** -52
+
+
+@pytest.mark.parametrize("G,n", [(33, 257), (48, 257), (64, 300)])
+def test_sixteen_lanes_per_cell_match_the_oracle(G, n):
+    """RHD_LANES_16: from 33 to 64 groups the FP32 passes, the first correction
+    step and the correction put a cell on 16 lanes with 4 groups each (two
+    cells per warp; 33 and 48 leave lanes with empty slots).  Same bounds
+    against the oracle as the default mapping, at the default and at tight
+    tolerances, and conservation at FP64 round-off."""
+    w = synth.preset("full_256cube_ng64", n_cells=n, seed=900 + G, n_groups=G)
+    o = run_oracle(w)
+    st0 = synth.to_numpy(w.state)
+    for kw, floor, bound in (({}, DEFAULT_FLOOR, MIXED_BOUND), (TIGHT, TIGHT_FLOOR, 1e-10)):
+        g = run_gpu(w, precision=rhd.MIXED, flags=rhd.LANES_16, **kw)
+        ok = agreed("sixteen_lanes_per_cell_match_the_oracle", g, oracle=o)
+        gs, os_, ss = select(g, ok), select(o, ok), select(st0, ok)
+        e = errors(gs, os_, ss, w.consts["c"], w.c_v, floor=floor)
+        print(G, "16 lanes", kw, " ".join(f"{k}={v:.2e}" for k, v in e.items()))
+        ce, cm = conservation(gs, ss, w.consts["c"], w.consts["c_hat"])
+        assert ce < 64 * 2.0 ** -52 and cm < 64 * 2.0 ** -52
+        for k in ("T", "egas", "erad"):
+            assert e[k] < bound, (kw, k, e[k])

@@ -107,3 +107,18 @@ def test_the_committed_table_is_what_the_generator_writes():
     with open(path) as f:
         committed = f.read()
     assert committed == json.dumps(OC.table(), indent=1, sort_keys=True) + "\n"
+
+
+def test_the_float_float_step_counts_the_fp64_residual_operations():
+    """residdf is the coupled residual of resid64 with its FP64 operations in
+    float-float (tallied under "df") and without the tests; stepdf is step32."""
+    w = synth.preset("full_256cube_ng64", n_cells=1, seed=5, n_groups=8)
+    ev = OC._event_counts(synth.to_numpy(w.state), 0, _params(w), oracle_groups(w))
+    assert ev["residdf"]["df"] == ev["resid64"]["f64"]
+    assert all(v == 0 for v in ev["residdf"]["f64"].values())
+    assert all(v == 0 for v in ev["residdf"]["f32"].values())
+    assert sum(ev["resid64"]["f32"].values()) > 0  # the tests, which residdf leaves out
+    assert ev["stepdf"] == ev["step32"]
+    # a float-float operation costs several FP32 operations, never none
+    for k in OC.KINDS:
+        assert sum(OC.DF_FP32_OPS[k].values()) >= 2
