@@ -129,9 +129,8 @@ __device__ __forceinline__ dflt df_min(dflt a, dflt b) { return b < a ? b : a; }
 __device__ __forceinline__ dflt df_max(dflt a, dflt b) { return a < b ? b : a; }
 
 // A double times 2^-sh as a float-float, from the bit pattern: the first 24
-// significant bits cut (not rounded) into hi, the next 24 into lo.  One FP64
-// subtraction (x minus its cut part, exact); results below FP32's normal
-// range give 0, above it +-inf.
+// significant bits cut (not rounded) into hi, the next 24 into lo.  No FP64
+// instruction; results below FP32's normal range give 0, above it +-inf.
 __device__ __forceinline__ float df_cut_bits(int hw, int lw, int sh) {
   const int E = (hw >> 20) & 0x7FF;
   const unsigned sign = (unsigned)hw & 0x80000000u;
@@ -143,11 +142,28 @@ __device__ __forceinline__ float df_cut_bits(int hw, int lw, int sh) {
   return __int_as_float((int)(sign | ((unsigned)fe << 23) | frac));
 }
 
+// The part of a normal double below its first 24 significant bits (the low
+// 29 bits of its fraction, r 2^(E - 1075)) times 2^-sh, cut to 24 bits, from
+// the bit pattern alone: the exact x - (its 24-bit cut) that an FP64
+// subtraction would form, then cut as df_cut_bits cuts.  Integer instructions
+// only; results below FP32's normal range give 0.
+__device__ __forceinline__ float df_rest_bits(int hw, int lw, int sh) {
+  const int E = (hw >> 20) & 0x7FF;
+  const unsigned sign = (unsigned)hw & 0x80000000u;
+  const unsigned r = (unsigned)lw & 0x1FFFFFFFu;
+  if (r == 0u) return 0.0f;  // an exact cut: the FP64 difference would be +0
+  if (E == 0) return __int_as_float((int)sign);
+  const int top = 31 - __clz((int)r);  // the leading one of r: r in [2^top, 2^(top+1))
+  const int fe = top + E - 1075 - sh + 127;
+  if (fe <= 0) return __int_as_float((int)sign);
+  if (fe >= 255) return __int_as_float((int)(sign | 0x7F800000u));
+  const unsigned m = (top >= 23 ? (r >> (top - 23)) : (r << (23 - top))) & 0x7FFFFFu;
+  return __int_as_float((int)(sign | ((unsigned)fe << 23) | m));
+}
+
 __device__ __forceinline__ dflt df_from_double(double x, int sh) {
   const int hw = __double2hiint(x), lw = __double2loint(x);
-  const double rest = x - __hiloint2double(hw, lw & ~((1 << 29) - 1));
-  return dflt{df_cut_bits(hw, lw, sh),
-              df_cut_bits(__double2hiint(rest), __double2loint(rest), sh)};
+  return dflt{df_cut_bits(hw, lw, sh), df_rest_bits(hw, lw, sh)};
 }
 
 }  // namespace rhd

@@ -4,14 +4,20 @@
 // The steps are those of rhd_mixed.cuh (energy-scaled variables: R~ = R /
 // E_tot, f = F / (c E_tot), beta = v / c).  What changes is where FP64 is
 // left: a cell's scalar work runs on every lane here, and on GB300 an FP64
-// instruction costs 64 FP32 ones, so the internal energy is carried as an
-// FP64 base E_int,0 (set once per outer pass, where E_gas - E_kin is formed)
-// plus an FP32 offset, E_int = E_int,0 + E_tot dE~; T, a_R T^4 and the energy
-// residual F_G are formed in FP32 relative to the base.  Each evaluation is
-// then FP32 throughout, including the Planck edges (planck_table.h
-// polynomials truncated to degree 7, whose dropped terms are below FP32
-// resolution).
+// instruction costs 64 FP32 ones (a warp-wide one holds the FP64 pipe of its
+// SM sub-partition for 64 cycles), so nothing of the iteration is FP64: the
+// quantities that cancel -- the internal energy E_int = E_gas - E_kin and the
+// momentum -- are carried in float-float arithmetic (rhd_df.cuh, ~48 bits) in
+// units of E_tot and rho c, the internal energy as a base E_int,0 (set once
+// per outer pass, where E_gas - E_kin is formed) plus an FP32 offset,
+// E_int = E_int,0 + E_tot dE~; T, a_R T^4 and the energy residual F_G are
+// formed in FP32 relative to the base.  Each evaluation is FP32 throughout,
+// including the Planck edges (planck_table.h polynomials truncated to degree
+// 7, whose dropped terms are below FP32 resolution).  FP64 is left to loading
+// a cell (its validity and E_tot, tested as the FP64 passes test them) and to
+// storing its iterate.
 #pragma once
+#include "rhd_df.cuh"
 #include "rhd_mixed.cuh"
 #include "rhd_warp.cuh"
 
@@ -23,11 +29,16 @@ constexpr int kPlanckF = (kDeg32 + 3) * planck_table::kSeg;  // coef [8][kSeg], 
 template <int L, int GPL>
 struct WCell32 {
   int64_t i;
-  double rho, irho, m0[3], eg0, chi0s, Etot, irc;  // irho = 1/rho
-  int shE, shV;  // E_tot = mE 2^shE, rho c = mV 2^shV (mE, mV in [0.5, 1))
-  float imE, imV;  // 1 / mE, 1 / mV
-  double m[3], KE, Eint;  // Eint: the FP64 base of the current pass
-  double chg_prev;
+  double chi0s, Etot, rhoc;  // rho kappa0, E_tot, rho c (loading and storing only)
+  int shE;     // E_tot = mE 2^shE (mE in [0.5, 1))
+  float imE;   // 1 / mE
+  float irc;   // E_tot / (rho c_v): T = (E_int / E_tot) irc
+  dflt egs;    // E_gas^t / E_tot
+  dflt bm0[3], bm[3];  // (rho v)^t and rho v in units of rho c: beta^t, beta
+  dflt kmu;    // E_tot / (rho c c_hat): beta = beta^t - kmu sum_g (f_g - f_g^t), eq. vupdate
+  dflt kke;    // rho c^2 / E_tot: E_kin / E_tot = kke |beta|^2 / 2
+  dflt ke, ei; // E_kin / E_tot and E_int,0 / E_tot (the base of the current pass)
+  float chg_prev;
   int nit, it, outer, slow;
   float eb;    // E_int,0 / E_tot
   float dlt;   // (E_int - E_int,0) / E_tot
@@ -111,22 +122,27 @@ __device__ __forceinline__ void w32_set_tau(const KParams &P, const GroupTable &
   }
 }
 
-// Load (as load_cell32); false for an invalid cell (the FP64 passes write its status).
+// x 2^k for a float x and |k| up to ~250, in two exact power-of-two steps.
+__device__ __forceinline__ float times_pow2(float x, int k) {
+  const int k1 = k / 2, k2 = k - k1;
+  return x * __int_as_float((127 + k1) << 23) * __int_as_float((127 + k2) << 23);
+}
+
+// Load (as load_cell32); false for an invalid cell (the FP64 passes write its
+// status).  S.r non-null starts the cell from S's internal energy and R_g.
 template <int L, int GPL>
 __device__ __forceinline__ bool w32_load(const KParams &P, const GroupTable &tab, int64_t i, int l,
-                                         unsigned mask, WCell32<L, GPL> &C) {
+                                         unsigned mask, const WarmStart &S, WCell32<L, GPL> &C) {
   const int G = P.G;
   C.i = i;
-  C.rho = P.rho[i];
-  C.m0[0] = P.mom[0][i];
-  C.m0[1] = P.mom[1][i];
-  C.m0[2] = P.mom[2][i];
-  C.eg0 = P.egas[i];
+  const double rho = P.rho[i];
+  const double m0[3] = {P.mom[0][i], P.mom[1][i], P.mom[2][i]};
+  const double eg0 = P.egas[i];
   const double k0 = P.kappa0 ? P.kappa0[i] : 1.0;
-  bool valid = C.rho > 0.0 && isfinite(C.rho) && isfinite(C.eg0) && isfinite(k0) && k0 >= 0.0 &&
-               isfinite(C.m0[0]) && isfinite(C.m0[1]) && isfinite(C.m0[2]);
-  const double KE0 = 0.5 * (C.m0[0] * C.m0[0] + C.m0[1] * C.m0[1] + C.m0[2] * C.m0[2]) / C.rho;
-  valid = valid && (C.eg0 - KE0 > 0.0);
+  bool valid = rho > 0.0 && isfinite(rho) && isfinite(eg0) && isfinite(k0) && k0 >= 0.0 &&
+               isfinite(m0[0]) && isfinite(m0[1]) && isfinite(m0[2]);
+  const double KE0 = 0.5 * (m0[0] * m0[0] + m0[1] * m0[1] + m0[2] * m0[2]) / rho;
+  valid = valid && (eg0 - KE0 > 0.0);  // the FP64 passes' test, to the bit
   double e[GPL], sumE0 = 0.0;
 #pragma unroll
   for (int j = 0; j < GPL; ++j) {
@@ -134,7 +150,7 @@ __device__ __forceinline__ bool w32_load(const KParams &P, const GroupTable &tab
     e[j] = 0.0;
     if (g < G) {
       const int64_t o = (int64_t)g * P.gs + i;
-      e[j] = P.erad[o] + (P.src ? P.src[o] : 0.0);
+      e[j] = P.src ? P.erad[o] + P.src[o] : P.erad[o];
       valid = valid && isfinite(e[j]) && isfinite(P.frad[0][o]) && isfinite(P.frad[1][o]) &&
               isfinite(P.frad[2][o]);
       sumE0 += e[j];
@@ -142,22 +158,33 @@ __device__ __forceinline__ bool w32_load(const KParams &P, const GroupTable &tab
   }
   if (!__all_sync(mask, valid)) return false;
   sumE0 = seg_sum<L>(sumE0, mask);
-  C.chi0s = C.rho * k0;
-  C.Etot = C.eg0 + P.cr * sumE0;
-  C.irho = 1.0 / C.rho;
-  C.irc = C.irho / P.c_v;
+  C.chi0s = rho * k0;
+  C.Etot = eg0 + P.cr * sumE0;
+  C.rhoc = rho * P.c;
   // the energy-scaled group values are formed in FP32 from the bit patterns
   // (exact power-of-two scaling by E_tot's exponent, then one FP32 multiply):
   // no FP64 instruction per group
-  C.imE = 1.0f / frexp_f(C.Etot, C.shE);
-  C.imV = 1.0f / frexp_f(C.rho * P.c, C.shV);
-  C.m[0] = C.m0[0];
-  C.m[1] = C.m0[1];
-  C.m[2] = C.m0[2];
-  C.Eint = C.eg0 - KE0;
+  const float mE = frexp_f(C.Etot, C.shE);
+  C.imE = 1.0f / mE;
+  int shV, shR;
+  frexp_f(C.rhoc, shV);
+  const float mR = frexp_f(rho * P.c_v, shR);
+  C.irc = times_pow2(mE / mR, C.shE - shR);
+  // the per-cell scalars in float-float, in units of E_tot and rho c
+  const dflt mEd = df_from_double(C.Etot, C.shE), imEd = df_rcp(mEd);
+  const dflt imVd = df_rcp(df_from_double(C.rhoc, shV));
+  C.egs = df_from_double(eg0, C.shE) * imEd;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) C.bm0[d] = C.bm[d] = df_from_double(m0[d], shV) * imVd;
+  C.kmu = mEd / df_from_double(C.rhoc * P.c_hat, C.shE);
+  C.kke = df_from_double(C.rhoc * P.c, C.shE) * imEd;
+  C.ke = df_scale(C.kke * (C.bm0[0] * C.bm0[0] + C.bm0[1] * C.bm0[1] + C.bm0[2] * C.bm0[2]), 0.5f);
+  C.ei = C.egs - C.ke;
+  const bool warm = S.r && S.eint[i] > 0.0;
+  if (warm) C.ei = df_from_double(S.eint[i], C.shE) * imEd;
   C.nit = 0;
   C.outer = 0;
-  C.chg_prev = HUGE_VAL;
+  C.chg_prev = __int_as_float(0x7F800000);
   C.slow = 0;
   const float fsf = C.imE / (float)P.c;
 #pragma unroll
@@ -168,6 +195,7 @@ __device__ __forceinline__ bool w32_load(const KParams &P, const GroupTable &tab
       const int64_t o = (int64_t)g * P.gs + i;
       C.e0[j] = scaled_f(e[j], C.shE) * C.imE;
       for (int d = 0; d < 3; ++d) C.ft[j][d] = C.f[j][d] = scaled_f(P.frad[d][o], C.shE) * fsf;
+      if (warm) C.R[j] = S.r[(int64_t)g * P.n + i];
     } else {
       C.e0[j] = 0.0f;
       for (int d = 0; d < 3; ++d) C.ft[j][d] = C.f[j][d] = 0.0f;
@@ -177,20 +205,24 @@ __device__ __forceinline__ bool w32_load(const KParams &P, const GroupTable &tab
   return true;
 }
 
-// a3 for a pass, and the FP64 base of the internal energy.
+// a3 for a pass, and the base of the internal energy.
 template <int L, int GPL>
 __device__ __forceinline__ void w32_outer_begin(const KParams &P, WCell32<L, GPL> &C) {
-  C.KE = 0.5 * (C.m[0] * C.m[0] + C.m[1] * C.m[1] + C.m[2] * C.m[2]) * C.irho;
-  for (int d = 0; d < 3; ++d) C.be[d] = scaled_f(C.m[d], C.shV) * C.imV;  // v / c
+  for (int d = 0; d < 3; ++d) C.be[d] = C.bm[d].hi;  // v / c
 #pragma unroll
   for (int j = 0; j < GPL; ++j)
     C.w[j] = C.be[0] * C.f[j][0] + C.be[1] * C.f[j][1] + C.be[2] * C.f[j][2];
-  const double T0 = C.Eint * C.irc;
-  C.eb = scaled_f(C.Eint, C.shE) * C.imE;
+  C.eb = C.ei.hi;
   C.dlt = 0.0f;
-  C.FG0 = scaled_f(C.Eint + C.KE - C.eg0, C.shE) * C.imE;
-  C.k4 = scaled_f(P.a_rad * T0 * T0 * T0 * T0, C.shE) * C.imE;
-  C.iT0 = 1.0f / (float)T0;
+  C.FG0 = ((C.ei + C.ke) - C.egs).hi;
+  // T0 = mT 2^eT; a_R T0^4 / E_tot = mT^4 (a_R 2^(4 eT - shE)) / mE, each factor
+  // inside FP32's range
+  const float T0 = C.eb * C.irc;
+  const int eT = ((__float_as_int(T0) >> 23) & 0xFF) - 126;
+  const float mT = __int_as_float((__float_as_int(T0) & 0x807FFFFF) | (126 << 23));
+  const float mT2 = mT * mT;
+  C.k4 = mT2 * mT2 * (scaled_f(P.a_rad, C.shE - 4 * eT) * C.imE);
+  C.iT0 = 1.0f / T0;
   C.it = 0;
 }
 
@@ -287,19 +319,19 @@ __device__ __forceinline__ int w32_inner_step(const KParams &P, const GroupTable
   return fabsf(dE) < 1e-8f ? 1 : 0;
 }
 
-// FP32 write-back, flux and momentum update, outer test (as outer_end32).
+// FP32 write-back, flux and momentum update, outer test (as outer_end32);
+// the gas energy, momentum and kinetic energy in float-float.
 template <int L, int GPL>
 __device__ __forceinline__ bool w32_outer_end(const KParams &P, const GroupTable &tab, int l,
                                               unsigned mask, WCell32<L, GPL> &C) {
   const int G = P.G;
-  const double Etot = C.Etot;
   const float cr = (float)P.cr;
   float sR = 0.0f;
 #pragma unroll
   for (int j = 0; j < GPL; ++j)
     if (l + L * j < G) sR += C.R[j];
   sR = seg_sumf<L>(sR, mask);
-  const double egas_new = C.eg0 - (double)cr * (double)sR * Etot;
+  const dflt egas_new = C.egs - two_prod(cr, sR);  // E_gas / E_tot after the write-back
   float df[3] = {0.0f, 0.0f, 0.0f};
   const float bmag = sqrtf(C.be[0] * C.be[0] + C.be[1] * C.be[1] + C.be[2] * C.be[2]);
 #pragma unroll
@@ -322,31 +354,37 @@ __device__ __forceinline__ bool w32_outer_end(const KParams &P, const GroupTable
     }
   }
   for (int d = 0; d < 3; ++d) df[d] = seg_sumf<L>(df[d], mask);
-  const double mf = Etot * P.icc * P.c;  // E_tot / c_hat
-  const double mn[3] = {C.m0[0] - mf * df[0], C.m0[1] - mf * df[1], C.m0[2] - mf * df[2]};
-  const double KEn = 0.5 * (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) * C.irho;
-  const float bn[3] = {scaled_f(mn[0], C.shV) * C.imV, scaled_f(mn[1], C.shV) * C.imV,
-                       scaled_f(mn[2], C.shV) * C.imV};
+  // eq. vupdate in units of rho c, and the kinetic energy of the new momentum
+  dflt bn[3];
+  for (int d = 0; d < 3; ++d) bn[d] = C.bm0[d] - C.kmu * df[d];
+  const dflt KEn = df_scale(C.kke * (bn[0] * bn[0] + bn[1] * bn[1] + bn[2] * bn[2]), 0.5f);
+  const float bnf[3] = {bn[0].hi, bn[1].hi, bn[2].hi};
   float cg = 0.0f;
 #pragma unroll
   for (int j = 0; j < GPL; ++j) {
     const int g = l + L * j;
     if (g >= G) continue;
-    const float wn = bn[0] * C.f[j][0] + bn[1] * C.f[j][1] + bn[2] * C.f[j][2];
+    const float wn = bnf[0] * C.f[j][0] + bnf[1] * C.f[j][1] + bnf[2] * C.f[j][2];
     cg += fabsf((1.0f + tab.alphaf[g]) * C.q[j] * (wn - C.w[j])) * C.qe[j];
   }
-  const float chg = scaled_f(fabs(KEn - C.KE), C.shE) * C.imE + seg_sumf<L>(cg, mask);
-  C.m[0] = mn[0];
-  C.m[1] = mn[1];
-  C.m[2] = mn[2];
-  if (C.outer >= 1 && chg > 0.25f * (float)C.chg_prev) C.slow = 1;
+  const float chg = fabsf((KEn - C.ke).hi) + seg_sumf<L>(cg, mask);
+  for (int d = 0; d < 3; ++d) C.bm[d] = bn[d];
+  if (C.outer >= 1 && chg > 0.25f * C.chg_prev) C.slow = 1;
   C.chg_prev = chg;
-  C.Eint = egas_new - KEn;  // the next pass's base (or the FP64 phase's start)
-  if (!(C.Eint > 0.0)) C.Eint = C.eg0 - C.KE;
+  dflt ein = egas_new - KEn;  // the next pass's base (or the correction's start)
+  if (!(ein.hi > 0.0f)) ein = C.egs - C.ke;
+  C.ei = ein;
+  C.ke = KEn;
   ++C.outer;
   if (chg <= 3e-8f || C.outer >= P.max_outer) return true;
   w32_outer_begin(P, C);
   return false;
+}
+
+// A float-float value in units of u (a double) as a double: two widenings
+// from the bit patterns (no FP64 instruction), one addition, one product.
+__device__ __forceinline__ double df_to_double(dflt v, double u) {
+  return (f2d(v.hi) + f2d(v.lo)) * u;
 }
 
 template <int L, int GPL>
@@ -354,10 +392,10 @@ __device__ __forceinline__ void w32_store(const KParams &P, const WarmOut &W, in
                                           const WCell32<L, GPL> &C) {
   const int64_t i = C.i, n = P.n;
   if (l == 0) {
-    W.eint[i] = C.Eint;
-    W.mom[i] = C.m[0];
-    W.mom[n + i] = C.m[1];
-    W.mom[2 * n + i] = C.m[2];
+    W.eint[i] = df_to_double(C.ei, C.Etot);
+    W.mom[i] = df_to_double(C.bm[0], C.rhoc);
+    W.mom[n + i] = df_to_double(C.bm[1], C.rhoc);
+    W.mom[2 * n + i] = df_to_double(C.bm[2], C.rhoc);
     W.nit[i] = (uint8_t)(C.nit > 255 ? 255 : C.nit);
   }
 #pragma unroll
@@ -379,15 +417,7 @@ template <int L, int GPL>
 __device__ __forceinline__ void w32_cell(const KParams &P, const GroupTable &tab, const float *pf,
                                          const WarmOut &W, const WarmStart &S, int64_t i, int l,
                                          int lane0, unsigned mask, WCell32<L, GPL> &C) {
-  if (!w32_load(P, tab, i, l, mask, C)) return;
-  if (S.r && S.eint[i] > 0.0) {
-    C.Eint = S.eint[i];
-#pragma unroll
-    for (int j = 0; j < GPL; ++j) {
-      const int g = l + L * j;
-      if (g < P.G) C.R[j] = S.r[(int64_t)g * P.n + i];
-    }
-  }
+  if (!w32_load(P, tab, i, l, mask, S, C)) return;
   w32_outer_begin(P, C);
   unsigned ne = 0, no = 0;
   for (;;) {
