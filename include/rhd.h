@@ -83,12 +83,13 @@ extern "C" {
                                  without the lane-replicated per-cell work: under this flag
                                  the thread mapping also takes the warp mapping's cached first
                                  iteration of each outer pass, which it otherwise skips) */
-#define RHD_LANES_16 8 /* 33..64 groups: the mixed form's FP32 passes, first correction step
-                          and correction spread a cell over 16 lanes with 4 groups each (two
-                          cells per warp) instead of 32 lanes with 2 groups each; same
-                          equations and results to rounding, a different balance of
-                          registers, shuffles and cells in flight; no effect on other group
-                          counts, on the FP64 form or with RHD_CELL_PER_THREAD */
+#define RHD_LANES_16 8 /* 33..64 groups: the warp kernels (FP64 passes; the mixed form's FP32
+                          passes, first correction step and correction) spread a cell over
+                          16 lanes with 4 groups each (two cells per warp) instead of 32
+                          lanes with 2 groups each; same equations and results to rounding,
+                          a different balance of registers, shuffles, per-cell work repeated
+                          on every lane of a cell, and cells in flight; no effect on other
+                          group counts or with RHD_CELL_PER_THREAD */
 #define RHD_FLUX_TEST 2  /* the outer iteration also stops only when the change of the
                             group fluxes, sum_g |F_g,new - F_g,old|_1 / c, is below
                             tol_outer E_tot (the paper's test sees F_g only through the

@@ -349,6 +349,7 @@ void launch_fp64_passes_impl(const KParams &kp, const WarmStart &W, int sms, cud
   }
   if (kp.G <= 16) launch_thread<16>(kp, W, sms, st);
   else if (kp.G <= 32) launch_thread<32>(kp, W, sms, st);
+  else if (kp.G <= 64 && (kp.flags & RHD_LANES_16)) launch_warp<16, 4>(kp, W, sms, st);
   else if (kp.G <= 64) launch_warp<32, 2>(kp, W, sms, st);
   else if (kp.G <= 128) launch_warp<32, 4>(kp, W, sms, st);
   else launch_thread<kMaxG>(kp, W, sms, st);

@@ -413,3 +413,22 @@ def test_breakpoints_inside_groups(G, n, v_max, tau_max, left_out, precision):
     print(f"interior G={G} prec={precision}: {matched} cells match, {roots} cells at a second "
           f"root (largest T difference {dT:.1e})")
     assert matched >= 0.5 * ok.sum()
+
+
+@pytest.mark.parametrize("G", [33, 48, 64])
+def test_fp64_passes_on_sixteen_lanes_per_cell(G):
+    """RHD_LANES_16 with the FP64 form: from 33 to 64 groups the FP64 passes put
+    a cell on 16 lanes with 4 groups each (two cells per warp; 33 and 48 leave
+    lanes with empty slots).  Same bounds against the oracle as the default
+    32-lane mapping, conservation at FP64 round-off."""
+    w = synth.preset("full_256cube_ng64", n_cells=257, seed=950 + G, n_groups=G)
+    g = run_gpu(w, precision=rhd.FP64, flags=rhd.LANES_16, **TIGHT)
+    o = run_oracle(w)
+    st0 = synth.to_numpy(w.state)
+    ok = agreed("fp64_passes_on_sixteen_lanes_per_cell", g, oracle=o)
+    e = errors(select(g, ok), select(o, ok), select(st0, ok), w.consts["c"], w.c_v, floor=FLOOR)
+    _report(f"G={G} 16 lanes fp64", e)
+    ce, cm = conservation(select(g, ok), select(st0, ok), w.consts["c"], w.consts["c_hat"])
+    assert ce < 64 * 2.0 ** -52 and cm < 64 * 2.0 ** -52
+    for k in (k for k in e if not k.endswith("_plain")):
+        assert e[k] < FP64_TOL, (k, e[k])
