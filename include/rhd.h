@@ -77,7 +77,8 @@ extern "C" {
                             that group's own energy (the paper's test is relative to
                             E_tot, which leaves groups far below E_tot loosely converged) */
 #define RHD_CELL_PER_THREAD 4 /* run every pass with one cell per thread (the other mapping
-                                 spreads a cell's 33..128 groups over a warp's lanes; same
+                                 spreads a cell's 33..128 groups over a warp's lanes, and in
+                                 the mixed form's FP32 passes 1..32 groups over 8 or 16; same
                                  equations and results to rounding, slower at those sizes;
                                  for comparison and for counting the algorithm's operations
                                  without the lane-replicated per-cell work: under this flag
@@ -260,11 +261,14 @@ int rhd_context_autotune(rhd_context_t *ctx, const rhd_grid_t *grids, int32_t n_
 int rhd_context_shape(const rhd_context_t *ctx, int32_t *threads, int32_t *cells_per_item);
 
 /* Read or set bucket `bucket`'s mappings, as lanes per cell: `passes` for the
- * FP32 and FP64 passes (bucket 0: 1 or 8; bucket 1: 1, 8, 16 or 32; bucket
- * 2: 1, 16 or 32), `correction` for the mixed form's correction step (bucket
- * 0: 8; bucket 1: 8 or 16; bucket 2: 16 or 32).  Defaults: passes 1, 1, 32;
- * correction 8, 16, 32.  RHD_EINVAL for another bucket or mapping (nothing
- * changed). */
+ * FP32 and FP64 passes (bucket 0: 0, 1 or 8; bucket 1: 0, 1, 8, 16 or 32;
+ * bucket 2: 0, 1, 16 or 32), `correction` for the mixed form's correction
+ * step (bucket 0: 8; bucket 1: 8 or 16; bucket 2: 16 or 32).  Passes 0 means
+ * the one-grid call's mapping for the call's precision: in the mixed form 8,
+ * 16 and 32 lanes (its FP32 passes' mapping, which the FP64 passes of the
+ * cells the correction leaves follow), in the FP64 form 1, 1 and 32.
+ * Defaults: passes 0, 0, 0; correction 8, 16, 32.  RHD_EINVAL for another
+ * bucket or mapping (nothing changed). */
 int rhd_context_mapping(const rhd_context_t *ctx, int32_t bucket, int32_t *passes,
                         int32_t *correction);
 int rhd_context_set_mapping(rhd_context_t *ctx, int32_t bucket, int32_t passes,

@@ -324,6 +324,12 @@ void launch_thread(const KParams &kp, const WarmStart &W, int sms, cudaStream_t 
   solve_fp64_kernel<MAXG, CACHE><<<b, threads, smem, st>>>(kp, W);
 }
 
+// Lanes per cell of the FP32 passes up to 16 and from 17 to 32 groups, 2
+// groups per lane (measured on GB300, 2M cells: 8 lanes at 16 groups 12.3 ms
+// against 23.9 ms one cell per thread; 16 lanes at 32 groups 23.2 ms against
+// 50.5 ms, 24.8 ms with 32 lanes of one group, 29.3 ms with 8 lanes of four).
+constexpr int kFp32LanesLe16 = 8, kFp32LanesLe32 = 16;
+
 void launch_fp64_passes_impl(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st);
 
 void launch_fp64_passes(const KParams &kp, const WarmStart &W, int sms, cudaStream_t st) {
@@ -347,6 +353,11 @@ void launch_fp64_passes_impl(const KParams &kp, const WarmStart &W, int sms, cud
     else launch_thread<kMaxG, true>(kp, W, sms, st);
     return;
   }
+  if (W.done && kp.G <= 32) {  // the mixed form's cells the correction left: its FP32 passes' lanes
+    if (kp.G <= 16) launch_warp<kFp32LanesLe16, 2>(kp, W, sms, st);
+    else launch_warp<kFp32LanesLe32, 2>(kp, W, sms, st);
+    return;
+  }
   if (kp.G <= 16) launch_thread<16>(kp, W, sms, st);
   else if (kp.G <= 32) launch_thread<32>(kp, W, sms, st);
   else if (kp.G <= 64 && (kp.flags & RHD_LANES_16)) launch_warp<16, 4>(kp, W, sms, st);
@@ -355,24 +366,38 @@ void launch_fp64_passes_impl(const KParams &kp, const WarmStart &W, int sms, cud
   else launch_thread<kMaxG>(kp, W, sms, st);
 }
 
+template <int L, int GPL>
+void launch_w32(const KParams &kp, const WarmOut &wo, const WarmStart &S, int sms,
+                cudaStream_t st) {
+  const int threads = 128;
+  const size_t smem = table_bytes(kp.G);
+  const int b = persistent_blocks(warm_warp32_kernel<L, GPL>, smem, sms, kp.n * L, threads);
+  warm_warp32_kernel<L, GPL><<<b, threads, smem, st>>>(kp, wo, S);
+}
+
+
 // The FP32 passes of the mixed form (writing the warm start wo; starting
-// from S where S.r is set): one cell per thread up to 32 groups and past 64,
-// a warp per cell in between (rhd_warp32.cuh).
+// from S where S.r is set): a warp per cell from 33 to 64 groups (two with
+// RHD_LANES_16), the lanes above at 1..32 groups (four or two cells per
+// warp), one cell per thread past 64 groups and with RHD_CELL_PER_THREAD
+// (rhd_warp32.cuh, rhd_mixed.cuh).
 template <int MAXG>
 void launch_fp32_passes_impl(const KParams &kp, const WarmOut &wo, const WarmStart &S, int sms,
                              cudaStream_t st) {
+  if (!(kp.flags & RHD_CELL_PER_THREAD)) {
+    const int lanes = kp.G <= 16 ? kFp32LanesLe16
+                      : kp.G <= 32 ? kFp32LanesLe32
+                      : kp.G <= 64 ? ((kp.flags & RHD_LANES_16) ? 16 : 32) : 0;
+    switch (kp.G <= 16 ? 100 + lanes : kp.G <= 32 ? 200 + lanes : 300 + lanes) {
+      case 108: launch_w32<8, 2>(kp, wo, S, sms, st); return;
+      case 216: launch_w32<16, 2>(kp, wo, S, sms, st); return;
+      case 316: launch_w32<16, 4>(kp, wo, S, sms, st); return;
+      case 332: launch_w32<32, 2>(kp, wo, S, sms, st); return;
+      default: break;
+    }
+  }
   const int threads = 128;
   const size_t smem = table_bytes(kp.G);
-  if (kp.G > 32 && kp.G <= 64 && !(kp.flags & RHD_CELL_PER_THREAD)) {
-    if (kp.flags & RHD_LANES_16) {  // two cells per warp
-      const int b = persistent_blocks(warm_warp32_kernel<16, 4>, smem, sms, kp.n * 16, threads);
-      warm_warp32_kernel<16, 4><<<b, threads, smem, st>>>(kp, wo, S);
-      return;
-    }
-    const int b = persistent_blocks(warm_warp32_kernel<32, 2>, smem, sms, kp.n * 32, threads);
-    warm_warp32_kernel<32, 2><<<b, threads, smem, st>>>(kp, wo, S);
-    return;
-  }
   const int ba = persistent_blocks(warm_fp32_kernel<MAXG>, smem, sms, kp.n, threads);
   warm_fp32_kernel<MAXG><<<ba, threads, smem, st>>>(kp, wo, S);
 }
@@ -643,11 +668,12 @@ int bucket_of(int G) { return G <= 16 ? 0 : G <= 32 ? 1 : 2; }
 
 // The mappings each bucket offers (lanes per cell; 1 = one cell per thread).
 // The groups per lane follow: the bucket's largest group count / lanes.
+// 0: the one-grid call's mapping for the call's precision (pass_lanes)
 bool pass_mapping_ok(int b, int m) {
   switch (b) {
-    case 0: return m == 1 || m == 8;
-    case 1: return m == 1 || m == 8 || m == 16 || m == 32;
-    case 2: return m == 1 || m == 16 || m == 32;
+    case 0: return m == 0 || m == 1 || m == 8;
+    case 1: return m == 0 || m == 1 || m == 8 || m == 16 || m == 32;
+    case 2: return m == 0 || m == 1 || m == 16 || m == 32;
   }
   return false;
 }
@@ -665,7 +691,7 @@ bool corr_mapping_ok(int b, int m) {
 struct rhd_context {
   int device = -1;
   int threads = 128, cpi = 512;                // shape of the cell-per-thread mapping (autotuned)
-  int pass_map[RHD_BATCH_BUCKETS] = {1, 1, 32};  // lanes per cell of each bucket's passes
+  int pass_map[RHD_BATCH_BUCKETS] = {0, 0, 0};   // lanes per cell of each bucket's passes (0: as one grid)
   int corr_map[RHD_BATCH_BUCKETS] = {8, 16, 32}; // lanes per cell of its correction step
   int cap_grids = 0;
   rhd::KParams *h_grids = nullptr, *d_grids = nullptr;
@@ -691,6 +717,17 @@ namespace rhd {
 namespace {
 
 const int64_t kTableWords = group_table_words(kMaxGB) + 1;
+
+// Lanes per cell of bucket b's passes: the mapping set, else the one-grid
+// call's for the precision (mixed form: the FP32 passes' 8, 16, 32 lanes,
+// which its FP64 passes follow; FP64 form: one cell per thread up to 32
+// groups, 32 lanes above).
+int pass_lanes(const rhd_context *c, int b, int prec) {
+  if (c->pass_map[b] != 0) return c->pass_map[b];
+  static const int mixed[kBuckets] = {kFp32LanesLe16, kFp32LanesLe32, 32};
+  static const int fp64[kBuckets] = {1, 1, 32};
+  return prec == RHD_MIXED ? mixed[b] : fp64[b];
+}
 
 void ctx_free(rhd_context *c) {
   if (c->exec) cudaGraphExecDestroy(c->exec);
@@ -781,7 +818,7 @@ int pack_batch(rhd_context *c, const rhd_grid_t *grids, int n_grids, int cpi, in
       carve(c->d_ws + at, g.n_cells, G, &c->h_warm[j], &unused);
       at += (warm_bytes(g.n_cells, G) + 255) & ~(size_t)255;
     }
-    const int per = c->pass_map[b] == 1 ? cpi : kCpiWarp;
+    const int per = pass_lanes(c, b, *prec) == 1 ? cpi : kCpiWarp;
     off_of(c->h_off, c, 2 * b)[ns[b]] = acc[2 * b];
     off_of(c->h_off, c, 2 * b + 1)[ns[b]] = acc[2 * b + 1];
     c->h_sel[(int64_t)b * c->cap_grids + ns[b]] = j;
@@ -908,7 +945,7 @@ cudaError_t enqueue_batch(rhd_context *c, int prec, int n_grids, int threads, in
       s = c->side[b - 1];
       cudaStreamWaitEvent(s, c->fork, 0);
     }
-    const int pm = c->pass_map[b];
+    const int pm = pass_lanes(c, b, prec);
     BatchArgs A{c->d_grids, c->d_tables, kTableWords, mixed ? c->d_warm : nullptr,
                 c->d_sel + (int64_t)b * cap, off_of(c->d_off, c, 2 * b), c->n_sel[b],
                 pm == 1 ? cpi : kCpiWarp, nullptr};

@@ -422,8 +422,9 @@ class GridSpec:
 
 
 BATCH_BUCKETS = 3  # RHD_BATCH_BUCKETS: group counts 1..16, 17..32, 33..64
-# the mappings each bucket offers, as lanes per cell (1: one cell per thread)
-PASS_MAPPINGS = ((1, 8), (1, 8, 16, 32), (1, 16, 32))
+# the mappings each bucket offers, as lanes per cell (1: one cell per thread;
+# passes 0: the one-grid call's mapping for the call's precision)
+PASS_MAPPINGS = ((0, 1, 8), (0, 1, 8, 16, 32), (0, 1, 16, 32))
 CORRECTION_MAPPINGS = ((8,), (8, 16), (16, 32))
 
 

@@ -158,7 +158,7 @@ def test_every_mapping_of_every_bucket_matches_the_oracle(precision):
 
 def test_set_mapping_rejects_what_a_bucket_does_not_offer():
     ctx = rhd.Context()
-    default = [(1, 8), (1, 16), (32, 32)]
+    default = [(0, 8), (0, 16), (0, 32)]  # passes 0: the one-grid call's, by precision
     assert ctx.mappings == default
     for b, p, c in [(0, 16, 8), (0, 1, 16), (1, 2, 8), (1, 1, 32), (2, 8, 32), (2, 1, 8),
                     (3, 1, 8), (-1, 1, 8)]:
