@@ -326,7 +326,9 @@ def run_ours(args, ws, rank):
     t_max = allmax(t_dev, ws)
     units = float(n) * G * args.steps
     total_units = allsum(units, ws)
-    launches = (1 if prec == rhd.FP64 else 3) + (1 if use_sur else 0)
+    # FP64 form: the FP64 passes; mixed form: FP32 passes, first correction step,
+    # correction, FP64 passes (no correction past 128 groups); + the inference
+    launches = (1 if prec == rhd.FP64 else (4 if G <= 128 else 2)) + (1 if use_sur else 0)
     form = ("mixed" if prec == rhd.MIXED else "fp64") + ("+surrogate" if use_sur else "")
 
     res = {"metric": METRIC, "value": total_units / t_max, "unit": UNIT, "n_gpus": ws,
@@ -475,9 +477,9 @@ def run_batched(args, ws, rank):
     restore()
     shape = ctx.autotune(specs, stream=stream)  # untimed; leaves the state unchanged
     buckets = sorted({0 if g.n_groups <= 16 else 1 if g.n_groups <= 32 else 2 for g in grids})
-    # per step: the table kernel, then per bucket its FP32 passes, correction
-    # and FP64 passes (mixed form) or its FP64 passes
-    launches = 1 + len(buckets) * (3 if prec == rhd.MIXED else 1)
+    # per step: the table kernel, then per bucket its FP32 passes, first
+    # correction step, correction and FP64 passes (mixed form) or its FP64 passes
+    launches = 1 + len(buckets) * (4 if prec == rhd.MIXED else 1)
     ms, clk = timed(batched, args.steps, args.warmup, True)
     t_max = allmax(sum(ms) / 1e3, ws)
     total = allsum(units1 * args.steps, ws)
