@@ -167,7 +167,15 @@ typedef struct {
  * dt (in place).  n_cells may be 0.  Returns RHD_OK or a negative RHD_E* code
  * (then nothing was launched).  The first call on a device initialises the
  * library's constant tables on that device (synchronously), so make it before
- * any stream capture. */
+ * any stream capture.  RHD_FP64 runs the paper's inner/outer iteration (Sec. 3)
+ * in FP64.  RHD_MIXED runs it in FP32 to FP32 resolution, takes a first Newton
+ * step on the coupled per-cell system from a float-float residual, then
+ * evaluates that system's residual in FP64, applies the paper's convergence
+ * tests to it and writes back in FP64 (another FP32-Jacobian step where the
+ * tests fail; the FP64 iteration for any cell left over), so its result
+ * meets the same tolerances and conserves energy and momentum to FP64
+ * round-off.  The mixed form uses a per-device workspace of 32 bytes per
+ * cell-group + 34 bytes per cell (grown on demand; RHD_ENOMEM if that fails). */
 int rhd_source_update(rhd_state_t *state, const rhd_groups_t *groups,
                       const rhd_opacity_law_t *opacity_law, double dt, int64_t n_cells,
                       void *stream);
